@@ -1,0 +1,17 @@
+"""Seeded synthetic instances of the multi-agent collision-avoidance QP.
+
+This module only *draws* problem data (starts, goals, model matrices,
+linearization halfspaces and the initial consensus positions). It holds none
+of the solver's arithmetic, and both the CPU oracle and the GPU path read the
+same arrays from it.
+"""
+from .generator import (  # noqa: F401
+    Batch,
+    SplitMix64,
+    make_config,
+    make_batch,
+    double_integrator,
+    pair_list,
+    random_scenario,
+    build_scenario,
+)

@@ -1,0 +1,254 @@
+"""ctypes binding of the plain-C FP64 oracle (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this package; the product library never does.  The C code lives in
+`tadmm_oracle.c`; see its header for what each routine computes and which part
+of the paper it follows.  Parity against numbers printed in the paper is
+unpinned (the paper prints no worked example); the routines are pinned in the
+tests against closed forms, bounded least squares, brute force and KKT
+invariants.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional
+
+import numpy as np
+
+from . import build as _build
+
+START_COLD, START_HOT, START_TURBO = 0, 1, 2
+QP_COLD, QP_LQR, QP_GIVEN = 0, 1, 2
+CONVERGED, NOT_CONVERGED, QP_FAIL, NUMERIC = 0, 1, 2, 3
+
+_dp = C.POINTER(C.c_double)
+_i8p = C.POINTER(C.c_int8)
+_u8p = C.POINTER(C.c_uint8)
+
+
+class AgentQP(C.Structure):
+    _fields_ = [("T", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("A", _dp), ("B", _dp),
+                ("Hx", _dp), ("gx", _dp), ("Hu", _dp), ("x0", _dp), ("umin", _dp), ("umax", _dp)]
+
+
+class Scenario(C.Structure):
+    _fields_ = [("N", C.c_int), ("T", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("dp", C.c_int),
+                ("A", _dp), ("B", _dp), ("Qd", _dp), ("Rd", _dp), ("Qfd", _dp),
+                ("x_init", _dp), ("x_ref", _dp), ("umin", _dp), ("umax", _dp),
+                ("a", _dp), ("w0", _dp), ("d_min", C.c_double), ("rho", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("start_mode", C.c_int), ("as_max", C.c_int), ("eps_rel", C.c_double),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("nthreads", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("X", _dp), ("U", _dp), ("theta", _dp), ("W", _i8p), ("mu", _dp), ("trace", _dp),
+                ("iters", C.c_int), ("status", C.c_int), ("r", C.c_double), ("s", C.c_double),
+                ("as_iters", C.c_int64), ("inv_dev", C.c_double)]
+
+
+class GlobalResult(C.Structure):
+    _fields_ = [("X", _dp), ("U", _dp), ("mu_h", _dp), ("act_h", _u8p), ("W", _i8p), ("mu_u", _dp),
+                ("iters", C.c_int), ("status", C.c_int), ("obj", C.c_double)]
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        _LIB = C.CDLL(path)
+        _LIB.orc_agent_qp_solve.argtypes = [C.POINTER(AgentQP), C.c_int, C.c_int, C.c_double, _dp, _i8p,
+                                            _dp, _dp, C.POINTER(C.c_int)]
+        _LIB.orc_agent_eqp.argtypes = [C.POINTER(AgentQP), _i8p, _dp, _dp, _dp]
+        _LIB.orc_agent_bruteforce.argtypes = [C.POINTER(AgentQP), C.c_double, _dp, _i8p]
+        _LIB.orc_halfspace_project.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp]
+        _LIB.orc_halfspace_project.restype = C.c_double
+        _LIB.orc_admm.argtypes = [C.POINTER(Scenario), C.POINTER(Options), C.POINTER(Result)]
+        _LIB.orc_admm_batch.argtypes = [C.POINTER(Scenario), C.c_int, C.POINTER(Options),
+                                        C.POINTER(Result), C.c_int]
+        _LIB.orc_global_qp.argtypes = [C.POINTER(Scenario), C.c_int, C.c_double, C.POINTER(GlobalResult)]
+        _LIB.orc_global_gradient.argtypes = [C.POINTER(Scenario), _u8p, _i8p, _dp, C.c_double, _dp, _dp,
+                                             _dp, _dp, _dp, _dp]
+    return _LIB
+
+
+def _d(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# ---------------------------------------------------------------- agent QP
+class _AgentQPData:
+    def __init__(self, A, B, Hx, gx, Hu, x0, umin, umax):
+        self.arrs = [_f64(v) for v in (A, B, Hx, gx, Hu, x0, umin, umax)]
+        A, B, Hx, gx, Hu, x0, umin, umax = self.arrs
+        self.T, self.nx = Hx.shape
+        self.nu = Hu.shape[0]
+        self.s = AgentQP(self.T, self.nx, self.nu, _d(A), _d(B), _d(Hx), _d(gx), _d(Hu), _d(x0),
+                         _d(umin), _d(umax))
+
+
+def agent_qp_solve(A, B, Hx, gx, Hu, x0, umin, umax, start=QP_LQR, as_max=1000, eps_rel=1e-12,
+                   u=None, W=None):
+    """Per-agent box-constrained LQ problem (dense KKT active set)."""
+    q = _AgentQPData(A, B, Hx, gx, Hu, x0, umin, umax)
+    T, nx, nu = q.T, q.nx, q.nu
+    u = np.zeros((T, nu)) if u is None else _f64(u).copy()
+    W = np.zeros((T, nu), dtype=np.int8) if W is None else np.ascontiguousarray(W, dtype=np.int8).copy()
+    x = np.zeros((T + 1, nx))
+    mu = np.zeros((T, nu))
+    n = C.c_int(0)
+    st = lib().orc_agent_qp_solve(C.byref(q.s), start, as_max, eps_rel, _d(u), W.ctypes.data_as(_i8p),
+                                  _d(x), _d(mu), C.byref(n))
+    return dict(status=st, u=u, W=W, x=x, mu=mu, n_eqp=n.value)
+
+
+def agent_eqp(A, B, Hx, gx, Hu, x0, umin, umax, W=None):
+    q = _AgentQPData(A, B, Hx, gx, Hu, x0, umin, umax)
+    T, nx, nu = q.T, q.nx, q.nu
+    W = np.zeros((T, nu), dtype=np.int8) if W is None else np.ascontiguousarray(W, dtype=np.int8)
+    u = np.zeros((T, nu)); x = np.zeros((T + 1, nx)); mu = np.zeros((T, nu))
+    rc = lib().orc_agent_eqp(C.byref(q.s), W.ctypes.data_as(_i8p), _d(u), _d(x), _d(mu))
+    if rc != 0:
+        raise RuntimeError("singular KKT system")
+    return dict(u=u, x=x, mu=mu)
+
+
+def agent_bruteforce(A, B, Hx, gx, Hu, x0, umin, umax, tol=1e-9):
+    q = _AgentQPData(A, B, Hx, gx, Hu, x0, umin, umax)
+    u = np.zeros((q.T, q.nu)); W = np.zeros((q.T, q.nu), dtype=np.int8)
+    found = lib().orc_agent_bruteforce(C.byref(q.s), tol, _d(u), W.ctypes.data_as(_i8p))
+    return dict(found=found, u=u, W=W)
+
+
+def halfspace_project(a, d, vi, vj):
+    """Projection of (vi, vj) onto {a'(wi - wj) >= d}; returns (theta, wi, wj)."""
+    a, vi, vj = _f64(a), _f64(vi), _f64(vj)
+    wi = np.zeros_like(vi); wj = np.zeros_like(vj)
+    th = lib().orc_halfspace_project(a.shape[0], _d(a), float(d), _d(vi), _d(vj), _d(wi), _d(wj))
+    return th, wi, wj
+
+
+# ---------------------------------------------------------------- scenarios
+class _ScenarioData:
+    """Keeps the numpy slices of scenario k of a Batch alive for the C call."""
+
+    def __init__(self, batch, k: int):
+        ao, po, so = batch.agent_off, batch.pairstep_off, batch.agentstep_off
+        N, T = int(batch.N[k]), int(batch.T[k])
+        sl = lambda arr, off: np.ascontiguousarray(arr[off[k]:off[k + 1]], dtype=np.float64)
+        self.N, self.T, self.nx, self.nu, self.dp = N, T, batch.nx, batch.nu, batch.dp
+        self.P = N * (N - 1) // 2
+        self.keep = dict(A=_f64(batch.A), B=_f64(batch.B), Qd=sl(batch.Qd, ao), Rd=sl(batch.Rd, ao),
+                         Qfd=sl(batch.Qfd, ao), x_init=sl(batch.x_init, ao), x_ref=sl(batch.x_ref, ao),
+                         umin=_f64(batch.umin), umax=_f64(batch.umax), a=sl(batch.a, po),
+                         w0=sl(batch.w0, so))
+        if self.keep["a"].size == 0:
+            self.keep["a"] = np.zeros(1)
+        kp = self.keep
+        self.s = Scenario(N, T, batch.nx, batch.nu, batch.dp, _d(kp["A"]), _d(kp["B"]), _d(kp["Qd"]),
+                          _d(kp["Rd"]), _d(kp["Qfd"]), _d(kp["x_init"]), _d(kp["x_ref"]),
+                          _d(kp["umin"]), _d(kp["umax"]), _d(kp["a"]), _d(kp["w0"]),
+                          float(batch.d_min[k]), float(batch.rho[k]))
+
+
+class _ResultData:
+    def __init__(self, sd: _ScenarioData, max_iter: int, trace: bool):
+        N, T, nx, nu = sd.N, sd.T, sd.nx, sd.nu
+        self.X = np.zeros((N, T + 1, nx))
+        self.U = np.zeros((N, T, nu))
+        self.theta = np.zeros((max(sd.P, 1), T))
+        self.W = np.zeros((N, T, nu), dtype=np.int8)
+        self.mu = np.zeros((N, T, nu))
+        self.trace = np.zeros((max(max_iter, 1), 2)) if trace else None
+        self.r = Result(_d(self.X), _d(self.U), _d(self.theta), self.W.ctypes.data_as(_i8p), _d(self.mu),
+                        _d(self.trace) if trace else None, 0, 0, 0.0, 0.0, 0, 0.0)
+        self.P = sd.P
+
+    def to_dict(self):
+        r = self.r
+        out = dict(X=self.X, U=self.U, theta=self.theta[:self.P], W=self.W, mu=self.mu,
+                   iters=r.iters, status=r.status, r=r.r, s=r.s, as_iters=int(r.as_iters),
+                   inv_dev=r.inv_dev)
+        if self.trace is not None:
+            out["trace"] = self.trace[:r.iters]
+        return out
+
+
+def _options(start_mode, as_max, eps_rel, tol, max_iter, nthreads):
+    return Options(start_mode, as_max, eps_rel, tol, max_iter, nthreads)
+
+
+def admm(batch, k: int = 0, start_mode=START_TURBO, tol=1e-4, max_iter=500, as_max=None,
+         eps_rel=1e-12, nthreads=0, trace=False):
+    """Literal vector-form ADMM on scenario k of `batch`."""
+    sd = _ScenarioData(batch, k)
+    if as_max is None:
+        as_max = 10 * sd.T * sd.nu + 10
+    rd = _ResultData(sd, max_iter, trace)
+    o = _options(start_mode, as_max, eps_rel, tol, max_iter, nthreads)
+    lib().orc_admm(C.byref(sd.s), C.byref(o), C.byref(rd.r))
+    return rd.to_dict()
+
+
+def admm_batch(batch, idx: Optional[List[int]] = None, start_mode=START_TURBO, tol=1e-4, max_iter=500,
+               as_max=None, eps_rel=1e-12, nthreads=None):
+    """ADMM on several scenarios in parallel over host cores. Returns (results, threads used)."""
+    idx = list(range(batch.n_scen)) if idx is None else list(idx)
+    sds = [_ScenarioData(batch, k) for k in idx]
+    rds = [_ResultData(sd, max_iter, False) for sd in sds]
+    S = len(idx)
+    sarr = (Scenario * S)(*[sd.s for sd in sds])
+    rarr = (Result * S)(*[rd.r for rd in rds])
+    am = as_max if as_max is not None else 10 * int(batch.T.max()) * batch.nu + 10
+    o = _options(start_mode, am, eps_rel, tol, max_iter, 0)
+    nt = os.cpu_count() if nthreads is None else nthreads
+    used = lib().orc_admm_batch(sarr, S, C.byref(o), rarr, nt)
+    out = []
+    for rd, rr in zip(rds, rarr):
+        rd.r = rr
+        out.append(rd.to_dict())
+    return out, used
+
+
+def global_qp(batch, k: int = 0, as_max=100000, eps_rel=1e-12):
+    """Centralized linearized QP (Eq. 1 with halfspaces), condensed, active set."""
+    sd = _ScenarioData(batch, k)
+    N, T, nx, nu, P = sd.N, sd.T, sd.nx, sd.nu, sd.P
+    X = np.zeros((N, T + 1, nx)); U = np.zeros((N, T, nu))
+    mu_h = np.zeros((max(P, 1), T)); act = np.zeros((max(P, 1), T), dtype=np.uint8)
+    W = np.zeros((N, T, nu), dtype=np.int8); mu_u = np.zeros((N, T, nu))
+    r = GlobalResult(_d(X), _d(U), _d(mu_h), act.ctypes.data_as(_u8p), W.ctypes.data_as(_i8p), _d(mu_u),
+                     0, 0, 0.0)
+    rc = lib().orc_global_qp(C.byref(sd.s), as_max, eps_rel, C.byref(r))
+    if rc != 0:
+        raise RuntimeError("global QP build failed")
+    return dict(X=X, U=U, mu_h=mu_h[:P], act_h=act[:P], W=W, mu_u=mu_u, iters=r.iters, status=r.status,
+                obj=r.obj)
+
+
+def global_gradient(batch, k: int, act_h, W, targets, qf_tie=10.0):
+    """Polished solution at the active set and the implicit-KKT loss gradient."""
+    sd = _ScenarioData(batch, k)
+    N, T, nx, nu, P = sd.N, sd.T, sd.nx, sd.nu, sd.P
+    act = np.zeros((max(P, 1), T), dtype=np.uint8)
+    act[:P] = np.asarray(act_h, dtype=np.uint8).reshape(P, T)
+    Wc = np.ascontiguousarray(W, dtype=np.int8).reshape(N, T, nu)
+    tg = _f64(targets).reshape(N, T, sd.dp)
+    X = np.zeros((N, T + 1, nx)); U = np.zeros((N, T, nu)); loss = np.zeros(1)
+    gQ = np.zeros((N, nx)); gR = np.zeros((N, nu)); gG = np.zeros((N, nx))
+    rc = lib().orc_global_gradient(C.byref(sd.s), act.ctypes.data_as(_u8p), Wc.ctypes.data_as(_i8p),
+                                   _d(tg), qf_tie, _d(X), _d(U), _d(loss), _d(gQ), _d(gR), _d(gG))
+    if rc != 0:
+        raise RuntimeError(f"gradient failed ({rc})")
+    return dict(X=X, U=U, loss=float(loss[0]), gQ=gQ, gR=gR, gGoal=gG)

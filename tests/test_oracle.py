@@ -1,0 +1,380 @@
+"""Pins of the CPU FP64 oracle against things other than itself.
+
+Each test checks one oracle routine against an independent formulation:
+condensed least squares, SciPy's bounded-variable least squares, exhaustive
+enumeration, a numpy adjoint recursion (the costate identity of Sec. IV.B),
+SLSQP for the consensus projection, the KKT conditions of the centralized QP
+of Eq. (1), finite differences for the gradient and the problem-size table of
+Sec. V.A (Table 1).
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import lsq_linear, minimize
+
+import oracle
+from instances import make_config, random_scenario, pair_list
+from instances.generator import SplitMix64, make_batch, build_scenario
+from tests.helpers import agent_condensed_qp, condensed, costate_gradient, random_agent_qp
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ sizes
+def test_table1_problem_dimensions():
+    """Sec. V.A Table 1: per-agent variables (T+1)nx + T nu, dynamics rows T nx,
+    and about N(N-1)/2 collision rows per step.  The table prints "~" and counts
+    T steps for 2 agents but T+1 for the others; the build constrains t = 1..T
+    (x_0 is data), i.e. N(N-1)/2 * T rows."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table1_problem_dimensions.txt"))
+    T, nx, nu = 20, 4, 2
+    for N, nvar, ndyn, ncol in rows:
+        N = int(N)
+        assert N * ((T + 1) * nx + T * nu) == nvar
+        assert N * T * nx == ndyn
+        assert ncol in (N * (N - 1) // 2 * T, N * (N - 1) // 2 * (T + 1))
+    b = make_config(2)
+    assert b.a.shape[0] == 91 * 20 and b.w0.shape[0] == 14 * 20
+    assert b.N[0] == 14 and b.T[0] == 20
+
+
+# ------------------------------------------------------------------ generator
+def test_generator_deterministic_and_certified():
+    b1 = make_config(3, n_scen=6)
+    b2 = make_config(3, n_scen=6)
+    for f in ("N", "T", "x_init", "x_ref", "a", "w0"):
+        assert np.array_equal(getattr(b1, f), getattr(b2, f))
+    # the first scenarios do not depend on the batch size
+    b3 = make_config(3, n_scen=3)
+    assert np.array_equal(b3.a, b1.a[:b3.a.shape[0]])
+    for k in range(b1.n_scen):
+        s = b1.scenario(k)
+        N, T, d = int(s.N[0]), int(s.T[0]), float(s.d_min[0])
+        g = s.w0.reshape(N, T, 2)
+        pl = pair_list(N)
+        a = s.a.reshape(len(pl), T, 2)
+        assert np.allclose(np.linalg.norm(a, axis=-1), 1.0)
+        sep = np.einsum("ptc,ptc->pt", a, g[pl[:, 0]] - g[pl[:, 1]])
+        assert sep.min() >= 1.1 * d - 1e-12          # the guess satisfies every halfspace
+        st = s.x_init[:, :2]
+        dd = np.linalg.norm(st[pl[:, 0]] - st[pl[:, 1]], axis=-1)
+        assert dd.min() >= 2 * d                      # rejection-sampled starts
+        # guesses are the zero-input trajectories of the double integrator
+        for i in range(N):
+            x = s.x_init[i].copy()
+            for t in range(T):
+                x = s.A @ x
+                assert np.allclose(x[:2], g[i, t], atol=1e-12)
+
+
+def test_splitmix64_reference_values():
+    """SplitMix64 (Steele, Lea & Flood 2014) outputs for seed 0: the published
+    first outputs 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4."""
+    r = SplitMix64(0)
+    v = r.next_u64(2)
+    assert int(v[0]) == 0xE220A8397B1DCDAF
+    assert int(v[1]) == 0x6E789E6AA1B965F4
+
+
+# ------------------------------------------------------------------ per-agent QP
+@pytest.mark.parametrize("seed", range(6))
+def test_eqp_unconstrained_equals_condensed_solve(seed):
+    """Empty working set: the dense KKT solve equals the minimiser of the
+    condensed quadratic (plain linear solve of its normal equations)."""
+    rng = np.random.default_rng(seed)
+    T = 5 + seed
+    A, B, Hx, gx, Hu, x0, umin, umax = random_agent_qp(rng, T, double_integrator=seed % 2 == 0)
+    out = oracle.agent_eqp(A, B, Hx, gx, Hu, x0, umin, umax)
+    H, g, F, G = agent_condensed_qp(A, B, Hx, gx, Hu, x0)
+    u = np.linalg.solve(H, -g)
+    assert np.allclose(out["u"].ravel(), u, rtol=1e-10, atol=1e-10 * max(1, np.abs(u).max()))
+    # forward pass satisfies the dynamics exactly (to rounding), Sec. IV.B
+    x = out["x"]
+    for t in range(T):
+        assert np.allclose(x[t + 1], A @ x[t] + B @ out["u"][t], atol=1e-10 * max(1, np.abs(x).max()))
+    # costate identity: gradient of the objective w.r.t. free inputs vanishes
+    grad = costate_gradient(A, B, Hx, gx, Hu, x, out["u"])
+    assert np.abs(grad).max() <= 1e-8 * max(1.0, np.abs(gx).max())
+
+
+def _bvls(A, B, Hx, gx, Hu, x0, umin, umax):
+    H, g, _, _ = agent_condensed_qp(A, B, Hx, gx, Hu, x0)
+    L = np.linalg.cholesky(H)
+    M = L.T
+    rhs = -np.linalg.solve(L, g)
+    T, nu = Hx.shape[0], B.shape[1]
+    lb = np.tile(umin, T)
+    ub = np.tile(umax, T)
+    res = lsq_linear(M, rhs, bounds=(lb, ub), method="bvls", tol=1e-15, lsmr_tol=None)
+    return res.x.reshape(T, nu), H, g
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("start", [oracle.QP_COLD, oracle.QP_LQR])
+def test_box_qp_matches_bvls(seed, start):
+    """Box-constrained per-agent QP: active-set result equals SciPy's BVLS on the
+    equivalent bounded least-squares problem; KKT conditions hold."""
+    rng = np.random.default_rng(100 + seed)
+    T = 6 + 2 * seed
+    A, B, Hx, gx, Hu, x0, umin, umax = random_agent_qp(rng, T, double_integrator=seed % 3 != 0)
+    out = oracle.agent_qp_solve(A, B, Hx, gx, Hu, x0, umin, umax, start=start)
+    assert out["status"] == oracle.CONVERGED
+    u_ref, H, g = _bvls(A, B, Hx, gx, Hu, x0, umin, umax)
+    scale = max(1.0, np.abs(u_ref).max())
+    assert np.abs(out["u"] - u_ref).max() <= 1e-8 * scale
+    # KKT: reduced gradient by the adjoint recursion
+    grad = costate_gradient(A, B, Hx, gx, Hu, out["x"], out["u"])
+    W = out["W"]
+    gs = max(1.0, np.abs(grad).max())
+    assert np.abs(grad[W == 0]).max(initial=0) <= 1e-8 * gs
+    mu_ref = np.where(W == 1, grad, np.where(W == 2, -grad, 0.0))
+    assert np.allclose(out["mu"], mu_ref, atol=1e-8 * gs)
+    assert out["mu"].min() >= -1e-9 * gs
+    lo = np.broadcast_to(umin, out["u"].shape)
+    hi = np.broadcast_to(umax, out["u"].shape)
+    assert np.all(out["u"] >= lo) and np.all(out["u"] <= hi)
+    assert np.array_equal(out["u"][W == 1], lo[W == 1]) and np.array_equal(out["u"][W == 2], hi[W == 2])
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_box_qp_matches_bruteforce(seed):
+    """Tiny QPs (T=3, nu=2: 3^6 working sets): exactly one KKT point exists and
+    every start of the active-set method reaches it with the same active set."""
+    rng = np.random.default_rng(200 + seed)
+    A, B, Hx, gx, Hu, x0, umin, umax = random_agent_qp(rng, 3, box=0.3)
+    bf = oracle.agent_bruteforce(A, B, Hx, gx, Hu, x0, umin, umax, tol=1e-10)
+    assert bf["found"] == 1
+    for start in (oracle.QP_COLD, oracle.QP_LQR):
+        out = oracle.agent_qp_solve(A, B, Hx, gx, Hu, x0, umin, umax, start=start)
+        assert out["status"] == oracle.CONVERGED
+        assert np.allclose(out["u"], bf["u"], atol=1e-10)
+        assert np.array_equal(out["W"], bf["W"])
+    u_ref, _, _ = _bvls(A, B, Hx, gx, Hu, x0, umin, umax)
+    assert np.allclose(bf["u"], u_ref, atol=1e-8)
+
+
+def test_box_qp_hot_start_from_solution_is_one_solve():
+    """Hot start from the optimal (u, W) of the same QP needs one EQP solve."""
+    rng = np.random.default_rng(7)
+    A, B, Hx, gx, Hu, x0, umin, umax = random_agent_qp(rng, 12)
+    first = oracle.agent_qp_solve(A, B, Hx, gx, Hu, x0, umin, umax, start=oracle.QP_COLD)
+    hot = oracle.agent_qp_solve(A, B, Hx, gx, Hu, x0, umin, umax, start=oracle.QP_GIVEN,
+                                u=first["u"], W=first["W"])
+    assert hot["n_eqp"] == 1
+    assert np.allclose(hot["u"], first["u"], atol=1e-12)
+
+
+def test_box_qp_wide_box_is_lqr():
+    """umin = -inf-like, umax = +inf-like: the QP is the unconstrained LQR."""
+    rng = np.random.default_rng(11)
+    A, B, Hx, gx, Hu, x0, umin, umax = random_agent_qp(rng, 9)
+    big = np.full_like(umin, 1e9)
+    out = oracle.agent_qp_solve(A, B, Hx, gx, Hu, x0, -big, big, start=oracle.QP_LQR)
+    assert out["n_eqp"] == 0 and not out["W"].any()
+    H, g, _, _ = agent_condensed_qp(A, B, Hx, gx, Hu, x0)
+    assert np.allclose(out["u"].ravel(), np.linalg.solve(H, -g), atol=1e-9)
+
+
+def test_as_max_reports_qp_fail():
+    rng = np.random.default_rng(3)
+    A, B, Hx, gx, Hu, x0, umin, umax = random_agent_qp(rng, 10, box=0.2)
+    out = oracle.agent_qp_solve(A, B, Hx, gx, Hu, x0, umin, umax, start=oracle.QP_COLD, as_max=1)
+    assert out["status"] == oracle.QP_FAIL
+
+
+# ------------------------------------------------------------------ consensus projection
+@pytest.mark.parametrize("seed", range(6))
+def test_halfspace_projection_matches_slsqp(seed):
+    """The consensus step equals the Euclidean projection computed by a generic
+    constrained solver, for active and inactive cases, 2D and 3D."""
+    rng = np.random.default_rng(300 + seed)
+    dp = 2 + seed % 2
+    a = rng.standard_normal(dp)
+    a /= np.linalg.norm(a)
+    vi, vj = rng.standard_normal(dp), rng.standard_normal(dp)
+    d = float(a @ (vi - vj)) + (0.7 if seed % 3 else -0.5)  # active unless seed % 3 == 0
+    th, wi, wj = oracle.halfspace_project(a, d, vi, vj)
+    v = np.concatenate([vi, vj])
+    n = np.concatenate([a, -a])
+    sol = minimize(lambda w: 0.5 * np.sum((w - v) ** 2), v, jac=lambda w: w - v, method="SLSQP",
+                   constraints=[dict(type="ineq", fun=lambda w: n @ w - d, jac=lambda w: n)],
+                   options=dict(ftol=1e-15, maxiter=200))
+    assert np.allclose(np.concatenate([wi, wj]), sol.x, atol=1e-7)
+    assert th >= 0.0
+    assert float(a @ (wi - wj)) >= d - 1e-12
+    assert np.allclose(wi - vi, th * a) and np.allclose(wj - vj, -th * a)
+    if seed % 3 == 0:
+        assert th == 0.0
+
+
+# ------------------------------------------------------------------ ADMM
+def test_admm_single_agent_one_iteration():
+    """N = 1: no coupling; ADMM stops after one x-update at the box-QP solution."""
+    b = random_scenario(seed=1, N=1, T=15)
+    r = oracle.admm(b, 0, max_iter=50)
+    assert r["status"] == oracle.CONVERGED and r["iters"] == 1
+    Hx = np.tile(2 * b.Qd[0], (15, 1))
+    Hx[-1] = 2 * b.Qfd[0]
+    gx = -Hx * b.x_ref[0]
+    u_ref, _, _ = _bvls(b.A, b.B, Hx, gx, 2 * b.Rd[0], b.x_init[0], b.umin, b.umax)
+    assert np.abs(r["U"][0] - u_ref).max() <= 1e-8
+
+
+def test_admm_start_modes_give_same_iterates():
+    """Cold, hot and turbo starts only change the active-set path: every ADMM
+    iterate is the unique per-agent QP solution, so the runs agree."""
+    b = make_config(1)
+    outs = [oracle.admm(b, 0, start_mode=m, max_iter=4, tol=0.0) for m in
+            (oracle.START_COLD, oracle.START_HOT, oracle.START_TURBO)]
+    for o in outs[1:]:
+        assert np.abs(o["X"] - outs[0]["X"]).max() <= 1e-9
+        assert np.abs(o["theta"] - outs[0]["theta"]).max() <= 1e-9
+    assert outs[0]["as_iters"] >= outs[1]["as_iters"]
+
+
+def test_admm_dual_invariant_and_uncoupled_case():
+    """Two agents that never come close: every halfspace stays inactive, theta = 0,
+    and the result equals two independent box-QP solutions."""
+    T = 12
+    starts = np.array([[-4.0, 0.0], [4.0, 0.0]])
+    goals = np.array([[-4.0, 2.0], [4.0, -2.0]])
+    x_init, x_ref, a, w0, c = build_scenario(starts, goals, T, 0.1, 0.5)
+    b = make_batch([dict(N=2, T=T, x_init=x_init, x_ref=x_ref, a=a, w0=w0, d=0.5, rho=1.0, umax=1.0, c=c)],
+                   dp=2, dt=0.1, umax=1.0)
+    r = oracle.admm(b, 0, tol=1e-11, max_iter=3000)
+    assert r["status"] == oracle.CONVERGED
+    assert np.all(r["theta"] == 0.0)
+    assert r["inv_dev"] <= 1e-12
+    for i in range(2):
+        Hx = np.tile(2 * b.Qd[i], (T, 1))
+        Hx[-1] = 2 * b.Qfd[i]
+        gx = -Hx * b.x_ref[i]
+        u_ref, _, _ = _bvls(b.A, b.B, Hx, gx, 2 * b.Rd[i], b.x_init[i], b.umin, b.umax)
+        assert np.abs(r["U"][i] - u_ref).max() <= 1e-7
+
+
+def _global_kkt_check(b, g, tol):
+    """KKT conditions of Eq. (1) with linearized halfspaces, written independently:
+    stationarity H U + g = sum mu_h n_h + bound terms, feasibility, complementarity."""
+    N, T, nx, nu, dp = int(b.N[0]), int(b.T[0]), b.nx, b.nu, b.dp
+    pl = pair_list(N)
+    m = T * nu
+    Hs, gs, Fs, Gs = [], [], [], []
+    for i in range(N):
+        Hx = np.tile(2 * b.Qd[i], (T, 1))
+        Hx[-1] = 2 * b.Qfd[i]
+        H, gg, F, G = agent_condensed_qp(b.A, b.B, Hx, -Hx * b.x_ref[i], 2 * b.Rd[i], b.x_init[i])
+        Hs.append(H); gs.append(gg); Fs.append(F); Gs.append(G)
+    U = g["U"].reshape(N, m)
+    grad = np.stack([Hs[i] @ U[i] + gs[i] for i in range(N)])
+    a = b.a.reshape(len(pl), T, dp)
+    res = grad.copy()
+    worst_slack = np.inf
+    for k, (i, j) in enumerate(pl):
+        for t in range(1, T + 1):
+            ni = a[k, t - 1] @ Gs[i][t][:dp]
+            nj = -a[k, t - 1] @ Gs[j][t][:dp]
+            slack = a[k, t - 1] @ ((Fs[i][t] + Gs[i][t] @ U[i])[:dp] - (Fs[j][t] + Gs[j][t] @ U[j])[:dp]) - b.d_min[0]
+            worst_slack = min(worst_slack, slack)
+            mu = g["mu_h"][k, t - 1]
+            assert mu >= -tol
+            assert abs(mu * slack) <= tol * max(1.0, abs(mu))
+            res[i] -= mu * ni
+            res[j] -= mu * nj
+    Wf = g["W"].reshape(N, m)
+    mu_u = g["mu_u"].reshape(N, m)
+    res -= np.where(Wf == 1, mu_u, 0.0) - np.where(Wf == 2, mu_u, 0.0)
+    assert worst_slack >= -tol
+    assert np.abs(res).max() <= tol * max(1.0, np.abs(grad).max())
+    assert mu_u.min() >= -tol
+
+
+@pytest.mark.parametrize("seed,N,T", [(1, 3, 8), (2, 4, 6), (5, 3, 10)])
+def test_global_qp_satisfies_kkt(seed, N, T):
+    b = random_scenario(seed=seed, N=N, T=T, box=2.0)
+    g = oracle.global_qp(b, 0)
+    assert g["status"] == oracle.CONVERGED
+    _global_kkt_check(b, g, 1e-8)
+
+
+def test_admm_converges_to_global_qp():
+    """The ADMM fixed point is the centralized optimum: run to tol 1e-10 and compare
+    with the global QP; the halfspace multipliers are rho * theta."""
+    b = random_scenario(seed=3, N=3, T=8, box=1.5, rho=20.0)
+    g = oracle.global_qp(b, 0)
+    assert g["status"] == oracle.CONVERGED and g["act_h"].sum() > 0
+    r = oracle.admm(b, 0, tol=1e-10, max_iter=20000)
+    assert r["status"] == oracle.CONVERGED
+    assert np.abs(r["X"] - g["X"]).max() <= 1e-7
+    assert np.abs(b.rho[0] * r["theta"] - g["mu_h"]).max() <= 1e-5 * max(1, g["mu_h"].max())
+    assert np.array_equal(r["W"], g["W"])
+    assert r["inv_dev"] <= 1e-10
+
+
+def test_literal_reading_is_infeasible_and_does_not_converge():
+    """Zero initial velocity with c = 1 guess lines (the literal reading): the
+    agents cannot swap sides in 2 s, the halfspace QP is infeasible and the
+    residual stalls."""
+    b = make_config(1, literal=True)
+    r = oracle.admm(b, 0, max_iter=300)
+    assert r["status"] == oracle.NOT_CONVERGED and r["iters"] == 300
+    assert r["r"] > 1e-2
+
+
+# ------------------------------------------------------------------ gradient
+def _loss(X, targets, dp):
+    N, T1, _ = X.shape
+    return float(((X[:, 1:, :dp] - targets.reshape(N, T1 - 1, dp)) ** 2).sum())
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_gradient_matches_central_differences(seed):
+    """Implicit-KKT gradient at the final active set equals central finite
+    differences (h = 1e-6) of the re-solved centralized QP."""
+    b = random_scenario(seed=seed, N=3, T=6, box=1.5)
+    rng = np.random.default_rng(seed)
+    targets = rng.uniform(-2, 2, size=(3 * 6, 2))
+    g = oracle.global_qp(b, 0)
+    gr = oracle.global_gradient(b, 0, g["act_h"], g["W"], targets, qf_tie=10.0)
+    assert np.abs(gr["X"] - g["X"]).max() <= 1e-9
+    h = 1e-6
+
+    def solve_loss(mod):
+        bb = b.subset([0])
+        mod(bb)
+        gg = oracle.global_qp(bb, 0)
+        same = np.array_equal(gg["act_h"], g["act_h"]) and np.array_equal(gg["W"], g["W"])
+        return _loss(gg["X"], targets, 2), same
+
+    checked = 0
+    for i in range(3):
+        for r in range(4):
+            def mq(bb, s):
+                bb.Qd = bb.Qd.copy(); bb.Qfd = bb.Qfd.copy()
+                bb.Qd[i, r] += s; bb.Qfd[i, r] += 10 * s
+            lp, s1 = solve_loss(lambda bb: mq(bb, h))
+            lm, s2 = solve_loss(lambda bb: mq(bb, -h))
+            if s1 and s2:
+                fd = (lp - lm) / (2 * h)
+                assert abs(fd - gr["gQ"][i, r]) <= 1e-5 * max(1.0, abs(fd)), (i, r)
+                checked += 1
+
+            def mg(bb, s):
+                bb.x_ref = bb.x_ref.copy(); bb.x_ref[i, r] += s
+            lp, s1 = solve_loss(lambda bb: mg(bb, h))
+            lm, s2 = solve_loss(lambda bb: mg(bb, -h))
+            if s1 and s2:
+                fd = (lp - lm) / (2 * h)
+                assert abs(fd - gr["gGoal"][i, r]) <= 1e-5 * max(1.0, abs(fd)), (i, r)
+                checked += 1
+        for c in range(2):
+            def mr(bb, s):
+                bb.Rd = bb.Rd.copy(); bb.Rd[i, c] += s
+            lp, s1 = solve_loss(lambda bb: mr(bb, h))
+            lm, s2 = solve_loss(lambda bb: mr(bb, -h))
+            if s1 and s2:
+                fd = (lp - lm) / (2 * h)
+                assert abs(fd - gr["gR"][i, c]) <= 1e-5 * max(1.0, abs(fd)), (i, c)
+                checked += 1
+    assert checked >= 20
