@@ -1,0 +1,149 @@
+/*
+ * tadmm — batched ADMM for densely coupled multi-agent trajectory QPs on GB300
+ * (sm_103a).  C ABI of the library libtadmm.so.
+ *
+ * The method (TurboADMM, arXiv 2602.15838) solves the centralized QP of
+ * Eq. (1) (Sec. III.A) with the collision constraints linearized to halfspaces
+ *     a_ijt' (p_it - p_jt) >= d_min,   i < j,  t = 1..T,
+ * by ADMM (Sec. III.B): each iteration solves one box-constrained LQ problem
+ * per agent (the local QP of Sec. IV.A, a Riccati-factorized primal active set
+ * that is warm-started from the affine LQR solution of Sec. IV.B on the first
+ * iteration and hot-started from the previous working set and factors
+ * afterwards, Sec. IV.C), then projects the per-pair consensus copies onto the
+ * halfspace, updates the scaled duals (Sec. IV.A consensus and dual updates)
+ * and reduces the primal and dual residuals (Sec. V.A convergence criteria).
+ *
+ * Model conventions: state x = [p; v] with the position p in the first dp
+ * components (C = [I_dp 0]); objective exactly as Eq. (1) (no factor 1/2):
+ * sum_t ||x_t - x_ref||^2_Q + ||u_t||^2_R over t < T plus ||x_T - x_ref||^2_Qf,
+ * diagonal Q, R, Qf; input box umin <= u_t <= umax; no state bounds.
+ * Supported dimensions: (nx, nu, dp) = (4, 2, 2) and (6, 3, 3).
+ *
+ * Errors: every call returns TADMM_OK (0) or a negative TADMM_E* code and
+ * never aborts; tadmm_last_error() describes the last failure of the calling
+ * thread.  Per-scenario outcomes are reported in a status array.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream); work is
+ * enqueued asynchronously unless stated.
+ */
+#ifndef TADMM_H
+#define TADMM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define TADMM_OK 0
+#define TADMM_EINVAL (-1) /* bad argument or unsupported dimensions */
+#define TADMM_ENOMEM (-2) /* device or host allocation failed */
+#define TADMM_ECUDA (-3)  /* a CUDA runtime call failed */
+#define TADMM_ESTATE (-4) /* call out of order (e.g. backward before solve) */
+
+/* per-scenario status */
+#define TADMM_CONVERGED 0     /* r <= tol and s <= tol */
+#define TADMM_NOT_CONVERGED 1 /* max_iter reached */
+#define TADMM_QP_FAIL 2       /* an agent QP hit the active-set iteration cap */
+#define TADMM_NUMERIC 3       /* non-finite residual or non-positive pivot */
+
+/* start modes of the per-agent QP (the paper's ablation variants, Sec. V.B) */
+#define TADMM_START_COLD 0  /* BaseADMM: u = clip(0), empty working set, every iteration */
+#define TADMM_START_HOT 1   /* HotstartADMM: cold first iteration, then previous (u, W, factors) */
+#define TADMM_START_TURBO 2 /* TurboADMM: clipped affine-LQR warm start, then hot start */
+
+/* execution modes */
+#define TADMM_MODE_BATCHED 0 /* all scenarios, all iterations in one persistent, graph-captured launch */
+#define TADMM_MODE_PLAIN 1   /* one scenario at a time, one launch per phase and a host
+                                read of the residuals after every iteration */
+
+/* A batch of independent scenarios sharing (nx, nu, dp), the dynamics (A, B)
+ * and the input box.  All pointers are HOST pointers, row-major float64, read
+ * only during the call that receives them.  Arrays are packed scenario after
+ * scenario in this order (P_s = N_s (N_s - 1) / 2):
+ *   per agent  (sum N_s rows):          Qd, Qfd, x_init, x_ref [nx]; Rd [nu]
+ *   per pair-step (sum P_s T_s rows):   a [dp], pairs (i<j) lexicographic, then t = 1..T
+ *   per agent-step (sum N_s T_s rows):  w0 [dp], agents, then t = 1..T          */
+typedef struct {
+  int32_t n_scen;
+  int32_t nx, nu, dp;
+  const int32_t* N;      /* [n_scen] agents per scenario, >= 1 */
+  const int32_t* T;      /* [n_scen] horizon per scenario, >= 1 */
+  const double* A;       /* [nx*nx] dynamics x_{t+1} = A x_t + B u_t */
+  const double* B;       /* [nx*nu] */
+  const double* umin;    /* [nu] */
+  const double* umax;    /* [nu] */
+  const double* Qd;      /* diag Q per agent */
+  const double* Rd;      /* diag R per agent */
+  const double* Qfd;     /* diag Q_T per agent */
+  const double* x_init;  /* initial state per agent */
+  const double* x_ref;   /* goal state per agent (constant over t) */
+  const double* a;       /* unit halfspace normal per pair-step */
+  const double* w0;      /* initial consensus position per agent-step (the guess) */
+  const double* d_min;   /* [n_scen] */
+  const double* rho;     /* [n_scen] ADMM penalty */
+} tadmm_batch;
+
+typedef struct {
+  int32_t precision;       /* 64 (float64 arithmetic) or 32 (float32) */
+  int32_t start_mode;      /* TADMM_START_* */
+  int32_t as_max;          /* cap on active-set EQP solves per agent QP; 0 = 10*T*nu + 10 */
+  double eps_rel;          /* multiplier drop tolerance scale; 0 = 1e-12 (fp64) / 1e-5 (fp32) */
+  int32_t mode;            /* TADMM_MODE_* */
+  int32_t threads_per_cta; /* batched mode: threads per scenario CTA; 0 = tuned/default */
+  int32_t ctas_per_sm;     /* batched mode: resident CTAs per SM; 0 = tuned/default */
+} tadmm_options;
+
+typedef struct tadmm_handle tadmm_handle;
+
+/* Validates the batch and deep-copies it into library-owned device memory on
+ * the current CUDA device (Sec. III problem data, already linearized).
+ * `opt` may be NULL (defaults: fp64, turbo, batched).  On success *out owns
+ * all device state until tadmm_destroy.  Synchronous. */
+int tadmm_create(const tadmm_batch* batch, const tadmm_options* opt, tadmm_handle** out);
+
+/* Re-uploads new problem data with the same shapes (N, T per scenario and the
+ * dimensions must match the handle) from host memory, asynchronously on
+ * `stream`; host arrays must stay valid until the stream reaches the copies. */
+int tadmm_update(tadmm_handle* h, const tadmm_batch* batch, void* stream);
+
+/* Runs ADMM from its initial point (consensus copies = w0, duals = 0) until
+ * r <= tol and s <= tol or max_iter iterations, for every scenario.
+ * r = max |p - w|_inf and s = rho * max |w^{k+1} - w^k|_inf over all pairs,
+ * steps, sides and components (Sec. V.A criterion, absolute infinity norms).
+ * Asynchronous on `stream`. */
+int tadmm_solve(tadmm_handle* h, double tol, int32_t max_iter, void* stream);
+
+/* Copies results into caller buffers (host or device pointers; any may be
+ * NULL), converted to float64, then synchronizes `stream`:
+ *   X [sum N][T_s+1][nx], U [sum N][T_s][nu], theta [sum P T] (pair-step order
+ *   of `a`; the halfspace multiplier is rho * theta), W [sum N][T_s][nu] int8
+ *   (0 free, 1 at lower bound, 2 at upper bound), status/iters [n_scen],
+ *   res [n_scen][2] (final r, s). */
+int tadmm_get_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W,
+                       int32_t* status, int32_t* iters, double* res, void* stream);
+
+/* Per-scenario work counters of the last solve (host buffers, synchronous):
+ * eqp [n_scen] active-set EQP solves summed over agents and iterations,
+ * fact [n_scen] Riccati stage factorizations, pairsteps processed. */
+int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pairsteps);
+
+/* Times the candidate launch shapes of the batched persistent kernel on this
+ * batch with `probe_iter` ADMM iterations each and keeps the fastest
+ * (threads_per_cta, ctas_per_sm).  Synchronous.  Writes the choice to
+ * *threads_out / *ctas_out when non-NULL. */
+int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* threads_out,
+                   int32_t* ctas_out);
+
+/* Frees all device memory of the handle (synchronizes the device first). */
+void tadmm_destroy(tadmm_handle* h);
+
+/* Message for the last non-OK return on the calling thread ("" if none). */
+const char* tadmm_last_error(void);
+
+/* Version string of the library build. */
+const char* tadmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TADMM_H */

@@ -1,0 +1,218 @@
+"""Python binding of libtadmm (GB300 batched ADMM for multi-agent trajectory QPs).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels of
+libtadmm.so, reached through its C ABI (include/tadmm.h).  PyTorch supplies the
+current CUDA stream and device tensors for results.  There is no CPU fallback:
+if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtadmm.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4
+CONVERGED, NOT_CONVERGED, QP_FAIL, NUMERIC = 0, 1, 2, 3
+START = {"cold": 0, "hot": 1, "turbo": 2}
+MODE = {"batched": 0, "plain": 1}
+
+_dp = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+
+
+class TadmmBatch(C.Structure):
+    _fields_ = [("n_scen", C.c_int32), ("nx", C.c_int32), ("nu", C.c_int32), ("dp", C.c_int32),
+                ("N", _i32p), ("T", _i32p), ("A", _dp), ("B", _dp), ("umin", _dp), ("umax", _dp),
+                ("Qd", _dp), ("Rd", _dp), ("Qfd", _dp), ("x_init", _dp), ("x_ref", _dp), ("a", _dp),
+                ("w0", _dp), ("d_min", _dp), ("rho", _dp)]
+
+
+class TadmmOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("start_mode", C.c_int32), ("as_max", C.c_int32),
+                ("eps_rel", C.c_double), ("mode", C.c_int32), ("threads_per_cta", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
+
+
+class TadmmError(RuntimeError):
+    pass
+
+
+_LIB = None
+
+
+def lib():
+    """Loads libtadmm.so; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise TadmmError(f"{LIB_PATH} is missing: build it with paper_2602_15838_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        L.tadmm_create.argtypes = [C.POINTER(TadmmBatch), C.POINTER(TadmmOptions), C.POINTER(C.c_void_p)]
+        L.tadmm_update.argtypes = [C.c_void_p, C.POINTER(TadmmBatch), C.c_void_p]
+        L.tadmm_solve.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]
+        L.tadmm_get_solution.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
+        L.tadmm_get_counters.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
+        L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p]
+        L.tadmm_destroy.argtypes = [C.c_void_p]
+        L.tadmm_destroy.restype = None
+        L.tadmm_last_error.restype = C.c_char_p
+        L.tadmm_version.restype = C.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        msg = lib().tadmm_last_error().decode()
+        raise TadmmError(f"{what} failed ({rc}): {msg}")
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class _HostBatch:
+    """Keeps the packed float64 arrays of an instance batch alive for a C call."""
+
+    def __init__(self, batch, pinned: bool = False):
+        fields = dict(A=batch.A, B=batch.B, umin=batch.umin, umax=batch.umax, Qd=batch.Qd, Rd=batch.Rd,
+                      Qfd=batch.Qfd, x_init=batch.x_init, x_ref=batch.x_ref,
+                      a=batch.a if batch.a.size else np.zeros((1, batch.dp)), w0=batch.w0,
+                      d_min=batch.d_min, rho=batch.rho)
+        self.keep = {k: _f64(v) for k, v in fields.items()}
+        if pinned:
+            import torch
+            self.pinned = {k: torch.from_numpy(v).pin_memory() for k, v in self.keep.items()}
+            ptr = {k: C.cast(C.c_void_p(t.data_ptr()), _dp) for k, t in self.pinned.items()}
+        else:
+            ptr = {k: v.ctypes.data_as(_dp) for k, v in self.keep.items()}
+        self.N = np.ascontiguousarray(batch.N, dtype=np.int32)
+        self.T = np.ascontiguousarray(batch.T, dtype=np.int32)
+        self.s = TadmmBatch(int(batch.n_scen), batch.nx, batch.nu, batch.dp, self.N.ctypes.data_as(_i32p),
+                            self.T.ctypes.data_as(_i32p), ptr["A"], ptr["B"], ptr["umin"], ptr["umax"],
+                            ptr["Qd"], ptr["Rd"], ptr["Qfd"], ptr["x_init"], ptr["x_ref"],
+                            None if not batch.a.size else ptr["a"], ptr["w0"], ptr["d_min"], ptr["rho"])
+
+
+class Solver:
+    """A batch of scenarios resident on the current GPU (tadmm_create).
+
+    precision: 64 or 32; start: 'turbo' | 'hot' | 'cold'; mode: 'batched' |
+    'plain'.  Results are float64 regardless of the arithmetic precision.
+    """
+
+    def __init__(self, batch, precision: int = 64, start: str = "turbo", mode: str = "batched",
+                 as_max: int = 0, eps_rel: float = 0.0, threads_per_cta: int = 0, ctas_per_sm: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise TadmmError("no CUDA device: the solver has no CPU path")
+        self.batch = batch
+        self.precision = precision
+        self._hb = _HostBatch(batch)
+        opt = TadmmOptions(precision, START[start], as_max, eps_rel, MODE[mode], threads_per_cta, ctas_per_sm)
+        h = C.c_void_p()
+        _check(lib().tadmm_create(C.byref(self._hb.s), C.byref(opt), C.byref(h)), "tadmm_create")
+        self.h = h
+        self.n_scen = int(batch.n_scen)
+        self.sizes = dict(X=int((batch.N * (batch.T + 1)).sum()) * batch.nx,
+                          U=int((batch.N * batch.T).sum()) * batch.nu,
+                          theta=int((batch.P * batch.T).sum()))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                lib().tadmm_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def close(self):
+        self.__del__()
+
+    def update(self, batch, stream=None, pinned_batch: Optional[_HostBatch] = None):
+        hb = pinned_batch if pinned_batch is not None else _HostBatch(batch)
+        self._upd = hb
+        _check(lib().tadmm_update(self.h, C.byref(hb.s), C.c_void_p(_stream_ptr(stream))), "tadmm_update")
+
+    def solve(self, tol: float = 1e-4, max_iter: int = 500, stream=None):
+        _check(lib().tadmm_solve(self.h, float(tol), int(max_iter), C.c_void_p(_stream_ptr(stream))), "tadmm_solve")
+
+    def autotune(self, probe_iter: int = 20, stream=None):
+        t = C.c_int32(0); c = C.c_int32(0)
+        _check(lib().tadmm_autotune(self.h, int(probe_iter), C.c_void_p(_stream_ptr(stream)), C.byref(t),
+                                    C.byref(c)), "tadmm_autotune")
+        return t.value, c.value
+
+    def solution(self, device: bool = False, stream=None):
+        """Results as numpy arrays (host) or float64 torch tensors on the GPU."""
+        import torch
+        b = self.batch
+        if device:
+            X = torch.empty(self.sizes["X"], dtype=torch.float64, device="cuda")
+            U = torch.empty(self.sizes["U"], dtype=torch.float64, device="cuda")
+            th = torch.empty(max(self.sizes["theta"], 1), dtype=torch.float64, device="cuda")
+            W = torch.empty(self.sizes["U"], dtype=torch.int8, device="cuda")
+            ptr = lambda t: C.c_void_p(t.data_ptr())
+        else:
+            X = np.zeros(self.sizes["X"]); U = np.zeros(self.sizes["U"])
+            th = np.zeros(max(self.sizes["theta"], 1)); W = np.zeros(self.sizes["U"], dtype=np.int8)
+            ptr = lambda a: C.c_void_p(a.ctypes.data)
+        st = np.zeros(self.n_scen, dtype=np.int32)
+        it = np.zeros(self.n_scen, dtype=np.int32)
+        res = np.zeros((self.n_scen, 2))
+        _check(lib().tadmm_get_solution(self.h, ptr(X), ptr(U), ptr(th) if self.sizes["theta"] else None, ptr(W),
+                                        C.c_void_p(st.ctypes.data), C.c_void_p(it.ctypes.data),
+                                        C.c_void_p(res.ctypes.data), C.c_void_p(_stream_ptr(stream))),
+               "tadmm_get_solution")
+        return dict(X=X, U=U, theta=th[:self.sizes["theta"]], W=W, status=st, iters=it, res=res)
+
+    def counters(self):
+        eqp = np.zeros(self.n_scen, dtype=np.int64)
+        fact = np.zeros(self.n_scen, dtype=np.int64)
+        ps = np.zeros(self.n_scen, dtype=np.int64)
+        _check(lib().tadmm_get_counters(self.h, eqp.ctypes.data_as(_i64p), fact.ctypes.data_as(_i64p),
+                                        ps.ctypes.data_as(_i64p)), "tadmm_get_counters")
+        return dict(eqp=eqp, fact=fact, pairsteps=ps)
+
+    def split(self, sol):
+        """Splits packed host results into per-scenario arrays (X [N,T+1,nx], U, theta [P,T], W)."""
+        b = self.batch
+        out = []
+        xo = uo = to = 0
+        for k in range(self.n_scen):
+            N, T, P = int(b.N[k]), int(b.T[k]), int(b.P[k])
+            nX, nU, nT = N * (T + 1) * b.nx, N * T * b.nu, P * T
+            out.append(dict(X=np.asarray(sol["X"][xo:xo + nX]).reshape(N, T + 1, b.nx),
+                            U=np.asarray(sol["U"][uo:uo + nU]).reshape(N, T, b.nu),
+                            W=np.asarray(sol["W"][uo:uo + nU]).reshape(N, T, b.nu),
+                            theta=np.asarray(sol["theta"][to:to + nT]).reshape(P, T),
+                            status=int(sol["status"][k]), iters=int(sol["iters"][k]),
+                            r=float(sol["res"][k, 0]), s=float(sol["res"][k, 1])))
+            xo += nX; uo += nU; to += nT
+        return out
+
+
+def version() -> str:
+    return lib().tadmm_version().decode()
+
+
+def solve(batch, tol: float = 1e-4, max_iter: int = 500, **kw):
+    """One-shot solve: returns (per-scenario results, solver)."""
+    s = Solver(batch, **kw)
+    s.solve(tol, max_iter)
+    return s.split(s.solution()), s

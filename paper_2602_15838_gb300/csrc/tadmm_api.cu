@@ -1,0 +1,416 @@
+// C ABI of libtadmm (declared in include/tadmm.h): validation, device memory,
+// input upload, dispatch to the per-precision implementations, results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "tadmm_impl.h"
+
+namespace tadmm {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TADMM_OK;
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return TADMM_ECUDA;
+}
+
+}  // namespace tadmm
+
+using tadmm::cuda_check;
+using tadmm::set_error;
+
+#define TADMM_DISPATCH(h, CALL)                                                      \
+  do {                                                                               \
+    if ((h)->prec == 64 && (h)->nx == 4) return tadmm::Impl<double, 4, 2, 2>::CALL;  \
+    if ((h)->prec == 64 && (h)->nx == 6) return tadmm::Impl<double, 6, 3, 3>::CALL;  \
+    if ((h)->prec == 32 && (h)->nx == 4) return tadmm::Impl<float, 4, 2, 2>::CALL;   \
+    if ((h)->prec == 32 && (h)->nx == 6) return tadmm::Impl<float, 6, 3, 3>::CALL;   \
+    return set_error(TADMM_EINVAL, "unsupported precision / dimensions");            \
+  } while (0)
+
+static int cache_words(int nx, int nu) { return nx * nx + nu * nx + nu * nu + nu + nx; }
+
+static bool finite_all(const double* p, int64_t n) {
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(p[k])) return false;
+  return true;
+}
+
+// Host-side checks that turn bad inputs into TADMM_EINVAL before any launch.
+static int validate(const tadmm_batch* b, const tadmm_handle* shape) {
+  if (!b) return set_error(TADMM_EINVAL, "batch is NULL");
+  if (b->n_scen < 1) return set_error(TADMM_EINVAL, "n_scen must be >= 1");
+  const bool dims_ok = (b->nx == 4 && b->nu == 2 && b->dp == 2) || (b->nx == 6 && b->nu == 3 && b->dp == 3);
+  if (!dims_ok) return set_error(TADMM_EINVAL, "supported (nx, nu, dp): (4, 2, 2) and (6, 3, 3)");
+  if (!b->N || !b->T || !b->A || !b->B || !b->umin || !b->umax || !b->Qd || !b->Rd || !b->Qfd || !b->x_init ||
+      !b->x_ref || !b->w0 || !b->d_min || !b->rho)
+    return set_error(TADMM_EINVAL, "a required array pointer is NULL");
+  int64_t na = 0, nps = 0, nas = 0;
+  for (int s = 0; s < b->n_scen; ++s) {
+    const int N = b->N[s], T = b->T[s];
+    if (N < 1 || N > 32767) return set_error(TADMM_EINVAL, "scenario " + std::to_string(s) + ": N must be in [1, 32767]");
+    if (T < 1 || T > 100000) return set_error(TADMM_EINVAL, "scenario " + std::to_string(s) + ": T must be in [1, 100000]");
+    if (shape && (shape->N[s] != N || shape->T[s] != T))
+      return set_error(TADMM_EINVAL, "update: N/T differ from the handle");
+    if (!std::isfinite(b->d_min[s])) return set_error(TADMM_EINVAL, "d_min must be finite");
+    if (!(b->rho[s] > 0.0) || !std::isfinite(b->rho[s])) return set_error(TADMM_EINVAL, "rho must be > 0");
+    na += N;
+    nps += (int64_t)N * (N - 1) / 2 * T;
+    nas += (int64_t)N * T;
+  }
+  if (nps > 0 && !b->a) return set_error(TADMM_EINVAL, "a is NULL but the batch has pairs");
+  const int nx = b->nx, nu = b->nu, dp = b->dp;
+  if (!finite_all(b->A, nx * nx) || !finite_all(b->B, nx * nu)) return set_error(TADMM_EINVAL, "A, B must be finite");
+  for (int c = 0; c < nu; ++c)
+    if (!std::isfinite(b->umin[c]) || !std::isfinite(b->umax[c]) || b->umin[c] > b->umax[c])
+      return set_error(TADMM_EINVAL, "need finite umin <= umax");
+  for (int64_t k = 0; k < na * nx; ++k) {
+    if (!(b->Qd[k] >= 0.0) || !std::isfinite(b->Qd[k]) || !(b->Qfd[k] >= 0.0) || !std::isfinite(b->Qfd[k]))
+      return set_error(TADMM_EINVAL, "Q and Qf diagonals must be finite and >= 0");
+  }
+  for (int64_t k = 0; k < na * nu; ++k)
+    if (!(b->Rd[k] > 0.0) || !std::isfinite(b->Rd[k])) return set_error(TADMM_EINVAL, "R diagonal must be finite and > 0");
+  if (!finite_all(b->x_init, na * nx) || !finite_all(b->x_ref, na * nx))
+    return set_error(TADMM_EINVAL, "x_init and x_ref must be finite");
+  if (!finite_all(b->w0, nas * dp)) return set_error(TADMM_EINVAL, "w0 must be finite");
+  if (nps > 0 && !finite_all(b->a, nps * dp)) return set_error(TADMM_EINVAL, "a must be finite");
+  return TADMM_OK;
+}
+
+static void free_all(tadmm_handle* h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  void* ptrs[] = {h->meta,   h->order, h->pairs, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
+                  h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->X,      h->h,
+                  h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
+                  h->res,    h->eqp,   h->fact,  h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
+                  h->ex_buf, h->flag,  h->red2};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+template <typename P>
+static int dmalloc(P** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(TADMM_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+  }
+  return TADMM_OK;
+}
+
+// Copies the caller's float64 arrays into staging and converts them to the
+// internal layouts on `st`.
+static int upload_inputs(tadmm_handle* h, const tadmm_batch* b, cudaStream_t st) {
+  const int nx = h->nx, nu = h->nu, dp = h->dp;
+  const int64_t na = h->tot_agents;
+  for (int s = 0; s < h->n_scen; ++s) {
+    h->meta_h[s].d = b->d_min[s];
+    h->meta_h[s].rho = b->rho[s];
+  }
+  int rc;
+  if ((rc = cuda_check(cudaMemcpyAsync(h->meta, h->meta_h.data(), sizeof(tadmm::ScenMeta) * h->n_scen,
+                                       cudaMemcpyHostToDevice, st), "copy scenario table")))
+    return rc;
+  double* m = h->st_model;
+  cudaMemcpyAsync(m, b->A, sizeof(double) * nx * nx, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(m + nx * nx, b->B, sizeof(double) * nx * nu, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(m + nx * nx + nx * nu, b->umin, sizeof(double) * nu, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(m + nx * nx + nx * nu + nu, b->umax, sizeof(double) * nu, cudaMemcpyHostToDevice, st);
+  double* ag = h->st_agent;
+  cudaMemcpyAsync(ag, b->Qd, sizeof(double) * na * nx, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(ag + na * nx, b->Rd, sizeof(double) * na * nu, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(ag + na * nx + na * nu, b->Qfd, sizeof(double) * na * nx, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(ag + 2 * na * nx + na * nu, b->x_init, sizeof(double) * na * nx, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(ag + 3 * na * nx + na * nu, b->x_ref, sizeof(double) * na * nx, cudaMemcpyHostToDevice, st);
+  if (h->tot_ps > 0) cudaMemcpyAsync(h->st_a, b->a, sizeof(double) * h->tot_ps * dp, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->st_w0, b->w0, sizeof(double) * h->tot_as * dp, cudaMemcpyHostToDevice, st);
+  if ((rc = cuda_check(cudaGetLastError(), "input copies"))) return rc;
+  TADMM_DISPATCH(h, import_inputs(h, st));
+}
+
+extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadmm_handle** out) {
+  if (!out) return set_error(TADMM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(b, nullptr);
+  if (rc) return rc;
+  tadmm_options o{};
+  o.precision = 64;
+  o.start_mode = TADMM_START_TURBO;
+  o.mode = TADMM_MODE_BATCHED;
+  if (opt) o = *opt;
+  if (o.precision != 64 && o.precision != 32) return set_error(TADMM_EINVAL, "precision must be 64 or 32");
+  if (o.start_mode < 0 || o.start_mode > 2) return set_error(TADMM_EINVAL, "start_mode must be 0, 1 or 2");
+  if (o.mode != TADMM_MODE_BATCHED && o.mode != TADMM_MODE_PLAIN) return set_error(TADMM_EINVAL, "bad mode");
+  if (o.as_max < 0 || o.eps_rel < 0 || !std::isfinite(o.eps_rel)) return set_error(TADMM_EINVAL, "bad as_max / eps_rel");
+  if (o.threads_per_cta != 0 && (o.threads_per_cta < 32 || o.threads_per_cta > 256 || o.threads_per_cta % 32))
+    return set_error(TADMM_EINVAL, "threads_per_cta must be 0 or a multiple of 32 in [32, 256]");
+  if (o.ctas_per_sm < 0) return set_error(TADMM_EINVAL, "ctas_per_sm must be >= 0");
+
+  tadmm_handle* h = new tadmm_handle();
+  h->prec = o.precision;
+  h->nx = b->nx;
+  h->nu = b->nu;
+  h->dp = b->dp;
+  h->n_scen = b->n_scen;
+  h->opt = o;
+  h->tpc = o.threads_per_cta;
+  h->cps = o.ctas_per_sm;
+  h->N.assign(b->N, b->N + b->n_scen);
+  h->T.assign(b->T, b->T + b->n_scen);
+  h->meta_h.resize(b->n_scen);
+  std::vector<int32_t> pairs, pair_scen, agent_scen;
+  for (int s = 0; s < b->n_scen; ++s) {
+    tadmm::ScenMeta& m = h->meta_h[s];
+    m.N = h->N[s];
+    m.T = h->T[s];
+    m.P = m.N * (m.N - 1) / 2;
+    m.pad = 0;
+    m.agent_off = h->tot_agents;
+    m.as_off = h->tot_as;
+    m.ps_off = h->tot_ps;
+    m.xs_off = h->tot_xs;
+    m.pair_off = h->tot_pairs;
+    m.d = b->d_min[s];
+    m.rho = b->rho[s];
+    h->tot_agents += m.N;
+    h->tot_as += (int64_t)m.N * m.T;
+    h->tot_ps += (int64_t)m.P * m.T;
+    h->tot_xs += (int64_t)m.N * (m.T + 1);
+    h->tot_pairs += m.P;
+    for (int i = 0; i < m.N; ++i) {
+      agent_scen.push_back(s);
+      for (int j = i + 1; j < m.N; ++j) {
+        pairs.push_back(i | (j << 16));
+        pair_scen.push_back(s);
+      }
+    }
+  }
+  // processing order of the persistent kernel: largest estimated work first
+  std::vector<int32_t> order(b->n_scen);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> work(b->n_scen);
+  for (int s = 0; s < b->n_scen; ++s)
+    work[s] = double(h->meta_h[s].P) * h->meta_h[s].T * 30.0 + double(h->meta_h[s].N) * h->meta_h[s].T * 400.0;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  const size_t fs = h->prec == 64 ? 8 : 4;
+  const int nx = h->nx, nu = h->nu, dp = h->dp;
+  const int64_t na = h->tot_agents;
+  const size_t ex_doubles = (size_t)std::max<int64_t>({h->tot_xs * nx, h->tot_as * nu, h->tot_ps, 1});
+  h->ex_bytes = ex_doubles * sizeof(double);
+  if ((rc = dmalloc(&h->meta, sizeof(tadmm::ScenMeta) * h->n_scen)) || (rc = dmalloc(&h->order, 4 * order.size())) ||
+      (rc = dmalloc(&h->pairs, 4 * pairs.size())) || (rc = dmalloc(&h->pair_scen, 4 * pair_scen.size())) ||
+      (rc = dmalloc(&h->agent_scen, 4 * agent_scen.size())) ||
+      (rc = dmalloc(&h->model, fs * (nx * nx + nx * nu + 2 * nu))) || (rc = dmalloc(&h->Qd, fs * na * nx)) ||
+      (rc = dmalloc(&h->Rd, fs * na * nu)) || (rc = dmalloc(&h->Qfd, fs * na * nx)) ||
+      (rc = dmalloc(&h->x_init, fs * na * nx)) || (rc = dmalloc(&h->x_ref, fs * na * nx)) ||
+      (rc = dmalloc(&h->a, fs * h->tot_ps * dp)) || (rc = dmalloc(&h->w0, fs * h->tot_as * dp)) ||
+      (rc = dmalloc(&h->theta, fs * 2 * h->tot_ps)) || (rc = dmalloc(&h->X, fs * 2 * h->tot_xs * nx)) ||
+      (rc = dmalloc(&h->h, fs * h->tot_as * dp)) || (rc = dmalloc(&h->U, fs * h->tot_as * nu)) ||
+      (rc = dmalloc(&h->Us, fs * h->tot_as * nu)) ||
+      (rc = dmalloc(&h->cache, fs * h->tot_xs * cache_words(nx, nu))) ||
+      (rc = dmalloc(&h->Wm, 2 * h->tot_as)) || (rc = dmalloc(&h->Cm, 2 * h->tot_as)) ||
+      (rc = dmalloc(&h->status, 4 * h->n_scen)) || (rc = dmalloc(&h->iters, 4 * h->n_scen)) ||
+      (rc = dmalloc(&h->cur_lvl, 4 * h->n_scen)) || (rc = dmalloc(&h->res, 16 * h->n_scen)) ||
+      (rc = dmalloc(&h->eqp, 8 * h->n_scen)) || (rc = dmalloc(&h->fact, 8 * h->n_scen)) ||
+      (rc = dmalloc(&h->queue, 16)) ||
+      (rc = dmalloc(&h->st_model, 8 * (nx * nx + nx * nu + 2 * nu))) ||
+      (rc = dmalloc(&h->st_agent, 8 * na * (4 * nx + nu))) || (rc = dmalloc(&h->st_a, 8 * h->tot_ps * dp)) ||
+      (rc = dmalloc(&h->st_w0, 8 * h->tot_as * dp)) || (rc = dmalloc(&h->ex_buf, h->ex_bytes + h->tot_as * nu + 16)) ||
+      (rc = dmalloc(&h->flag, 16)) || (rc = dmalloc(&h->red2, 16))) {
+    free_all(h);
+    return rc;
+  }
+  if (cudaMallocHost(&h->pinned, 64) != cudaSuccess) {
+    free_all(h);
+    return set_error(TADMM_ENOMEM, "cudaMallocHost failed");
+  }
+  if ((rc = cuda_check(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream create"))) {
+    free_all(h);
+    return rc;
+  }
+  cudaStream_t st = h->cap_stream;
+  cudaMemcpyAsync(h->order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, st);
+  if (!pairs.empty()) {
+    cudaMemcpyAsync(h->pairs, pairs.data(), 4 * pairs.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->pair_scen, pair_scen.data(), 4 * pair_scen.size(), cudaMemcpyHostToDevice, st);
+  }
+  cudaMemcpyAsync(h->agent_scen, agent_scen.data(), 4 * agent_scen.size(), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(h->status, 0xFF, 4 * h->n_scen, st);
+  cudaMemsetAsync(h->iters, 0, 4 * h->n_scen, st);
+  cudaMemsetAsync(h->cur_lvl, 0, 4 * h->n_scen, st);
+  cudaMemsetAsync(h->res, 0, 16 * h->n_scen, st);
+  cudaMemsetAsync(h->eqp, 0, 8 * h->n_scen, st);
+  cudaMemsetAsync(h->fact, 0, 8 * h->n_scen, st);
+  if ((rc = upload_inputs(h, b, st)) || (rc = cuda_check(cudaStreamSynchronize(st), "create: upload"))) {
+    free_all(h);
+    return rc;
+  }
+  *out = h;
+  return TADMM_OK;
+}
+
+extern "C" int tadmm_update(tadmm_handle* h, const tadmm_batch* b, void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!b || b->n_scen != h->n_scen || b->nx != h->nx || b->nu != h->nu || b->dp != h->dp)
+    return set_error(TADMM_EINVAL, "update: batch shape differs from the handle");
+  int rc = validate(b, h);
+  if (rc) return rc;
+  return upload_inputs(h, b, (cudaStream_t)stream);
+}
+
+extern "C" int tadmm_solve(tadmm_handle* h, double tol, int32_t max_iter, void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return set_error(TADMM_EINVAL, "tol must be finite and >= 0");
+  if (max_iter < 1) return set_error(TADMM_EINVAL, "max_iter must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if (h->opt.mode == TADMM_MODE_PLAIN) {
+    auto run = [&]() -> int { TADMM_DISPATCH(h, solve_plain(h, tol, max_iter, st)); };
+    rc = run();
+  } else {
+    auto run = [&]() -> int { TADMM_DISPATCH(h, solve_batched(h, tol, max_iter, st)); };
+    rc = run();
+  }
+  if (rc == TADMM_OK) h->solved = 1;
+  return rc;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int tadmm_get_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W, int32_t* status,
+                                  int32_t* iters, double* res, void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!h->solved) return set_error(TADMM_ESTATE, "get_solution before solve");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nx = h->nx, nu = h->nu;
+  auto export_one = [&](double* Xd, double* Ud, double* Td, int8_t* Wd) -> int {
+    TADMM_DISPATCH(h, export_solution(h, Xd, Ud, Td, Wd, st));
+  };
+  int rc;
+  double* ex = h->ex_buf;
+  int8_t* exw = (int8_t*)((char*)h->ex_buf + h->ex_bytes);
+  struct Item { void* dst; size_t bytes; int kind; };
+  const Item items[4] = {{X, sizeof(double) * h->tot_xs * nx, 0},
+                         {U, sizeof(double) * h->tot_as * nu, 1},
+                         {theta, sizeof(double) * h->tot_ps, 2},
+                         {W, (size_t)h->tot_as * nu, 3}};
+  for (const Item& it : items) {
+    if (!it.dst || it.bytes == 0) continue;
+    const bool dev = is_device_ptr(it.dst);
+    void* tgt = dev ? it.dst : (it.kind == 3 ? (void*)exw : (void*)ex);
+    rc = export_one(it.kind == 0 ? (double*)tgt : nullptr, it.kind == 1 ? (double*)tgt : nullptr,
+                    it.kind == 2 ? (double*)tgt : nullptr, it.kind == 3 ? (int8_t*)tgt : nullptr);
+    if (rc) return rc;
+    if (!dev && (rc = cuda_check(cudaMemcpyAsync(it.dst, tgt, it.bytes, cudaMemcpyDefault, st), "copy result")))
+      return rc;
+  }
+  if (status && (rc = cuda_check(cudaMemcpyAsync(status, h->status, 4 * h->n_scen, cudaMemcpyDefault, st), "status")))
+    return rc;
+  if (iters && (rc = cuda_check(cudaMemcpyAsync(iters, h->iters, 4 * h->n_scen, cudaMemcpyDefault, st), "iters")))
+    return rc;
+  if (res && (rc = cuda_check(cudaMemcpyAsync(res, h->res, 16 * h->n_scen, cudaMemcpyDefault, st), "res")))
+    return rc;
+  return cuda_check(cudaStreamSynchronize(st), "get_solution sync");
+}
+
+extern "C" int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pairsteps) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!h->solved) return set_error(TADMM_ESTATE, "get_counters before solve");
+  int rc;
+  if ((rc = cuda_check(cudaDeviceSynchronize(), "counters sync"))) return rc;
+  if (eqp && (rc = cuda_check(cudaMemcpy(eqp, h->eqp, 8 * h->n_scen, cudaMemcpyDeviceToHost), "eqp"))) return rc;
+  if (fact && (rc = cuda_check(cudaMemcpy(fact, h->fact, 8 * h->n_scen, cudaMemcpyDeviceToHost), "fact"))) return rc;
+  if (pairsteps) {
+    std::vector<int32_t> it(h->n_scen);
+    if ((rc = cuda_check(cudaMemcpy(it.data(), h->iters, 4 * h->n_scen, cudaMemcpyDeviceToHost), "iters"))) return rc;
+    for (int s = 0; s < h->n_scen; ++s) pairsteps[s] = (int64_t)it[s] * h->meta_h[s].P * h->meta_h[s].T;
+  }
+  return TADMM_OK;
+}
+
+extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* threads_out,
+                              int32_t* ctas_out) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (probe_iter < 1) return set_error(TADMM_EINVAL, "probe_iter must be >= 1");
+  if (h->opt.mode != TADMM_MODE_BATCHED) return set_error(TADMM_EINVAL, "autotune applies to the batched mode");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_t = 128, best_c = 0;
+  const int cand_t[] = {32, 64, 128, 256};
+  int rc = TADMM_OK;
+  for (int tpc : cand_t) {
+    int maxc = 1;
+    auto occ = [&]() -> int { TADMM_DISPATCH(h, max_ctas_per_sm(tpc)); };
+    maxc = occ();
+    std::vector<int> cands = {maxc};
+    if (maxc >= 2) cands.push_back(maxc / 2);
+    for (int cps : cands) {
+      h->tpc = tpc;
+      h->cps = cps;
+      float ms = 0;
+      for (int rep = 0; rep < 2 && rc == TADMM_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = tadmm_solve(h, 0.0, probe_iter, stream);
+        cudaEventRecord(e1, st);
+        if (rc == TADMM_OK) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
+        if (rc == TADMM_OK) cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (rc) break;
+      if (ms < best) {
+        best = ms;
+        best_t = tpc;
+        best_c = cps;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  h->tpc = best_t;
+  h->cps = best_c;
+  if (threads_out) *threads_out = best_t;
+  if (ctas_out) *ctas_out = best_c;
+  return TADMM_OK;
+}
+
+extern "C" void tadmm_destroy(tadmm_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+}
+
+extern "C" const char* tadmm_last_error(void) { return tadmm::g_err.c_str(); }
+
+extern "C" const char* tadmm_version(void) { return "tadmm 0.1 (sm_103a)"; }

@@ -1,0 +1,793 @@
+// Device code of the batched ADMM hot path (arXiv 2602.15838, Sec. III.B-IV).
+//
+// Three phases per ADMM iteration, written as device functions so that the
+// batched persistent kernel (one CTA per scenario) and the per-phase kernels of
+// the plain mode share them:
+//   x-update  (K-a)  one thread per agent: Riccati-factorized primal active set
+//                    for the box-constrained local QP (Sec. IV.A-C);
+//   pair      (K-b)  one thread per (pair, step): halfspace projection of the
+//                    consensus copies, scaled dual update and residuals;
+//   gather    (K-b') one thread per (agent, step): the aggregate linear term of
+//                    the next x-update.
+//
+// Per-scenario internal layouts (agent index fastest, so that consecutive
+// threads touch consecutive words):
+//   X[lvl]  [T+1][NX][N]   states of the x-update (two levels: p^k and p^{k+1})
+//   h       [T][DP][N]     sum over partners of (w - y), t = 1..T
+//   U, Us   [T][NU][N]     current active-set iterate and EQP solution
+//   Wm, Cm  [T][N]         working-set and cached-factor bit masks
+//   cache   [T+1][E][N]    Riccati cache per stage: P, K, L (Cholesky of the
+//                          reduced S with inverted diagonal), k, p
+//   theta   [lvl][T][P]    projection steps theta^k (multiplier / rho)
+//   a       [T][DP][P]     halfspace normals
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tadmm {
+
+enum { ST_CONVERGED = 0, ST_NOT_CONVERGED = 1, ST_QP_FAIL = 2, ST_NUMERIC = 3 };
+enum { START_COLD = 0, START_HOT = 1, START_TURBO = 2 };
+enum { QP_COLD = 0, QP_LQR = 1, QP_GIVEN = 2 };
+
+struct ScenMeta {
+  int32_t N, T, P, pad;
+  int64_t agent_off;  // first agent of the scenario (sum of N)
+  int64_t as_off;     // agent-step offset (sum of N*T)
+  int64_t ps_off;     // pair-step offset (sum of P*T)
+  int64_t xs_off;     // agent-state offset (sum of N*(T+1))
+  int64_t pair_off;   // pair offset (sum of P)
+  double d, rho;
+};
+
+template <typename F>
+struct Dev {
+  const ScenMeta* meta;
+  const int32_t* order;   // scenario processing order (largest work first)
+  const int32_t* pairs;   // [sum P] packed i | j << 16 (i < j)
+  const F* model;         // A [NX*NX], B [NX*NU], umin [NU], umax [NU]
+  const F* Qd;            // [agents][NX]
+  const F* Rd;            // [agents][NU]
+  const F* Qfd;           // [agents][NX]
+  const F* x_init;        // [agents][NX]
+  const F* x_ref;         // [agents][NX]
+  const F* a;             // per scenario [T][DP][P] at ps_off*DP
+  const F* w0;            // per scenario [T][DP][N] at as_off*DP
+  F* theta;               // level l at l*tot_ps, per scenario [T][P] at ps_off
+  F* X;                   // level l at l*tot_xs*NX, per scenario [T+1][NX][N] at xs_off*NX
+  F* h;                   // per scenario [T][DP][N] at as_off*DP
+  F* U;                   // per scenario [T][NU][N] at as_off*NU
+  F* Us;
+  uint16_t* Wm;           // per scenario [T][N] at as_off
+  uint16_t* Cm;
+  F* cache;               // per scenario [T+1][E][N] at xs_off*E
+  int64_t tot_ps, tot_xs;
+  int32_t n_scen;
+  int32_t* status;        // [n_scen]
+  int32_t* iters;         // [n_scen]
+  int32_t* cur_lvl;       // [n_scen] level holding the final iterate
+  double* res;            // [n_scen][2]
+  unsigned long long* eqp;   // [n_scen]
+  unsigned long long* fact;  // [n_scen]
+  int32_t* queue;            // work-queue head of the persistent kernel
+  double tol;
+  int32_t max_iter;
+  int32_t start_mode;
+  int32_t as_max;            // 0: 10*T*NU + 10
+  double eps_rel;
+};
+
+template <int NX, int NU>
+struct CacheLayout {
+  static constexpr int P = 0;
+  static constexpr int K = NX * NX;
+  static constexpr int L = K + NU * NX;
+  static constexpr int k = L + NU * NU;
+  static constexpr int p = k + NU;
+  static constexpr int E = p + NX;
+};
+
+template <typename F, int NX, int NU>
+struct Model {
+  F A[NX][NX];
+  F B[NX][NU];
+  F umin[NU];
+  F umax[NU];
+};
+
+template <typename F, int NX, int NU>
+__device__ __forceinline__ void load_model(Model<F, NX, NU>& M, const F* src) {
+  for (int e = threadIdx.x; e < NX * NX + NX * NU + 2 * NU; e += blockDim.x) {
+    if (e < NX * NX) (&M.A[0][0])[e] = src[e];
+    else if (e < NX * NX + NX * NU) (&M.B[0][0])[e - NX * NX] = src[e];
+    else if (e < NX * NX + NX * NU + NU) M.umin[e - NX * NX - NX * NU] = src[e];
+    else M.umax[e - NX * NX - NX * NU - NU] = src[e];
+  }
+}
+
+// Non-negative floating values ordered through their bit patterns, so that
+// maxima run on the integer pipe (NaN sorts above +inf and survives a max).
+__device__ __forceinline__ unsigned long long ord_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+__device__ __forceinline__ unsigned long long ord_bits(float v) {
+  return (unsigned long long)(unsigned int)__float_as_int(v);
+}
+__device__ __forceinline__ double from_bits(unsigned long long b, double) {
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ float from_bits(unsigned long long b, float) {
+  return __int_as_float((int)(unsigned int)b);
+}
+__device__ __forceinline__ double fabs_(double v) { return fabs(v); }
+__device__ __forceinline__ float fabs_(float v) { return fabsf(v); }
+__device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+
+__device__ __forceinline__ int pair_index(int N, int i, int j) {  // i < j
+  return i * N - (i * (i + 1)) / 2 + (j - i - 1);
+}
+
+// ---------------------------------------------------------------------------
+// K-a: per-agent x-update
+// ---------------------------------------------------------------------------
+
+// Result of one equality-constrained solve (EQP) with the working set held at
+// its bounds, fused with the ratio test and the multiplier scan.
+template <typename F>
+struct EqpScan {
+  F anum, aden;   // blocking step length as anum / aden (aden > 0); 1/1 = full step
+  int blk;        // index t*NU + c of the blocking input, -1 if none
+  int bside;      // 1 lower, 2 upper
+  F worst;        // most negative multiplier over the working set (0 if none)
+  int widx;       // its index, -1 if none
+  F scale;        // max(1, max |mu| over the working set)
+  int bad;        // non-positive pivot or non-finite value
+};
+
+template <typename F, int NX, int NU, int DP>
+struct AgentCtx {
+  const Model<F, NX, NU>* M;
+  int N, T, i;
+  F* cache;          // scenario base
+  uint16_t* Wm;      // scenario base
+  uint16_t* Cm;
+  F* U;
+  F* Us;
+  F* Xo;             // output level, scenario base
+  const F* h;        // scenario base
+  F qbar[NX], qbarT[NX];   // Hessian diagonals of x_t (t < T) and x_T
+  F qlin[NX], qlinT[NX];   // -2 Q x_ref and -2 Qf x_ref
+  F rbar[NU];
+  F x0[NX];
+  F rho;
+
+  __device__ __forceinline__ F& C(int t, int e) const {
+    return cache[((size_t)t * CacheLayout<NX, NU>::E + e) * N + i];
+  }
+  __device__ __forceinline__ uint16_t& W(int t) const { return Wm[(size_t)t * N + i]; }
+  __device__ __forceinline__ uint16_t& CM(int t) const { return Cm[(size_t)t * N + i]; }
+  __device__ __forceinline__ F& u(int t, int c) const { return U[((size_t)t * NU + c) * N + i]; }
+  __device__ __forceinline__ F& us(int t, int c) const { return Us[((size_t)t * NU + c) * N + i]; }
+  __device__ __forceinline__ F& x(int t, int r) const { return Xo[((size_t)t * NX + r) * N + i]; }
+  // linear term of x_t (t = 1..T): -2 Q_t x_ref - rho C' h_t
+  __device__ __forceinline__ F q(int t, int r) const {
+    F v = (t < T) ? qlin[r] : qlinT[r];
+    if (r < DP) v -= rho * h[((size_t)(t - 1) * DP + r) * N + i];
+    return v;
+  }
+};
+
+// Factorization of one stage with inputs in `mask` fixed (Riccati backward
+// recursion of Sec. IV.B restricted to the free inputs):
+//   S = Rbar + B'P B, M = B'P A (fixed rows/cols replaced by identity / zero),
+//   S = L L', K = -S^{-1} M, P_t = Qbar_t + A'P A + M'K.
+template <typename F, int NX, int NU>
+__device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F (&Pn)[NX][NX],
+                                            uint16_t mask, const F (&rbar)[NU], const F* qdiag,
+                                            F (&Pt)[NX][NX], F (&K)[NU][NX], F (&L)[NU][NU]) {
+  F PA[NX][NX], PB[NX][NU];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) {
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      F acc = 0;
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc = fma(Pn[r][k], Mo.A[k][c], acc);
+      PA[r][c] = acc;
+    }
+#pragma unroll
+    for (int c = 0; c < NU; ++c) {
+      F acc = 0;
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc = fma(Pn[r][k], Mo.B[k][c], acc);
+      PB[r][c] = acc;
+    }
+  }
+  F S[NU][NU], Mm[NU][NX];
+#pragma unroll
+  for (int a = 0; a < NU; ++a) {
+    const bool fa = (mask >> a) & 0x101;
+#pragma unroll
+    for (int b = 0; b < NU; ++b) {
+      const bool fb = (mask >> b) & 0x101;
+      F acc = (a == b) ? rbar[a] : F(0);
+#pragma unroll
+      for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], PB[r][b], acc);
+      S[a][b] = (fa || fb) ? F(a == b ? 1 : 0) : acc;
+    }
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      F acc = 0;
+#pragma unroll
+      for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], PA[r][c], acc);
+      Mm[a][c] = fa ? F(0) : acc;
+    }
+  }
+  // Cholesky S = L L', diagonal stored inverted
+  int bad = 0;
+#pragma unroll
+  for (int j = 0; j < NU; ++j) {
+    F dj = S[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) dj = fma(-L[j][k], L[j][k], dj);
+    if (!(dj > F(0))) bad = 1;
+    const F inv = F(1) / sqrt_(dj);
+    L[j][j] = inv;
+#pragma unroll
+    for (int r = j + 1; r < NU; ++r) {
+      F v = S[r][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v = fma(-L[r][k], L[j][k], v);
+      L[r][j] = v * inv;
+    }
+#pragma unroll
+    for (int r = 0; r < j; ++r) L[r][j] = 0;
+  }
+  // K = -S^{-1} M, column by column
+#pragma unroll
+  for (int c = 0; c < NX; ++c) {
+    F y[NU];
+#pragma unroll
+    for (int r = 0; r < NU; ++r) {
+      F v = -Mm[r][c];
+#pragma unroll
+      for (int k = 0; k < r; ++k) v = fma(-L[r][k], y[k], v);
+      y[r] = v * L[r][r];
+    }
+#pragma unroll
+    for (int r = NU - 1; r >= 0; --r) {
+      F v = y[r];
+#pragma unroll
+      for (int k = r + 1; k < NU; ++k) v = fma(-L[k][r], K[k][c], v);
+      K[r][c] = v * L[r][r];
+    }
+  }
+  if (qdiag != nullptr) {
+    // P_t = Qbar_t + A'(P A) + M'K, upper triangle mirrored
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+#pragma unroll
+      for (int c = r; c < NX; ++c) {
+        F acc = (r == c) ? qdiag[r] : F(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], PA[k][c], acc);
+#pragma unroll
+        for (int k = 0; k < NU; ++k) acc = fma(Mm[k][r], K[k][c], acc);
+        Pt[r][c] = acc;
+        Pt[c][r] = acc;
+      }
+    }
+  }
+  return bad;
+}
+
+// One EQP solve: backward pass (refactor stages t <= dirty, affine pass at
+// every stage), then forward pass (Sec. IV.B forward rollout, costates
+// lambda_{t+1} = P_{t+1} x_{t+1} + p_{t+1}) writing Us and X, with the ratio
+// test of the primal active set against the current iterate U and the scan of
+// the working-set multipliers mu = +-(Rbar u + B' lambda_{t+1}).
+template <typename F, int NX, int NU, int DP>
+__device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, unsigned long long& nfact) {
+  using CL = CacheLayout<NX, NU>;
+  const Model<F, NX, NU>& Mo = *A.M;
+  const int T = A.T;
+  EqpScan<F> o;
+  o.anum = 1; o.aden = 1; o.blk = -1; o.bside = 0; o.worst = 0; o.widx = -1; o.scale = 1; o.bad = 0;
+
+  F Pn[NX][NX], pn[NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) {
+#pragma unroll
+    for (int c = 0; c < NX; ++c) Pn[r][c] = (r == c) ? A.qbarT[r] : F(0);
+    pn[r] = A.q(T, r);
+  }
+  if (dirty >= T - 1) {
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int c = 0; c < NX; ++c) A.C(T, CL::P + r * NX + c) = Pn[r][c];
+  }
+#pragma unroll
+  for (int r = 0; r < NX; ++r) A.C(T, CL::p + r) = pn[r];
+
+  for (int t = T - 1; t >= 0; --t) {
+    const uint16_t mask = A.W(t);
+    F Pt[NX][NX], K[NU][NX], L[NU][NU];
+    if (t <= dirty) {
+      o.bad |= factor_stage<F, NX, NU>(Mo, Pn, mask, A.rbar, t >= 1 ? A.qbar : nullptr, Pt, K, L);
+      ++nfact;
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) A.C(t, CL::K + a * NX + c) = K[a][c];
+#pragma unroll
+        for (int b = 0; b <= a; ++b) A.C(t, CL::L + a * NU + b) = L[a][b];
+      }
+      if (t >= 1) {
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int c = 0; c < NX; ++c) A.C(t, CL::P + r * NX + c) = Pt[r][c];
+      }
+      A.CM(t) = mask;
+    } else {
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) K[a][c] = A.C(t, CL::K + a * NX + c);
+#pragma unroll
+        for (int b = 0; b < NU; ++b) L[a][b] = (b <= a) ? A.C(t, CL::L + a * NU + b) : F(0);
+      }
+      if (t >= 1) {
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int c = 0; c < NX; ++c) Pt[r][c] = A.C(t, CL::P + r * NX + c);
+      }
+    }
+    // affine pass: Pc + p with c = B_fixed u_fixed
+    F Pcp[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) Pcp[r] = pn[r];
+    if (mask) {
+      F cv[NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        F acc = 0;
+#pragma unroll
+        for (int c = 0; c < NU; ++c) {
+          if (mask & (1u << c)) acc = fma(Mo.B[r][c], Mo.umin[c], acc);
+          else if (mask & (0x100u << c)) acc = fma(Mo.B[r][c], Mo.umax[c], acc);
+        }
+        cv[r] = acc;
+      }
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        F acc = Pcp[r];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) acc = fma(Pn[r][c], cv[c], acc);
+        Pcp[r] = acc;
+      }
+    }
+    F sv[NU], kk[NU];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      F acc = 0;
+#pragma unroll
+      for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], Pcp[r], acc);
+      sv[a] = (mask & (0x101u << a)) ? F(0) : acc;
+    }
+    {
+      F y[NU];
+#pragma unroll
+      for (int r = 0; r < NU; ++r) {
+        F v = -sv[r];
+#pragma unroll
+        for (int k = 0; k < r; ++k) v = fma(-L[r][k], y[k], v);
+        y[r] = v * L[r][r];
+      }
+#pragma unroll
+      for (int r = NU - 1; r >= 0; --r) {
+        F v = y[r];
+#pragma unroll
+        for (int k = r + 1; k < NU; ++k) v = fma(-L[k][r], kk[k], v);
+        kk[r] = v * L[r][r];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) A.C(t, CL::k + a) = kk[a];
+    if (t >= 1) {
+      F pt[NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        F acc = A.q(t, r);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], Pcp[k], acc);
+#pragma unroll
+        for (int k = 0; k < NU; ++k) acc = fma(K[k][r], sv[k], acc);
+        pt[r] = acc;
+      }
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        A.C(t, CL::p + r) = pt[r];
+        pn[r] = pt[r];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) Pn[r][c] = Pt[r][c];
+      }
+    }
+  }
+
+  // forward rollout
+  F xv[NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) {
+    xv[r] = A.x0[r];
+    A.x(0, r) = xv[r];
+  }
+  for (int t = 0; t < T; ++t) {
+    const uint16_t mask = A.W(t);
+    F uv[NU];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      if (mask & (1u << a)) uv[a] = Mo.umin[a];
+      else if (mask & (0x100u << a)) uv[a] = Mo.umax[a];
+      else {
+        F acc = A.C(t, CL::k + a);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) acc = fma(A.C(t, CL::K + a * NX + c), xv[c], acc);
+        uv[a] = acc;
+      }
+    }
+    F xn[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      F acc = 0;
+#pragma unroll
+      for (int c = 0; c < NX; ++c) acc = fma(Mo.A[r][c], xv[c], acc);
+#pragma unroll
+      for (int c = 0; c < NU; ++c) acc = fma(Mo.B[r][c], uv[c], acc);
+      xn[r] = acc;
+    }
+    F lam[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      F acc = A.C(t + 1, CL::p + r);
+#pragma unroll
+      for (int c = 0; c < NX; ++c) acc = fma(A.C(t + 1, CL::P + r * NX + c), xn[c], acc);
+      lam[r] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      const int idx = t * NU + a;
+      if (mask & (0x101u << a)) {
+        F g = A.rbar[a] * uv[a];
+#pragma unroll
+        for (int r = 0; r < NX; ++r) g = fma(Mo.B[r][a], lam[r], g);
+        const F mu = (mask & (1u << a)) ? g : -g;
+        const F am = fabs_(mu);
+        if (am > o.scale) o.scale = am;
+        if (mu < o.worst) { o.worst = mu; o.widx = idx; }
+        if (!(am == am)) o.bad = 1;
+      } else {
+        // ratio test: step p = us - u, blocking ratio num / den with den > 0
+        const F cu = A.u(t, a);
+        const F p = uv[a] - cu;
+        F num = 0, den = 0;
+        int side = 0;
+        if (p < F(0)) { num = cu - Mo.umin[a]; den = -p; side = 1; }
+        else if (p > F(0)) { num = Mo.umax[a] - cu; den = p; side = 2; }
+        if (side) {
+          if (num < F(0)) num = 0;
+          // num/den < anum/aden  <=>  num*aden < anum*den (both denominators > 0)
+          if (num * o.aden < o.anum * den) { o.anum = num; o.aden = den; o.blk = idx; o.bside = side; }
+        }
+      }
+      A.us(t, a) = uv[a];
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      A.x(t + 1, r) = xn[r];
+      xv[r] = xn[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+    if (!(xv[r] == xv[r]) || fabs_(xv[r]) > F(1e30)) o.bad = 1;
+  return o;
+}
+
+// Box-constrained local QP of agent i (Sec. IV.A) by the primal active-set
+// method (Nocedal & Wright Alg. 16.3) over Riccati EQP solves.
+// start_kind: QP_COLD (u = clip(0), W empty), QP_LQR (clipped affine-LQR warm
+// start, Sec. IV.B-C) or QP_GIVEN (hot start from the stored u, W and factors).
+// Returns ST_CONVERGED, ST_QP_FAIL or ST_NUMERIC.
+template <typename F, int NX, int NU, int DP>
+__device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, int as_max, F eps_rel,
+                             unsigned long long& neqp, unsigned long long& nfact) {
+  const int T = A.T;
+  const Model<F, NX, NU>& Mo = *A.M;
+  if (start_kind == QP_COLD) {
+    for (int t = 0; t < T; ++t) {
+      A.W(t) = 0;
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        F z = 0;
+        if (z < Mo.umin[a]) z = Mo.umin[a];
+        if (z > Mo.umax[a]) z = Mo.umax[a];
+        A.u(t, a) = z;
+      }
+    }
+  } else if (start_kind == QP_LQR) {
+    for (int t = 0; t < T; ++t) A.W(t) = 0;
+  }
+  // stages whose cached factors do not match the working set
+  int dirty = -1;
+  for (int t = 0; t < T; ++t)
+    if (A.CM(t) != A.W(t)) dirty = t;
+
+  if (start_kind == QP_LQR) {
+    EqpScan<F> o = eqp_solve<F, NX, NU, DP>(A, dirty, nfact);
+    if (o.bad) return ST_NUMERIC;
+    dirty = -1;
+    bool clipped = false;
+    for (int t = 0; t < T; ++t) {
+      uint16_t m = 0;
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        F v = A.us(t, a);
+        if (v < Mo.umin[a]) { v = Mo.umin[a]; m |= (uint16_t)(1u << a); }
+        else if (v > Mo.umax[a]) { v = Mo.umax[a]; m |= (uint16_t)(0x100u << a); }
+        A.u(t, a) = v;
+      }
+      if (m) { A.W(t) = m; clipped = true; dirty = t; }
+    }
+    if (!clipped) return ST_CONVERGED;  // the LQR solution is the QP solution
+  }
+
+  bool need_solve = true;
+  EqpScan<F> o;
+  for (;;) {
+    if (need_solve) {
+      if (as_max <= 0) return ST_QP_FAIL;
+      --as_max;
+      ++neqp;
+      o = eqp_solve<F, NX, NU, DP>(A, dirty, nfact);
+      if (o.bad) return ST_NUMERIC;
+      dirty = -1;
+      if (o.blk >= 0) {
+        const F alpha = o.anum / o.aden;
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+          for (int a = 0; a < NU; ++a) {
+            const F cu = A.u(t, a);
+            A.u(t, a) = fma(alpha, A.us(t, a) - cu, cu);
+          }
+        const int bt = o.blk / NU, ba = o.blk - bt * NU;
+        A.u(bt, ba) = (o.bside == 1) ? Mo.umin[ba] : Mo.umax[ba];
+        A.W(bt) = (uint16_t)(A.W(bt) | (o.bside == 1 ? (1u << ba) : (0x100u << ba)));
+        dirty = bt;
+        continue;
+      }
+      for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int a = 0; a < NU; ++a) A.u(t, a) = A.us(t, a);
+      need_solve = false;
+    }
+    if (o.widx >= 0 && o.worst < -eps_rel * o.scale) {
+      const int bt = o.widx / NU, ba = o.widx - bt * NU;
+      A.W(bt) = (uint16_t)(A.W(bt) & ~(0x101u << ba));
+      dirty = bt;
+      need_solve = true;
+      continue;
+    }
+    return ST_CONVERGED;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Scenario-level phases
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
+
+// State of one scenario at its first iteration: consensus copies w = w0 (the
+// guess positions, stored as the previous positions p^0), duals zero
+// (theta^0 = theta^{-1} = 0), aggregate h = n_c w0, caches invalid.
+template <typename F, int NX, int NU, int DP>
+__device__ void init_phase(const Dev<F>& D, const ScenMeta& s, int64_t t0, int64_t stride) {
+  const int N = s.N, T = s.T, P = s.P;
+  F* X0 = D.X + s.xs_off * NX;
+  F* h = D.h + s.as_off * DP;
+  const F* w0 = D.w0 + s.as_off * DP;
+  F* U = D.U + s.as_off * NU;
+  const F nc = F(N - 1);
+  for (int64_t idx = t0; idx < (int64_t)N * T; idx += stride) {
+    const int tm1 = (int)(idx / N), i = (int)(idx - (int64_t)tm1 * N);
+#pragma unroll
+    for (int c = 0; c < DP; ++c) {
+      const F w = w0[((size_t)tm1 * DP + c) * N + i];
+      X0[((size_t)(tm1 + 1) * NX + c) * N + i] = w;
+      h[((size_t)tm1 * DP + c) * N + i] = nc * w;
+    }
+#pragma unroll
+    for (int c = 0; c < NU; ++c) U[((size_t)tm1 * NU + c) * N + i] = 0;
+    D.Wm[s.as_off + idx] = 0;
+    D.Cm[s.as_off + idx] = 0xFFFF;
+  }
+  F* th0 = D.theta + s.ps_off;
+  F* th1 = D.theta + D.tot_ps + s.ps_off;
+  for (int64_t q = t0; q < (int64_t)P * T; q += stride) {
+    th0[q] = 0;
+    th1[q] = 0;
+  }
+}
+
+template <typename F, int NX, int NU, int DP>
+__device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, const Model<F, NX, NU>& M,
+                                                              const ScenMeta& s, int i, int lvl_out) {
+  AgentCtx<F, NX, NU, DP> A;
+  A.M = &M;
+  A.N = s.N;
+  A.T = s.T;
+  A.i = i;
+  A.cache = D.cache + s.xs_off * CacheLayout<NX, NU>::E;
+  A.Wm = D.Wm + s.as_off;
+  A.Cm = D.Cm + s.as_off;
+  A.U = D.U + s.as_off * NU;
+  A.Us = D.Us + s.as_off * NU;
+  A.Xo = D.X + (size_t)lvl_out * D.tot_xs * NX + s.xs_off * NX;
+  A.h = D.h + s.as_off * DP;
+  A.rho = F(s.rho);
+  const int64_t ag = s.agent_off + i;
+  const F rnc = F(s.rho) * F(s.N - 1);
+#pragma unroll
+  for (int r = 0; r < NX; ++r) {
+    const F q = D.Qd[ag * NX + r], qf = D.Qfd[ag * NX + r], xr = D.x_ref[ag * NX + r];
+    A.qbar[r] = F(2) * q + (r < DP ? rnc : F(0));
+    A.qbarT[r] = F(2) * qf + (r < DP ? rnc : F(0));
+    A.qlin[r] = (F(-2) * q) * xr;
+    A.qlinT[r] = (F(-2) * qf) * xr;
+    A.x0[r] = D.x_init[ag * NX + r];
+  }
+#pragma unroll
+  for (int c = 0; c < NU; ++c) A.rbar[c] = F(2) * D.Rd[ag * NU + c];
+  return A;
+}
+
+template <typename F>
+__device__ __forceinline__ int start_kind_of(const Dev<F>& D, int k) {
+  if (D.start_mode == START_COLD) return QP_COLD;
+  if (k == 0) return D.start_mode == START_TURBO ? QP_LQR : QP_COLD;
+  return QP_GIVEN;
+}
+
+template <typename F, int NX, int NU, int DP>
+__device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, int k,
+                             int lvl_out, int i0, int stride, unsigned long long& neqp,
+                             unsigned long long& nfact) {
+  const int kind = start_kind_of(D, k);
+  const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
+  const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
+  int st = ST_CONVERGED;
+  for (int i = i0; i < s.N; i += stride) {
+    AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, i, lvl_out);
+    const int r = xupdate_agent<F, NX, NU, DP>(A, kind, as_max, eps, neqp, nfact);
+    if (r > st) st = r;
+  }
+  return st;
+}
+
+// Consensus projection + scaled dual update in theta form, residual maxima.
+// theta^{k+1} = max(0, theta^k + (d - a'(p_i - p_j)) / 2); the dual copies are
+// y_i = -theta a, y_j = +theta a; r = |theta^{k+1} - theta^k| max|a_c|;
+// s/rho = |Delta p +- (theta^{k+1} - 2 theta^k + theta^{k-1}) a|.
+// theta^{k-1} is read from the other level and overwritten with theta^{k+1}.
+template <typename F, int NX, int NU, int DP>
+__device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int cur, int64_t q0, int64_t stride,
+                           unsigned long long& rb, unsigned long long& sb) {
+  const int N = s.N, P = s.P;
+  const int64_t PT = (int64_t)P * s.T;
+  const F* Xn = D.X + (size_t)(cur ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+  const F* Xc = D.X + (size_t)cur * D.tot_xs * NX + s.xs_off * NX;
+  const F* thc = D.theta + (size_t)cur * D.tot_ps + s.ps_off;
+  F* tho = D.theta + (size_t)(cur ^ 1) * D.tot_ps + s.ps_off;
+  const F* a = D.a + s.ps_off * DP;
+  const int32_t* pr = D.pairs + s.pair_off;
+  const F d = F(s.d);
+  for (int64_t q = q0; q < PT; q += stride) {
+    const int tm1 = (int)(q / P);
+    const int pair = (int)(q - (int64_t)tm1 * P);
+    const int pk = pr[pair];
+    const int i = pk & 0xFFFF, j = pk >> 16;
+    F av[DP], dpi[DP], dpj[DP];
+    F sdot = 0, amax = 0;
+#pragma unroll
+    for (int c = 0; c < DP; ++c) {
+      av[c] = a[((size_t)tm1 * DP + c) * P + pair];
+      const size_t oi = ((size_t)(tm1 + 1) * NX + c) * N + i;
+      const size_t oj = ((size_t)(tm1 + 1) * NX + c) * N + j;
+      const F pi = Xn[oi], pj = Xn[oj];
+      dpi[c] = pi - Xc[oi];
+      dpj[c] = pj - Xc[oj];
+      sdot = fma(av[c], pi - pj, sdot);
+      const F aa = fabs_(av[c]);
+      amax = aa > amax ? aa : amax;
+    }
+    const F th = thc[q], thp = tho[q];
+    F tn = fma(d - sdot, F(0.5), th);
+    if (tn < F(0)) tn = 0;
+    const F dth = tn - th;
+    const F e2 = dth - (th - thp);
+    unsigned long long v = ord_bits(fabs_(dth) * amax);
+    rb = v > rb ? v : rb;
+#pragma unroll
+    for (int c = 0; c < DP; ++c) {
+      v = ord_bits(fabs_(fma(e2, av[c], dpi[c])));
+      sb = v > sb ? v : sb;
+      v = ord_bits(fabs_(fma(-e2, av[c], dpj[c])));
+      sb = v > sb ? v : sb;
+    }
+    tho[q] = tn;
+  }
+}
+
+// Aggregate linear term of the next x-update for agent i at step t:
+// h_it = sum_{j != i} (w_i - y_i) = n_c p_it + sum_j sigma_ij (2 theta^{k+1} - theta^k) a_ijt,
+// sigma = +1 when i is the first agent of the pair, -1 otherwise.
+template <typename F, int NX, int NU, int DP>
+__device__ void gather_phase(const Dev<F>& D, const ScenMeta& s, int lvl_new, int64_t t0, int64_t stride) {
+  const int N = s.N, P = s.P;
+  const F* Xn = D.X + (size_t)lvl_new * D.tot_xs * NX + s.xs_off * NX;
+  const F* thn = D.theta + (size_t)lvl_new * D.tot_ps + s.ps_off;
+  const F* tho = D.theta + (size_t)(lvl_new ^ 1) * D.tot_ps + s.ps_off;
+  const F* a = D.a + s.ps_off * DP;
+  F* h = D.h + s.as_off * DP;
+  const F nc = F(N - 1);
+  for (int64_t idx = t0; idx < (int64_t)N * s.T; idx += stride) {
+    const int tm1 = (int)(idx / N), i = (int)(idx - (int64_t)tm1 * N);
+    F acc[DP];
+#pragma unroll
+    for (int c = 0; c < DP; ++c) acc[c] = nc * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
+    const size_t qb = (size_t)tm1 * P;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      const bool first = i < j;
+      const int pair = first ? pair_index(N, i, j) : pair_index(N, j, i);
+      F e = fma(F(2), thn[qb + pair], -tho[qb + pair]);
+      if (!first) e = -e;
+#pragma unroll
+      for (int c = 0; c < DP; ++c) acc[c] = fma(e, a[((size_t)tm1 * DP + c) * P + pair], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+  }
+}
+
+// Maximum of two non-negative bit-ordered values over the CTA; every thread
+// receives the result.  Contains two barriers.
+__device__ __forceinline__ void block_max2(unsigned long long& a, unsigned long long& b,
+                                           unsigned long long (*red)[32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, o);
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+    a = oa > a ? oa : a;
+    b = ob > b ? ob : b;
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][w] = a; red[1][w] = b; }
+  __syncthreads();
+  a = 0;
+  b = 0;
+  for (int k = 0; k < nw; ++k) {
+    a = red[0][k] > a ? red[0][k] : a;
+    b = red[1][k] > b ? red[1][k] : b;
+  }
+  __syncthreads();
+}
+
+}  // namespace tadmm

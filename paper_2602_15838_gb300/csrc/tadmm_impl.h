@@ -1,0 +1,90 @@
+// Host-side state of a tadmm handle and the per-precision / per-dimension
+// implementation entry points (explicitly instantiated in tadmm_f64.cu and
+// tadmm_f32.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tadmm.h"
+#include "tadmm_device.cuh"
+
+struct tadmm_handle {
+  int prec = 64, nx = 0, nu = 0, dp = 0, n_scen = 0;
+  int64_t tot_agents = 0, tot_as = 0, tot_ps = 0, tot_xs = 0, tot_pairs = 0;
+  tadmm_options opt{};
+  std::vector<int32_t> N, T;
+  std::vector<tadmm::ScenMeta> meta_h;
+  int device = 0, sm_count = 0;
+
+  // device state
+  tadmm::ScenMeta* meta = nullptr;
+  int32_t* order = nullptr;
+  int32_t* pairs = nullptr;
+  int32_t* pair_scen = nullptr;
+  int32_t* agent_scen = nullptr;
+  void* model = nullptr;
+  void* Qd = nullptr;
+  void* Rd = nullptr;
+  void* Qfd = nullptr;
+  void* x_init = nullptr;
+  void* x_ref = nullptr;
+  void* a = nullptr;
+  void* w0 = nullptr;
+  void* theta = nullptr;
+  void* X = nullptr;
+  void* h = nullptr;
+  void* U = nullptr;
+  void* Us = nullptr;
+  void* cache = nullptr;
+  uint16_t* Wm = nullptr;
+  uint16_t* Cm = nullptr;
+  int32_t* status = nullptr;
+  int32_t* iters = nullptr;
+  int32_t* cur_lvl = nullptr;
+  double* res = nullptr;
+  unsigned long long* eqp = nullptr;
+  unsigned long long* fact = nullptr;
+  int32_t* queue = nullptr;
+
+  // float64 staging in the caller's layouts (imports and exports)
+  double* st_model = nullptr;   // A, B, umin, umax
+  double* st_agent = nullptr;   // Qd, Rd, Qfd, x_init, x_ref (5 blocks)
+  double* st_a = nullptr;       // [tot_ps][dp]
+  double* st_w0 = nullptr;      // [tot_as][dp]
+  double* ex_buf = nullptr;     // export scratch
+  size_t ex_bytes = 0;
+
+  // plain mode
+  int32_t* flag = nullptr;               // device: agent QP failure code
+  unsigned long long* red2 = nullptr;    // device: residual maxima bits
+  void* pinned = nullptr;                // host pinned readback buffer
+
+  // batched mode launch shape and captured graph
+  int tpc = 0, cps = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double g_tol = -1.0;
+  int g_iter = -1, g_tpc = -1, g_cps = -1;
+  int solved = 0;
+  int64_t launches = 0;   // kernel launches enqueued by the last solve
+};
+
+namespace tadmm {
+
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+
+template <typename F, int NX, int NU, int DP>
+struct Impl {
+  static int import_inputs(tadmm_handle* h, cudaStream_t st);
+  static int solve_batched(tadmm_handle* h, double tol, int max_iter, cudaStream_t st);
+  static int solve_plain(tadmm_handle* h, double tol, int max_iter, cudaStream_t st);
+  static int export_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W,
+                             cudaStream_t st);
+  static int max_ctas_per_sm(int tpc);
+};
+
+}  // namespace tadmm

@@ -1,0 +1,392 @@
+// Kernels and host launchers of the batched ADMM path, templated on the
+// arithmetic type F and the dimensions (NX, NU, DP).
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+
+#include "tadmm_impl.h"
+
+namespace tadmm {
+
+// ---------------------------------------------------------------------------
+// Batched persistent kernel: each CTA repeatedly takes the next scenario from
+// a work queue (largest estimated work first) and runs every ADMM iteration of
+// it on-chip, phases separated by CTA barriers.
+// ---------------------------------------------------------------------------
+template <typename F, int NX, int NU, int DP>
+__global__ void __launch_bounds__(256) k_batched(Dev<F> D) {
+  __shared__ Model<F, NX, NU> M;
+  __shared__ unsigned long long red[2][32];
+  __shared__ unsigned long long cnt[2];
+  __shared__ int s_q;
+  __shared__ int s_flag;
+  load_model<F, NX, NU>(M, D.model);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      s_q = atomicAdd(D.queue, 1);
+      s_flag = 0;
+      cnt[0] = 0;
+      cnt[1] = 0;
+    }
+    __syncthreads();
+    const int qi = s_q;
+    if (qi >= D.n_scen) return;
+    const int sc = D.order[qi];
+    const ScenMeta s = D.meta[sc];
+    init_phase<F, NX, NU, DP>(D, s, tid, nt);
+    __syncthreads();
+    int cur = 0, status = ST_NOT_CONVERGED, iters = 0;
+    F r = F(0), sres = F(0);
+    unsigned long long neqp = 0, nfact = 0;
+    for (int k = 0; k < D.max_iter; ++k) {
+      const int st = xupdate_phase<F, NX, NU, DP>(D, M, s, k, cur ^ 1, tid, nt, neqp, nfact);
+      if (st) atomicMax(&s_flag, st);
+      __syncthreads();
+      iters = k + 1;
+      const int flag = s_flag;
+      if (flag) { status = flag; break; }
+      unsigned long long rb = 0, sb = 0;
+      pair_phase<F, NX, NU, DP>(D, s, cur, tid, nt, rb, sb);
+      block_max2(rb, sb, red);
+      r = from_bits(rb, F(0));
+      sres = F(s.rho) * from_bits(sb, F(0));
+      if (!finite_(r) || !finite_(sres)) { status = ST_NUMERIC; cur ^= 1; break; }
+      if (r <= F(D.tol) && sres <= F(D.tol)) { status = ST_CONVERGED; cur ^= 1; break; }
+      gather_phase<F, NX, NU, DP>(D, s, cur ^ 1, tid, nt);
+      __syncthreads();
+      cur ^= 1;
+    }
+    if (neqp) atomicAdd(&cnt[0], neqp);
+    if (nfact) atomicAdd(&cnt[1], nfact);
+    __syncthreads();
+    if (tid == 0) {
+      D.status[sc] = status;
+      D.iters[sc] = iters;
+      D.cur_lvl[sc] = cur;
+      D.res[2 * sc] = double(r);
+      D.res[2 * sc + 1] = double(sres);
+      D.eqp[sc] = cnt[0];
+      D.fact[sc] = cnt[1];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plain mode: one scenario, one launch per phase, host reads the residuals.
+// ---------------------------------------------------------------------------
+template <typename F, int NX, int NU, int DP>
+__global__ void k_init(Dev<F> D, int sc) {
+  const ScenMeta s = D.meta[sc];
+  init_phase<F, NX, NU, DP>(D, s, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                            (int64_t)gridDim.x * blockDim.x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.eqp[sc] = 0;
+    D.fact[sc] = 0;
+  }
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void __launch_bounds__(128) k_xupdate(Dev<F> D, int sc, int k, int lvl_out, int32_t* flag) {
+  __shared__ Model<F, NX, NU> M;
+  load_model<F, NX, NU>(M, D.model);
+  __syncthreads();
+  const ScenMeta s = D.meta[sc];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.N) return;
+  unsigned long long neqp = 0, nfact = 0;
+  const int st = xupdate_phase<F, NX, NU, DP>(D, M, s, k, lvl_out, i, s.N, neqp, nfact);
+  if (st) atomicMax(flag, st);
+  if (neqp) atomicAdd(&D.eqp[sc], neqp);
+  if (nfact) atomicAdd(&D.fact[sc], nfact);
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void __launch_bounds__(256) k_pair(Dev<F> D, int sc, int cur, unsigned long long* red2) {
+  __shared__ unsigned long long red[2][32];
+  const ScenMeta s = D.meta[sc];
+  unsigned long long rb = 0, sb = 0;
+  pair_phase<F, NX, NU, DP>(D, s, cur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                            (int64_t)gridDim.x * blockDim.x, rb, sb);
+  block_max2(rb, sb, red);
+  if (threadIdx.x == 0) {
+    if (rb) atomicMax(&red2[0], rb);
+    if (sb) atomicMax(&red2[1], sb);
+  }
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void k_gather(Dev<F> D, int sc, int lvl_new) {
+  const ScenMeta s = D.meta[sc];
+  gather_phase<F, NX, NU, DP>(D, s, lvl_new, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                              (int64_t)gridDim.x * blockDim.x);
+}
+
+template <typename F>
+__global__ void k_finish(Dev<F> D, int sc, int status, int iters, int cur, double r, double sres) {
+  D.status[sc] = status;
+  D.iters[sc] = iters;
+  D.cur_lvl[sc] = cur;
+  D.res[2 * sc] = r;
+  D.res[2 * sc + 1] = sres;
+}
+
+// ---------------------------------------------------------------------------
+// Import (caller layouts, float64) and export kernels
+// ---------------------------------------------------------------------------
+template <typename F>
+__global__ void k_convert(const double* __restrict__ src, F* __restrict__ dst, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = F(src[k]);
+}
+
+// a: caller [pair-step][dp] (pair-major, then t) -> internal [T][DP][P]
+template <typename F, int DP>
+__global__ void k_import_a(const ScenMeta* __restrict__ meta, const int32_t* __restrict__ pair_scen,
+                           const double* __restrict__ src, F* __restrict__ dst, int64_t tot_pairs) {
+  for (int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gp < tot_pairs;
+       gp += (int64_t)gridDim.x * blockDim.x) {
+    const ScenMeta s = meta[pair_scen[gp]];
+    const int lp = (int)(gp - s.pair_off);
+    for (int t = 0; t < s.T; ++t)
+#pragma unroll
+      for (int c = 0; c < DP; ++c)
+        dst[s.ps_off * DP + ((size_t)t * DP + c) * s.P + lp] = F(src[(s.ps_off + (int64_t)lp * s.T + t) * DP + c]);
+  }
+}
+
+// w0: caller [agent-step][dp] (agent-major, then t) -> internal [T][DP][N]
+template <typename F, int DP>
+__global__ void k_import_w0(const ScenMeta* __restrict__ meta, const int32_t* __restrict__ agent_scen,
+                            const double* __restrict__ src, F* __restrict__ dst, int64_t tot_agents) {
+  for (int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ga < tot_agents;
+       ga += (int64_t)gridDim.x * blockDim.x) {
+    const ScenMeta s = meta[agent_scen[ga]];
+    const int i = (int)(ga - s.agent_off);
+    for (int t = 0; t < s.T; ++t)
+#pragma unroll
+      for (int c = 0; c < DP; ++c)
+        dst[s.as_off * DP + ((size_t)t * DP + c) * s.N + i] = F(src[(s.as_off + (int64_t)i * s.T + t) * DP + c]);
+  }
+}
+
+template <typename F, int NX, int NU>
+__global__ void k_export_agents(Dev<F> D, const int32_t* __restrict__ agent_scen, int64_t tot_agents,
+                                double* X, double* U, int8_t* W) {
+  for (int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ga < tot_agents;
+       ga += (int64_t)gridDim.x * blockDim.x) {
+    const int sc = agent_scen[ga];
+    const ScenMeta s = D.meta[sc];
+    const int i = (int)(ga - s.agent_off), N = s.N, T = s.T;
+    const F* Xl = D.X + (size_t)D.cur_lvl[sc] * D.tot_xs * NX + s.xs_off * NX;
+    if (X)
+      for (int t = 0; t <= T; ++t)
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+          X[(s.xs_off + (int64_t)i * (T + 1) + t) * NX + r] = double(Xl[((size_t)t * NX + r) * N + i]);
+    for (int t = 0; t < T; ++t) {
+      const uint16_t m = D.Wm[s.as_off + (size_t)t * N + i];
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        const int64_t o = (s.as_off + (int64_t)i * T + t) * NU + c;
+        if (U) U[o] = double(D.U[s.as_off * NU + ((size_t)t * NU + c) * N + i]);
+        if (W) W[o] = (m & (1u << c)) ? 1 : ((m & (0x100u << c)) ? 2 : 0);
+      }
+    }
+  }
+}
+
+template <typename F>
+__global__ void k_export_theta(Dev<F> D, const int32_t* __restrict__ pair_scen, int64_t tot_pairs, double* th) {
+  for (int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gp < tot_pairs;
+       gp += (int64_t)gridDim.x * blockDim.x) {
+    const int sc = pair_scen[gp];
+    const ScenMeta s = D.meta[sc];
+    const int lp = (int)(gp - s.pair_off);
+    const F* tl = D.theta + (size_t)D.cur_lvl[sc] * D.tot_ps + s.ps_off;
+    for (int t = 0; t < s.T; ++t) th[s.ps_off + (int64_t)lp * s.T + t] = double(tl[(size_t)t * s.P + lp]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <typename F>
+static Dev<F> make_dev(tadmm_handle* h) {
+  Dev<F> D;
+  std::memset(&D, 0, sizeof(D));
+  D.meta = h->meta;
+  D.order = h->order;
+  D.pairs = h->pairs;
+  D.model = (const F*)h->model;
+  D.Qd = (const F*)h->Qd;
+  D.Rd = (const F*)h->Rd;
+  D.Qfd = (const F*)h->Qfd;
+  D.x_init = (const F*)h->x_init;
+  D.x_ref = (const F*)h->x_ref;
+  D.a = (const F*)h->a;
+  D.w0 = (const F*)h->w0;
+  D.theta = (F*)h->theta;
+  D.X = (F*)h->X;
+  D.h = (F*)h->h;
+  D.U = (F*)h->U;
+  D.Us = (F*)h->Us;
+  D.Wm = h->Wm;
+  D.Cm = h->Cm;
+  D.cache = (F*)h->cache;
+  D.tot_ps = h->tot_ps;
+  D.tot_xs = h->tot_xs;
+  D.n_scen = h->n_scen;
+  D.status = h->status;
+  D.iters = h->iters;
+  D.cur_lvl = h->cur_lvl;
+  D.res = h->res;
+  D.eqp = h->eqp;
+  D.fact = h->fact;
+  D.queue = h->queue;
+  D.start_mode = h->opt.start_mode;
+  D.as_max = h->opt.as_max;
+  D.eps_rel = h->opt.eps_rel;
+  return D;
+}
+
+static inline int grid_for(int64_t n, int threads, int cap = 65535) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::import_inputs(tadmm_handle* h, cudaStream_t st) {
+  const int nm = NX * NX + NX * NU + 2 * NU;
+  k_convert<F><<<1, 128, 0, st>>>(h->st_model, (F*)h->model, nm);
+  const int64_t na = h->tot_agents;
+  k_convert<F><<<grid_for(na * NX, 256), 256, 0, st>>>(h->st_agent + 0 * na * NX, (F*)h->Qd, na * NX);
+  k_convert<F><<<grid_for(na * NU, 256), 256, 0, st>>>(h->st_agent + 1 * na * NX, (F*)h->Rd, na * NU);
+  k_convert<F><<<grid_for(na * NX, 256), 256, 0, st>>>(h->st_agent + 1 * na * NX + na * NU, (F*)h->Qfd, na * NX);
+  k_convert<F><<<grid_for(na * NX, 256), 256, 0, st>>>(h->st_agent + 2 * na * NX + na * NU, (F*)h->x_init, na * NX);
+  k_convert<F><<<grid_for(na * NX, 256), 256, 0, st>>>(h->st_agent + 3 * na * NX + na * NU, (F*)h->x_ref, na * NX);
+  if (h->tot_pairs > 0)
+    k_import_a<F, DP><<<grid_for(h->tot_pairs, 256), 256, 0, st>>>(h->meta, h->pair_scen, h->st_a, (F*)h->a,
+                                                                    h->tot_pairs);
+  k_import_w0<F, DP><<<grid_for(na, 128), 128, 0, st>>>(h->meta, h->agent_scen, h->st_w0, (F*)h->w0, na);
+  return cuda_check(cudaGetLastError(), "import kernels");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::max_ctas_per_sm(int tpc) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<F, NX, NU, DP>, tpc, 0) != cudaSuccess)
+    return 1;
+  return n < 1 ? 1 : n;
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter, cudaStream_t st) {
+  int tpc = h->tpc > 0 ? h->tpc : 128;
+  int cps = h->cps > 0 ? h->cps : max_ctas_per_sm(tpc);
+  cps = std::min(cps, max_ctas_per_sm(tpc));
+  const int grid = std::max(1, std::min(h->n_scen, h->sm_count * cps));
+  if (!h->gexec || h->g_tol != tol || h->g_iter != max_iter || h->g_tpc != tpc || h->g_cps != cps) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    Dev<F> D = make_dev<F>(h);
+    D.tol = tol;
+    D.max_iter = max_iter;
+    cudaGraph_t g = nullptr;
+    int rc = cuda_check(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc) return rc;
+    cudaMemsetAsync(h->queue, 0, sizeof(int32_t), h->cap_stream);
+    k_batched<F, NX, NU, DP><<<grid, tpc, 0, h->cap_stream>>>(D);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_check(le, "batched kernel launch"); }
+    if ((rc = cuda_check(ee, "end capture"))) return rc;
+    rc = cuda_check(cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    if (rc) return rc;
+    h->g_tol = tol;
+    h->g_iter = max_iter;
+    h->g_tpc = tpc;
+    h->g_cps = cps;
+  }
+  h->launches = 1;
+  return cuda_check(cudaGraphLaunch(h->gexec, st), "graph launch");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, cudaStream_t st) {
+  Dev<F> D = make_dev<F>(h);
+  D.tol = tol;
+  D.max_iter = max_iter;
+  unsigned long long* hb = (unsigned long long*)h->pinned;  // [0] flag, [1] r bits, [2] s bits
+  int64_t launches = 0;
+  for (int sc = 0; sc < h->n_scen; ++sc) {
+    const ScenMeta& s = h->meta_h[sc];
+    const int64_t PT = (int64_t)s.P * s.T, NT = (int64_t)s.N * s.T;
+    k_init<F, NX, NU, DP><<<grid_for(std::max(PT, NT), 256, 4096), 256, 0, st>>>(D, sc);
+    ++launches;
+    int cur = 0, status = ST_NOT_CONVERGED, iters = 0;
+    double r = 0, sres = 0;
+    for (int k = 0; k < max_iter; ++k) {
+      cudaMemsetAsync(h->flag, 0, sizeof(int32_t), st);
+      cudaMemsetAsync(h->red2, 0, 2 * sizeof(unsigned long long), st);
+      k_xupdate<F, NX, NU, DP><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, cur ^ 1, h->flag);
+      k_pair<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, cur, h->red2);
+      launches += 2;
+      cudaMemcpyAsync(hb, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(hb + 1, h->red2, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+      int rc = cuda_check(cudaStreamSynchronize(st), "plain-mode residual readback");
+      if (rc) return rc;
+      iters = k + 1;
+      const int flag = (int)(*(int32_t*)hb);
+      if (flag) { status = flag; break; }
+      if (sizeof(F) == 8) {
+        double rv, sv;
+        std::memcpy(&rv, &hb[1], 8);
+        std::memcpy(&sv, &hb[2], 8);
+        r = rv;
+        sres = s.rho * sv;
+        // the residual test is taken in the arithmetic type F
+        if (!std::isfinite(r) || !std::isfinite(sres)) { status = ST_NUMERIC; cur ^= 1; break; }
+        if (r <= tol && sres <= tol) { status = ST_CONVERGED; cur ^= 1; break; }
+      } else {
+        float rv, sv;
+        uint32_t rbits = (uint32_t)hb[1], sbits = (uint32_t)hb[2];
+        std::memcpy(&rv, &rbits, 4);
+        std::memcpy(&sv, &sbits, 4);
+        const float sf = float(s.rho) * sv;
+        r = rv;
+        sres = sf;
+        if (!std::isfinite(rv) || !std::isfinite(sf)) { status = ST_NUMERIC; cur ^= 1; break; }
+        if (rv <= float(tol) && sf <= float(tol)) { status = ST_CONVERGED; cur ^= 1; break; }
+      }
+      k_gather<F, NX, NU, DP><<<grid_for(NT, 128, h->sm_count * 8), 128, 0, st>>>(D, sc, cur ^ 1);
+      ++launches;
+      cur ^= 1;
+    }
+    k_finish<F><<<1, 1, 0, st>>>(D, sc, status, iters, cur, r, sres);
+    ++launches;
+  }
+  h->launches = launches;
+  return cuda_check(cudaGetLastError(), "plain-mode launches");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::export_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W,
+                                         cudaStream_t st) {
+  Dev<F> D = make_dev<F>(h);
+  if (X || U || W)
+    k_export_agents<F, NX, NU><<<grid_for(h->tot_agents, 128), 128, 0, st>>>(D, h->agent_scen, h->tot_agents,
+                                                                              X, U, W);
+  if (theta && h->tot_pairs > 0)
+    k_export_theta<F><<<grid_for(h->tot_pairs, 128), 128, 0, st>>>(D, h->pair_scen, h->tot_pairs, theta);
+  return cuda_check(cudaGetLastError(), "export kernels");
+}
+
+}  // namespace tadmm

@@ -1,0 +1,83 @@
+"""The C-ABI library builds for sm_103a, loads, exports every symbol declared in
+include/tadmm.h, and rejects invalid inputs on the host before any launch
+(no GPU needed for these calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libtadmm():
+    from paper_2602_15838_gb300 import build
+    path = build.build()
+    import paper_2602_15838_gb300 as tg
+    return tg, tg.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tadmm_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(libtadmm):
+    _, L = libtadmm
+    names = _declared()
+    assert "tadmm_create" in names and "tadmm_solve" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version_and_last_error(libtadmm):
+    tg, L = libtadmm
+    assert b"sm_103a" in L.tadmm_version()
+    assert isinstance(L.tadmm_last_error(), bytes)
+
+
+def _create_rc(tg, batch, **opt):
+    hb = tg._HostBatch(batch)
+    o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0)
+    h = C.c_void_p()
+    rc = tg.lib().tadmm_create(C.byref(hb.s), C.byref(o), C.byref(h))
+    return rc, tg.lib().tadmm_last_error().decode()
+
+
+@pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec"])
+def test_invalid_inputs_rejected_on_host(libtadmm, fault):
+    tg, _ = libtadmm
+    from instances import make_config
+    b = make_config(1)
+    opt = {}
+    if fault == "nan_q":
+        b.Qd = b.Qd.copy(); b.Qd[0, 1] = np.nan
+    elif fault == "neg_r":
+        b.Rd = b.Rd.copy(); b.Rd[1, 0] = -0.1
+    elif fault == "box":
+        b.umin = np.array([0.5, -1.0]); b.umax = np.array([0.4, 1.0])
+    elif fault == "rho":
+        b.rho = np.array([0.0])
+    elif fault == "dims":
+        b.dp = 3
+    elif fault == "N0":
+        b.N = np.array([0], dtype=np.int32)
+    elif fault == "prec":
+        opt["precision"] = 16
+    rc, msg = _create_rc(tg, b, **opt)
+    assert rc == tg.EINVAL, msg
+    assert msg
+
+
+def test_null_batch_rejected(libtadmm):
+    tg, L = libtadmm
+    h = C.c_void_p()
+    assert L.tadmm_create(None, None, C.byref(h)) == tg.EINVAL
+    assert L.tadmm_solve(None, 1e-4, 10, None) == tg.EINVAL

@@ -1,0 +1,183 @@
+"""GPU path (through the C ABI) against the CPU FP64 oracle, element by element.
+
+Tolerances (FP64): every ADMM iterate within 1e-9 relative
+(|gpu - oracle|_inf / max(1, |oracle|_inf)) on X, U and theta at equal
+iteration count; final working sets equal except degenerate entries (a bound
+multiplier within 1e-7 of zero, or a free input within 1e-9 of its bound).
+FP32 runs are stated against the FP64 oracle with 1e-4 relative on positions
+and inputs after a fixed number of iterations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from instances import make_config, random_scenario
+from instances.generator import make_batch, build_scenario
+
+pytestmark = pytest.mark.gpu
+
+START = {"cold": oracle.START_COLD, "hot": oracle.START_HOT, "turbo": oracle.START_TURBO}
+
+
+@pytest.fixture(scope="module")
+def tg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2602_15838_gb300 import build
+    build.build()
+    import paper_2602_15838_gb300 as m
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.size == 0:
+        return 0.0
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+def gpu_run(tg, batch, tol, max_iter, **kw):
+    s = tg.Solver(batch, **kw)
+    s.solve(tol, max_iter)
+    out = s.split(s.solution())
+    cnt = s.counters()
+    s.close()
+    return out, cnt
+
+
+def nondegenerate_w_equal(w_gpu, orc, batch, k=0):
+    Wg = w_gpu
+    Wo = orc["W"]
+    mu = orc["mu"]
+    U = orc["U"]
+    lo = batch.umin[None, None, :]
+    hi = batch.umax[None, None, :]
+    degen = ((Wo != 0) & (np.abs(mu) <= 1e-7)) | ((Wo == 0) & ((np.abs(U - lo) <= 1e-9) | (np.abs(U - hi) <= 1e-9)))
+    return np.array_equal(Wg[~degen], Wo[~degen]), int(degen.sum())
+
+
+@pytest.mark.parametrize("start", ["turbo", "hot", "cold"])
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_config1_every_iterate_fp64(tg, start, k):
+    b = make_config(1)
+    g, _ = gpu_run(tg, b, 0.0, k, start=start)
+    o = oracle.admm(b, 0, start_mode=START[start], tol=0.0, max_iter=k)
+    g = g[0]
+    assert g["iters"] == k == o["iters"]
+    assert rel(g["X"], o["X"]) <= 1e-9
+    assert rel(g["U"], o["U"]) <= 1e-9
+    assert rel(g["theta"], o["theta"]) <= 1e-9
+    ok, _ = nondegenerate_w_equal(g["W"], o, b)
+    assert ok
+
+
+def test_config1_converged_fp64(tg):
+    b = make_config(1)
+    g, cnt = gpu_run(tg, b, 1e-4, 500)
+    o = oracle.admm(b, 0, tol=1e-4, max_iter=500)
+    g = g[0]
+    assert g["status"] == o["status"] == tg.CONVERGED
+    assert g["iters"] == o["iters"]
+    assert rel(g["X"], o["X"]) <= 1e-9
+    assert abs(g["r"] - o["r"]) <= 1e-9 and abs(g["s"] - o["s"]) <= 1e-9
+    ok, _ = nondegenerate_w_equal(g["W"], o, b)
+    assert ok
+    assert cnt["eqp"][0] == o["as_iters"]
+
+
+@pytest.mark.parametrize("k", [1, 4, 30])
+def test_config2_iterates_fp64(tg, k):
+    b = make_config(2)
+    g, _ = gpu_run(tg, b, 0.0, k)
+    o = oracle.admm(b, 0, tol=0.0, max_iter=k, nthreads=8)
+    g = g[0]
+    assert rel(g["X"], o["X"]) <= 1e-9
+    assert rel(g["U"], o["U"]) <= 1e-9
+    assert rel(g["theta"], o["theta"]) <= 1e-9
+    ok, nd = nondegenerate_w_equal(g["W"], o, b)
+    assert ok
+
+
+def test_config2_plain_mode_matches_batched(tg):
+    b = make_config(2)
+    gb, cb = gpu_run(tg, b, 1e-4, 60)
+    gp, cp = gpu_run(tg, b, 1e-4, 60, mode="plain")
+    assert gb[0]["iters"] == gp[0]["iters"]
+    assert rel(gb[0]["X"], gp[0]["X"]) <= 1e-12
+    assert rel(gb[0]["theta"], gp[0]["theta"]) <= 1e-12
+    assert np.array_equal(gb[0]["W"], gp[0]["W"])
+    assert cb["eqp"][0] == cp["eqp"][0]
+
+
+def test_ragged_batch_and_edge_cases_fp64(tg):
+    """One batch mixing N = 1 (no pairs), N = 2 with T = 1, and uneven N, T:
+    every scenario matches its own oracle run at iteration 6."""
+    scen = []
+    specs = [(1, 7), (2, 1), (3, 11), (5, 4), (2, 9), (7, 13)]
+    for k, (N, T) in enumerate(specs):
+        s = random_scenario(seed=50 + k, N=N, T=T, box=2.5)
+        scen.append(s)
+    from instances.generator import Batch
+    parts = []
+    for s in scen:
+        parts.append(dict(N=int(s.N[0]), T=int(s.T[0]), x_init=s.x_init, x_ref=s.x_ref, a=s.a, w0=s.w0,
+                          d=float(s.d_min[0]), rho=float(s.rho[0]), umax=1.0, c=None))
+    b = make_batch(parts, dp=2, dt=0.1, umax=1.0)
+    g, _ = gpu_run(tg, b, 0.0, 6)
+    for k in range(len(specs)):
+        o = oracle.admm(b, k, tol=0.0, max_iter=6)
+        assert rel(g[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(g[k]["U"], o["U"]) <= 1e-9, k
+        if specs[k][0] > 1:
+            assert rel(g[k]["theta"], o["theta"]) <= 1e-9, k
+    # N = 1 converges after one iteration
+    g1, _ = gpu_run(tg, b.subset([0]), 1e-4, 50)
+    assert g1[0]["status"] == tg.CONVERGED and g1[0]["iters"] == 1
+
+
+def test_config3_sampled_scenarios_full_batch(tg):
+    """Full 4096-scenario batch in the benchmark's launch shape: sampled
+    scenarios agree with the oracle after a few iterations."""
+    b = make_config(3)
+    s = tg.Solver(b)
+    s.solve(0.0, 4)
+    out = s.split(s.solution())
+    s.close()
+    rng = np.random.default_rng(0)
+    for k in sorted(rng.choice(b.n_scen, 6, replace=False).tolist()) + [0, b.n_scen - 1]:
+        o = oracle.admm(b, k, tol=0.0, max_iter=4)
+        assert rel(out[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(out[k]["theta"], o["theta"]) <= 1e-9, k
+
+
+def test_config4_reduced_3d_fp64(tg):
+    """3D double integrator (nx=6, nu=3) at the large-coupling configuration's
+    model, horizon and spacing rules with fewer agents."""
+    b = make_config(4, N_override=12)
+    g, _ = gpu_run(tg, b, 0.0, 5)
+    o = oracle.admm(b, 0, tol=0.0, max_iter=5, nthreads=8)
+    assert rel(g[0]["X"], o["X"]) <= 1e-9
+    assert rel(g[0]["theta"], o["theta"]) <= 1e-9
+    assert rel(g[0]["U"], o["U"]) <= 1e-9
+
+
+def test_config2_fp32_against_fp64_oracle(tg):
+    b = make_config(2)
+    g, _ = gpu_run(tg, b, 0.0, 10, precision=32)
+    o = oracle.admm(b, 0, tol=0.0, max_iter=10, nthreads=8)
+    assert rel(g[0]["X"], o["X"]) <= 1e-4
+    assert rel(g[0]["U"], o["U"]) <= 1e-3
+
+
+def test_literal_infeasible_not_converged(tg):
+    b = make_config(1, literal=True)
+    g, _ = gpu_run(tg, b, 1e-4, 200)
+    assert g[0]["status"] == tg.NOT_CONVERGED and g[0]["iters"] == 200
+
+
+def test_as_max_one_reports_qp_fail(tg):
+    b = make_config(2)
+    g, _ = gpu_run(tg, b, 1e-4, 20, start="cold", as_max=1)
+    assert g[0]["status"] == tg.QP_FAIL
