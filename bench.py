@@ -1,0 +1,371 @@
+"""Benchmark: multi-agent QP solves/sec at residual 1e-4, batched GPU vs plain GPU.
+
+Workload (one step): the 4096-scenario mixed batch (N ~ U{2..32} agents,
+T ~ U{20..40} steps, 2D double integrator, d_min 0.4, rho 1, |u| <= 1), FP64,
+solved from scratch by ADMM to primal and dual residual 1e-4 or 500 iterations
+in one persistent, graph-captured launch.  A solve is a scenario that reaches
+the tolerance; scenarios stopped by the iteration cap are reported, not counted.
+
+value      converged solves / second, inputs resident in HBM, device-timed (CUDA
+           events on the launch stream around each step, L2 flushed between steps).
+e2e        the same metric through the C ABI from pinned host buffers: upload of
+           every input array, solve, download of X, U, theta, W, status, iters,
+           residuals, all inside the timed region.
+roofline   FP64 pipe (ALU-bound): algorithmic flops of the step from the kernel's
+           own event counters (pair-steps, EQP stages, factorized stages) over the
+           device time; peak 1.259 TFLOP/s = 152 SMs x 4 FP64 flop/clk x 2.07 GHz.
+plain_gpu  the same kernels, one scenario at a time, one launch per phase and a
+           host read of the residuals every iteration, on a seeded sample.
+cpu_baseline  the FP64 oracle on the host cores on a bounded seeded sample
+           (20 ADMM iterations per sampled scenario), scaled to solves/s with the
+           GPU run's solves per scenario-iteration.
+
+--impl reference runs that oracle as the reference arm (rank 0 only).
+Multi-GPU (torchrun): each rank solves its own batch (scenario ids offset by
+rank), no collective on the data path; whole-job value = all solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multi-agent QP solves/sec at residual 1e-4 (batched vs plain GPU); ms/solve"
+UNIT = "solves/s"
+PEAK_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 1.259
+# Solves per scenario-iteration of this workload at tol 1e-4, max_iter 500 (a
+# property of the ADMM iterates on these instances; the GPU arm measures it live
+# and the CPU baselines use it to express oracle throughput in solves/s).
+WORKLOAD_SOLVES_PER_SCEN_ITER = None
+# algorithmic flops per unit (2D double integrator, nx=4, nu=2)
+FLOPS_PAIRSTEP, FLOPS_EQP_STAGE, FLOPS_FACT_STAGE = 30.0, 190.0, 580.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", type=int, default=64)
+    p.add_argument("--n-scen", type=int, default=4096)
+    p.add_argument("--tol", type=float, default=1e-4)
+    p.add_argument("--max-iter", type=int, default=500)
+    p.add_argument("--plain-sample", type=int, default=16)
+    p.add_argument("--cpu-iters", type=int, default=20)
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def workload_batch(n_scen: int, rank: int):
+    from instances import make_config
+    return make_config(3, n_scen=n_scen, first=rank * n_scen)
+
+
+def algorithmic_flops(batch, cnt, sol):
+    """Flops of one step from the kernel's counters (per-unit figures above)."""
+    T = batch.T.astype(np.float64)
+    lqr = np.where(sol["iters"] > 0, batch.N, 0) * T   # warm-start LQR solve of the first iteration
+    eqp_stages = float((cnt["eqp"] * T).sum() + lqr.sum())
+    fact_stages = float(cnt["fact"].sum())
+    pairsteps = float(cnt["pairsteps"].sum())
+    flops = FLOPS_PAIRSTEP * pairsteps + FLOPS_EQP_STAGE * eqp_stages + FLOPS_FACT_STAGE * fact_stages
+    return flops, dict(pairsteps=pairsteps, eqp_stages=eqp_stages, fact_stages=fact_stages)
+
+
+def cpu_baseline(batch, args, gpu_solves_per_scen_iter):
+    """Oracle on a bounded seeded sample; scaled to solves/s."""
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(1234)
+    nsamp = min(batch.n_scen, cores)
+    idx = sorted(rng.choice(batch.n_scen, nsamp, replace=False).tolist())
+    t0 = time.perf_counter()
+    res, used = oracle.admm_batch(batch, idx, start_mode=oracle.START_TURBO, tol=0.0, max_iter=args.cpu_iters,
+                                  nthreads=cores)
+    dt = time.perf_counter() - t0
+    scen_iter_per_s = sum(r["iters"] for r in res) / dt
+    return dict(value=scen_iter_per_s * gpu_solves_per_scen_iter, unit=UNIT, cores=int(used), kind="oracle",
+                sample=f"{nsamp} seeded scenarios of the batch x {args.cpu_iters} ADMM iterations each "
+                       f"({dt:.1f} s, {scen_iter_per_s:.2f} scenario-iterations/s), scaled by the GPU run's "
+                       f"solves per scenario-iteration")
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    batch = workload_batch(args.n_scen, 0)
+    cores = os.cpu_count() or 1
+    nsamp = min(batch.n_scen, cores)
+    rng = np.random.default_rng(1234)
+    times, solves, iters_done = [], 0, 0
+    for step in range(args.warmup + args.steps):
+        idx = sorted(rng.choice(batch.n_scen, nsamp, replace=False).tolist())
+        t0 = time.perf_counter()
+        res, used = oracle.admm_batch(batch, idx, start_mode=oracle.START_TURBO, tol=args.tol,
+                                      max_iter=args.cpu_iters, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            solves += sum(r["status"] == 0 for r in res)
+            iters_done += sum(r["iters"] for r in res)
+    total = sum(times)
+    value = solves / total if total > 0 else 0.0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"mixed batch of {args.n_scen} scenarios (N~U{{2..32}}, T~U{{20..40}}, 2D), "
+                                   f"oracle on {nsamp} seeded scenarios per step, tol {args.tol}, "
+                                   f"max_iter {args.cpu_iters}", "n_scen": args.n_scen},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": int(used),
+                             "sample": f"{nsamp} seeded scenarios per step, {args.cpu_iters} ADMM iterations cap, "
+                                       f"{iters_done} scenario-iterations in the timed steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+    import paper_2602_15838_gb300 as tg
+    from paper_2602_15838_gb300 import build as tb
+    tb.build()
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    batch = workload_batch(args.n_scen, rank)
+    solver = tg.Solver(batch, precision=args.precision, start="turbo", mode="batched")
+    tpc, cps = (0, 0) if args.no_autotune else solver.autotune(probe_iter=10)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        solver.solve(args.tol, args.max_iter)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(dev)
+    barrier()
+    torch.cuda.synchronize()
+    with clocks:
+        for k in range(args.steps):
+            flush.zero_()                       # evict L2 between steps (outside the events)
+            ev[k][0].record(stream)
+            solver.solve(args.tol, args.max_iter)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    sol = solver.solution()
+    cnt = solver.counters()
+    solves_local = int((sol["status"] == tg.CONVERGED).sum())
+    scen_iters = int(sol["iters"].sum())
+    if dist is not None:
+        t = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s_ = torch.tensor([solves_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(s_)
+        t_max, solves_all = float(t.item()), float(s_.item())
+    else:
+        t_max, solves_all = t_local, float(solves_local)
+    value = solves_all * args.steps / t_max if t_max > 0 else 0.0
+    ms_step = 1e3 * t_max / args.steps
+    flops, units = algorithmic_flops(batch, cnt, sol)
+    achieved = flops / (t_local / args.steps) / 1e12
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hb = tg._HostBatch(batch, pinned=True)
+        X = torch.empty(solver.sizes["X"], dtype=torch.float64).pin_memory()
+        U = torch.empty(solver.sizes["U"], dtype=torch.float64).pin_memory()
+        TH = torch.empty(max(1, solver.sizes["theta"]), dtype=torch.float64).pin_memory()
+        W = torch.empty(solver.sizes["U"], dtype=torch.int8).pin_memory()
+        st = torch.empty(batch.n_scen, dtype=torch.int32).pin_memory()
+        it = torch.empty(batch.n_scen, dtype=torch.int32).pin_memory()
+        rs = torch.empty(2 * batch.n_scen, dtype=torch.float64).pin_memory()
+        import ctypes as C
+        L = tg.lib()
+        sp = C.c_void_p(stream.cuda_stream)
+        e2e_ms, e2e_solves = [], 0
+        for k in range(1 + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tg._check(L.tadmm_update(solver.h, C.byref(hb.s), sp), "tadmm_update")
+            tg._check(L.tadmm_solve(solver.h, args.tol, args.max_iter, sp), "tadmm_solve")
+            tg._check(L.tadmm_get_solution(solver.h, C.c_void_p(X.data_ptr()), C.c_void_p(U.data_ptr()),
+                                           C.c_void_p(TH.data_ptr()), C.c_void_p(W.data_ptr()),
+                                           C.c_void_p(st.data_ptr()), C.c_void_p(it.data_ptr()),
+                                           C.c_void_p(rs.data_ptr()), sp), "tadmm_get_solution")
+            dt = time.perf_counter() - t0
+            if k >= 1:
+                e2e_ms.append(dt * 1e3)
+                e2e_solves += int((st.numpy() == 0).sum())
+        h2d = sum(v.nbytes for v in hb.keep.values()) + hb.N.nbytes + hb.T.nbytes
+        d2h = X.numel() * 8 + U.numel() * 8 + TH.numel() * 8 + W.numel() + 4 * 2 * batch.n_scen + 16 * batch.n_scen
+        e2e = {"value": e2e_solves / (sum(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)}
+
+    out = None
+    if rank == 0:
+        plain = None
+        if not args.no_plain:
+            rng = np.random.default_rng(99)
+            idx = sorted(rng.choice(batch.n_scen, min(args.plain_sample, batch.n_scen), replace=False).tolist())
+            sub = batch.subset(idx)
+            ps = tg.Solver(sub, precision=args.precision, start="turbo", mode="plain")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ps.solve(args.tol, args.max_iter)
+            torch.cuda.synchronize()
+            pdt = time.perf_counter() - t0
+            psol = ps.solution()
+            pconv = int((psol["status"] == 0).sum())
+            pscen_iters = int(psol["iters"].sum())
+            ps.close()
+            # batched on the same sample, for the work-matched comparison
+            bs = tg.Solver(sub, precision=args.precision, start="turbo", mode="batched")
+            bs.solve(args.tol, args.max_iter)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bs.solve(args.tol, args.max_iter)
+            torch.cuda.synchronize()
+            bdt = time.perf_counter() - t0
+            bs.close()
+            plain = {"value": pconv / pdt, "unit": UNIT, "scenarios": len(idx), "solves": pconv,
+                     "seconds": pdt, "scenario_iterations_per_s": pscen_iters / pdt,
+                     "batched_same_sample_seconds": bdt,
+                     "speedup_batched_full_vs_plain": (value / (pconv / pdt)) if pconv else None,
+                     "speedup_same_sample_wall": pdt / bdt}
+        cpu = None
+        if not args.no_cpu:
+            cpu = cpu_baseline(batch, args, solves_local / max(1, scen_iters))
+        clk = clocks.summary()
+        launches = args.steps * solver_launches(solver)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == 64 else "f32", "data": "synthetic",
+            "config": {"workload": f"mixed batch: {args.n_scen} scenarios per GPU, N~U{{2..32}} agents, "
+                                   f"T~U{{20..40}}, 2D double integrator, d_min 0.4, rho 1, |u|<=1; "
+                                   f"tol {args.tol}, max_iter {args.max_iter}",
+                       "n_scen": args.n_scen, "tol": args.tol, "max_iter": args.max_iter,
+                       "precision": args.precision, "parallelism": f"replicas x{world} (scenario shards)",
+                       "launch": {"threads_per_cta": tpc, "ctas_per_sm": cps, "autotuned": not args.no_autotune},
+                       "l2": "256 MB buffer written between steps (outside timing); working set > L2"},
+            "solves_per_step": solves_all, "scenarios_per_step": args.n_scen * world,
+            "ms_per_solve": (1e3 * t_max / args.steps) / max(1.0, solves_all),
+            "scenario_iterations_per_s": scen_iters * args.steps / t_local,
+            "clocks": clk,
+            "roofline": {"bound": "alu", "kernel": "k_batched (FP64 pipe)", "achieved": achieved,
+                         "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
+                         "traffic": None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                         "algorithmic_units": units, "algorithmic_flops_per_step": flops},
+            "plain_gpu": plain,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def solver_launches(solver) -> int:
+    return 1   # one persistent kernel per step (the graph also holds one memset node)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -306,12 +306,13 @@ def _scenario_points(cfg: int, k: int, rng: SplitMix64, dp: int, N_override=None
 
 def make_config(cfg: int, n_scen: Optional[int] = None, literal: bool = False,
                 N_override: Optional[int] = None, T_override: Optional[int] = None,
-                dt: float = 0.1) -> Batch:
-    """Instances of synthetic configuration `cfg` (1..5), seeded per scenario."""
+                dt: float = 0.1, first: int = 0) -> Batch:
+    """Instances of synthetic configuration `cfg` (1..5), seeded per scenario;
+    scenario ids first .. first + n_scen - 1."""
     dp = CONFIG_DEFAULTS[cfg]["dp"]
     S = CONFIG_DEFAULTS[cfg]["n_scen"] if n_scen is None else n_scen
     scen = []
-    for k in range(S):
+    for k in range(first, first + S):
         rng = SplitMix64((cfg << 32) + k)
         N, T, starts, goals, d, rho, umax = _scenario_points(cfg, k, rng, dp, N_override, T_override)
         x_init, x_ref, a, w0, c = build_scenario(starts, goals, T, dt, d, literal=literal)
