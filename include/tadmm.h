@@ -134,6 +134,49 @@ int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pa
 int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* threads_out,
                    int32_t* ctas_out);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free single-scenario solve.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory while they run, such as a real-time control loop
+ * allowed to allocate only at start-up (cudaMalloc takes unpredictable time and
+ * can synchronize the device) or a program whose device memory belongs to an
+ * outside allocator.  It solves one scenario exactly like tadmm_create +
+ * tadmm_solve + tadmm_get_solution in float64, but calls no allocating routine:
+ * inputs and outputs are DEVICE buffers owned by the caller, in the layouts of
+ * tadmm_batch for n_scen = 1, and all solver state lives in one fixed array of
+ * TADMM_NOALLOC_SCRATCH_BYTES in device global memory that the library reserves
+ * on every GPU that loads it and holds until the process exits.
+ *
+ * Limits and behaviour:
+ *  - a scenario whose state does not fit (about 32 bytes per pair-step plus
+ *    ~400 bytes per agent-step in 2D) is rejected with TADMM_EINVAL naming the
+ *    required size; nothing is launched;
+ *  - the first call on each device looks up the array's device address on that
+ *    device (it must be current); make that first call before any stream
+ *    capture;
+ *  - every call shares the array and re-initializes all state it reads; calls
+ *    whose GPU work overlaps (other streams or host threads on the same device)
+ *    race on it and must be serialized by the caller;
+ *  - input values are not checked on the host (they are on the device);
+ *  - asynchronous on `stream`; outputs: X [N][T+1][nx], U [N][T][nu],
+ *    theta [P*T] (may be NULL), status_iters [2] = {status, iterations},
+ *    res [2] = {r, s}; any output pointer may be NULL.                        */
+#define TADMM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+typedef struct {
+  int32_t nx, nu, dp;    /* (4, 2, 2) or (6, 3, 3) */
+  int32_t N, T;          /* agents (1..32767) and horizon (>= 1) */
+  const double *A, *B, *umin, *umax;              /* device pointers */
+  const double *Qd, *Rd, *Qfd, *x_init, *x_ref;   /* device pointers, per agent */
+  const double *a;       /* device, [P*T][dp]; may be NULL when N == 1 */
+  const double *w0;      /* device, [N*T][dp] */
+  double d_min, rho;
+} tadmm_scenario_dev;
+
+int tadmm_solve_noalloc(const tadmm_scenario_dev* scenario, int32_t start_mode, double tol, int32_t max_iter,
+                        double* X, double* U, double* theta, int32_t* status_iters, double* res, void* stream);
+
 /* Frees all device memory of the handle (synchronizes the device first). */
 void tadmm_destroy(tadmm_handle* h);
 
