@@ -215,7 +215,7 @@ def run_ours(args, rank, world):
 
     batch = workload_batch(args.n_scen, rank)
     solver = tg.Solver(batch, precision=args.precision, start="turbo", mode="batched")
-    tpc, cps = (0, 0) if args.no_autotune else solver.autotune(probe_iter=10)
+    tpc, cps, var = (0, 0, 0) if args.no_autotune else solver.autotune(probe_iter=10)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -332,7 +332,8 @@ def run_ours(args, rank, world):
                                    f"tol {args.tol}, max_iter {args.max_iter}",
                        "n_scen": args.n_scen, "tol": args.tol, "max_iter": args.max_iter,
                        "precision": args.precision, "parallelism": f"replicas x{world} (scenario shards)",
-                       "launch": {"threads_per_cta": tpc, "ctas_per_sm": cps, "autotuned": not args.no_autotune},
+                       "launch": {"threads_per_cta": tpc, "ctas_per_sm": cps, "kernel_variant": var,
+                                  "autotuned": not args.no_autotune},
                        "l2": "256 MB buffer written between steps (outside timing); working set > L2"},
             "solves_per_step": solves_all, "scenarios_per_step": args.n_scen * world,
             "ms_per_solve": (1e3 * t_max / args.steps) / max(1.0, solves_all),

@@ -91,6 +91,8 @@ typedef struct {
   int32_t mode;            /* TADMM_MODE_* */
   int32_t threads_per_cta; /* batched mode: threads per scenario CTA; 0 = tuned/default */
   int32_t ctas_per_sm;     /* batched mode: resident CTAs per SM; 0 = tuned/default */
+  int32_t kernel_variant;  /* batched mode: register-budget variant 0..4 of the persistent kernel
+                              (0: no cap; 1: 32 thr x 12 CTAs; 2: 32 x 16; 3: 32 x 24; 4: 64 x 8) */
 } tadmm_options;
 
 typedef struct tadmm_handle tadmm_handle;
@@ -127,12 +129,12 @@ int tadmm_get_solution(tadmm_handle* h, double* X, double* U, double* theta, int
  * fact [n_scen] Riccati stage factorizations, pairsteps processed. */
 int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pairsteps);
 
-/* Times the candidate launch shapes of the batched persistent kernel on this
- * batch with `probe_iter` ADMM iterations each and keeps the fastest
- * (threads_per_cta, ctas_per_sm).  Synchronous.  Writes the choice to
- * *threads_out / *ctas_out when non-NULL. */
+/* Times the candidate launch shapes of the batched persistent kernel (threads
+ * per CTA, resident CTAs per SM, register-budget variant) on this batch with
+ * `probe_iter` ADMM iterations each and keeps the fastest.  Synchronous.
+ * Writes the choice to the non-NULL outputs. */
 int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* threads_out,
-                   int32_t* ctas_out);
+                   int32_t* ctas_out, int32_t* variant_out);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free single-scenario solve.

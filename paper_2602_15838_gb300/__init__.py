@@ -36,7 +36,7 @@ class TadmmBatch(C.Structure):
 class TadmmOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("start_mode", C.c_int32), ("as_max", C.c_int32),
                 ("eps_rel", C.c_double), ("mode", C.c_int32), ("threads_per_cta", C.c_int32),
-                ("ctas_per_sm", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("kernel_variant", C.c_int32)]
 
 
 class TadmmError(RuntimeError):
@@ -59,7 +59,7 @@ def lib():
         L.tadmm_get_solution.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_get_counters.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
-        L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p]
+        L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p, _i32p]
         L.tadmm_destroy.argtypes = [C.c_void_p]
         L.tadmm_destroy.restype = None
         L.tadmm_last_error.restype = C.c_char_p
@@ -116,14 +116,16 @@ class Solver:
     """
 
     def __init__(self, batch, precision: int = 64, start: str = "turbo", mode: str = "batched",
-                 as_max: int = 0, eps_rel: float = 0.0, threads_per_cta: int = 0, ctas_per_sm: int = 0):
+                 as_max: int = 0, eps_rel: float = 0.0, threads_per_cta: int = 0, ctas_per_sm: int = 0,
+                 kernel_variant: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise TadmmError("no CUDA device: the solver has no CPU path")
         self.batch = batch
         self.precision = precision
         self._hb = _HostBatch(batch)
-        opt = TadmmOptions(precision, START[start], as_max, eps_rel, MODE[mode], threads_per_cta, ctas_per_sm)
+        opt = TadmmOptions(precision, START[start], as_max, eps_rel, MODE[mode], threads_per_cta, ctas_per_sm,
+                           kernel_variant)
         h = C.c_void_p()
         _check(lib().tadmm_create(C.byref(self._hb.s), C.byref(opt), C.byref(h)), "tadmm_create")
         self.h = h
@@ -153,10 +155,11 @@ class Solver:
         _check(lib().tadmm_solve(self.h, float(tol), int(max_iter), C.c_void_p(_stream_ptr(stream))), "tadmm_solve")
 
     def autotune(self, probe_iter: int = 20, stream=None):
-        t = C.c_int32(0); c = C.c_int32(0)
+        """Returns the chosen (threads_per_cta, ctas_per_sm, kernel_variant)."""
+        t = C.c_int32(0); c = C.c_int32(0); v = C.c_int32(0)
         _check(lib().tadmm_autotune(self.h, int(probe_iter), C.c_void_p(_stream_ptr(stream)), C.byref(t),
-                                    C.byref(c)), "tadmm_autotune")
-        return t.value, c.value
+                                    C.byref(c), C.byref(v)), "tadmm_autotune")
+        return t.value, c.value, v.value
 
     def solution(self, device: bool = False, stream=None):
         """Results as numpy arrays (host) or float64 torch tensors on the GPU."""

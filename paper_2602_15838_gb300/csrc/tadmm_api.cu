@@ -163,6 +163,7 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   if (o.threads_per_cta != 0 && (o.threads_per_cta < 32 || o.threads_per_cta > 256 || o.threads_per_cta % 32))
     return set_error(TADMM_EINVAL, "threads_per_cta must be 0 or a multiple of 32 in [32, 256]");
   if (o.ctas_per_sm < 0) return set_error(TADMM_EINVAL, "ctas_per_sm must be >= 0");
+  if (o.kernel_variant < 0 || o.kernel_variant > 4) return set_error(TADMM_EINVAL, "kernel_variant must be in 0..4");
 
   tadmm_handle* h = new tadmm_handle();
   h->prec = o.precision;
@@ -173,6 +174,7 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   h->opt = o;
   h->tpc = o.threads_per_cta;
   h->cps = o.ctas_per_sm;
+  h->variant = o.kernel_variant;
   h->N.assign(b->N, b->N + b->n_scen);
   h->T.assign(b->T, b->T + b->n_scen);
   h->meta_h.resize(b->n_scen);
@@ -225,7 +227,7 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
       (rc = dmalloc(&h->Rd, fs * na * nu)) || (rc = dmalloc(&h->Qfd, fs * na * nx)) ||
       (rc = dmalloc(&h->x_init, fs * na * nx)) || (rc = dmalloc(&h->x_ref, fs * na * nx)) ||
       (rc = dmalloc(&h->a, fs * h->tot_ps * dp)) || (rc = dmalloc(&h->w0, fs * h->tot_as * dp)) ||
-      (rc = dmalloc(&h->theta, fs * 2 * h->tot_ps)) || (rc = dmalloc(&h->X, fs * 2 * h->tot_xs * nx)) ||
+      (rc = dmalloc(&h->theta, fs * 3 * h->tot_ps)) || (rc = dmalloc(&h->X, fs * 2 * h->tot_xs * nx)) ||
       (rc = dmalloc(&h->h, fs * h->tot_as * dp)) || (rc = dmalloc(&h->U, fs * h->tot_as * nu)) ||
       (rc = dmalloc(&h->Us, fs * h->tot_as * nu)) ||
       (rc = dmalloc(&h->cache, fs * h->tot_xs * cache_words(nx, nu))) ||
@@ -357,7 +359,7 @@ extern "C" int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, 
 }
 
 extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* threads_out,
-                              int32_t* ctas_out) {
+                              int32_t* ctas_out, int32_t* variant_out) {
   if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
   if (probe_iter < 1) return set_error(TADMM_EINVAL, "probe_iter must be >= 1");
   if (h->opt.mode != TADMM_MODE_BATCHED) return set_error(TADMM_EINVAL, "autotune applies to the batched mode");
@@ -366,16 +368,19 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_t = 128, best_c = 0;
-  const int cand_t[] = {32, 64, 128, 256};
+  int best_t = 128, best_c = 0, best_v = 0;
+  struct Cand { int v, tpc; };
+  const Cand cands[] = {{0, 32}, {0, 64}, {0, 128}, {1, 32}, {2, 32}, {3, 32}, {4, 64}};
   int rc = TADMM_OK;
-  for (int tpc : cand_t) {
-    int maxc = 1;
-    auto occ = [&]() -> int { TADMM_DISPATCH(h, max_ctas_per_sm(tpc)); };
-    maxc = occ();
-    std::vector<int> cands = {maxc};
-    if (maxc >= 2) cands.push_back(maxc / 2);
-    for (int cps : cands) {
+  for (const Cand& cd : cands) {
+    const int tpc = cd.tpc;
+    auto occ = [&]() -> int { TADMM_DISPATCH(h, max_ctas_per_sm(tpc, cd.v)); };
+    const int maxc = occ();
+    if (maxc < 1) continue;
+    std::vector<int> cps_list = {maxc};
+    if (maxc >= 4) cps_list.push_back(maxc / 2);
+    for (int cps : cps_list) {
+      h->variant = cd.v;
       h->tpc = tpc;
       h->cps = cps;
       float ms = 0;
@@ -391,6 +396,7 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
         best = ms;
         best_t = tpc;
         best_c = cps;
+        best_v = cd.v;
       }
     }
     if (rc) break;
@@ -400,8 +406,10 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
   if (rc) return rc;
   h->tpc = best_t;
   h->cps = best_c;
+  h->variant = best_v;
   if (threads_out) *threads_out = best_t;
   if (ctas_out) *ctas_out = best_c;
+  if (variant_out) *variant_out = best_v;
   return TADMM_OK;
 }
 

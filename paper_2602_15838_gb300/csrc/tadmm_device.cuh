@@ -18,7 +18,8 @@
 //   Wm, Cm  [T][N]         working-set and cached-factor bit masks
 //   cache   [T+1][E][N]    Riccati cache per stage: P, K, L (Cholesky of the
 //                          reduced S with inverted diagonal), k, p
-//   theta   [lvl][T][P]    projection steps theta^k (multiplier / rho)
+//   theta   [slot][T][P]   projection steps theta^k (multiplier / rho), three
+//                          slots rotating with k mod 3
 //   a       [T][DP][P]     halfspace normals
 #pragma once
 
@@ -54,7 +55,7 @@ struct Dev {
   const F* x_ref;         // [agents][NX]
   const F* a;             // per scenario [T][DP][P] at ps_off*DP
   const F* w0;            // per scenario [T][DP][N] at as_off*DP
-  F* theta;               // level l at l*tot_ps, per scenario [T][P] at ps_off
+  F* theta;               // slot l (0..2) at l*tot_ps, per scenario [T][P] at ps_off
   F* X;                   // level l at l*tot_xs*NX, per scenario [T+1][NX][N] at xs_off*NX
   F* h;                   // per scenario [T][DP][N] at as_off*DP
   F* U;                   // per scenario [T][NU][N] at as_off*NU
@@ -66,7 +67,7 @@ struct Dev {
   int32_t n_scen;
   int32_t* status;        // [n_scen]
   int32_t* iters;         // [n_scen]
-  int32_t* cur_lvl;       // [n_scen] level holding the final iterate
+  int32_t* cur_lvl;       // [n_scen] X level (bit 0) and theta slot (bits 1-2) of the final iterate
   double* res;            // [n_scen][2]
   unsigned long long* eqp;   // [n_scen]
   unsigned long long* fact;  // [n_scen]
@@ -125,6 +126,26 @@ __device__ __forceinline__ float fabs_(float v) { return fabsf(v); }
 __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
 __device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
 
+// |v| as a bit-ordered key (sign bit cleared on the integer pipe).
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float v) {
+  return (unsigned long long)((unsigned int)__float_as_int(v) & 0x7FFFFFFFu);
+}
+// Order-preserving integer key of a floating value (-0 sorts just below +0),
+// so that range checks run on the integer pipe.
+__device__ __forceinline__ unsigned long long mono_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return (unsigned long long)(b ^ ((b >> 63) | (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ unsigned long long mono_key(float v) {
+  const int b = __float_as_int(v);
+  return (unsigned long long)(unsigned int)(b ^ ((b >> 31) | (int)0x80000000u));
+}
+__device__ __forceinline__ bool sign_set(double v) { return __double_as_longlong(v) < 0; }
+__device__ __forceinline__ bool sign_set(float v) { return __float_as_int(v) < 0; }
+
 __device__ __forceinline__ int pair_index(int N, int i, int j) {  // i < j
   return i * N - (i * (i + 1)) / 2 + (j - i - 1);
 }
@@ -144,6 +165,7 @@ struct EqpScan {
   int widx;       // its index, -1 if none
   F scale;        // max(1, max |mu| over the working set)
   int bad;        // non-positive pivot or non-finite value
+  int out;        // some free input of the EQP solution left the box
 };
 
 template <typename F, int NX, int NU, int DP>
@@ -284,38 +306,42 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
 }
 
 // One EQP solve: backward pass (refactor stages t <= dirty, affine pass at
-// every stage), then forward pass (Sec. IV.B forward rollout, costates
-// lambda_{t+1} = P_{t+1} x_{t+1} + p_{t+1}) writing Us and X, with the ratio
-// test of the primal active set against the current iterate U and the scan of
-// the working-set multipliers mu = +-(Rbar u + B' lambda_{t+1}).
+// every stage), then forward pass (Sec. IV.B forward rollout) writing Us and X.
+// The forward pass also scans the working-set multipliers
+// mu = +-(Rbar u + B' lambda_{t+1}) with the costate lambda_{t+1} =
+// P_{t+1} x_{t+1} + p_{t+1} (Sec. IV.B dual recovery), evaluated only at stages
+// that hold fixed inputs, and flags free inputs that left the box (integer
+// keys); the exact ratio test runs only when such an input exists.
 template <typename F, int NX, int NU, int DP>
 __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, unsigned long long& nfact) {
   using CL = CacheLayout<NX, NU>;
   const Model<F, NX, NU>& Mo = *A.M;
   const int T = A.T;
   EqpScan<F> o;
-  o.anum = 1; o.aden = 1; o.blk = -1; o.bside = 0; o.worst = 0; o.widx = -1; o.scale = 1; o.bad = 0;
+  o.anum = 1; o.aden = 1; o.blk = -1; o.bside = 0; o.worst = 0; o.widx = -1; o.scale = 1; o.bad = 0; o.out = 0;
 
-  F Pn[NX][NX], pn[NX];
+  F pn[NX];
 #pragma unroll
-  for (int r = 0; r < NX; ++r) {
-#pragma unroll
-    for (int c = 0; c < NX; ++c) Pn[r][c] = (r == c) ? A.qbarT[r] : F(0);
-    pn[r] = A.q(T, r);
-  }
+  for (int r = 0; r < NX; ++r) pn[r] = A.q(T, r);
   if (dirty >= T - 1) {
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
-      for (int c = 0; c < NX; ++c) A.C(T, CL::P + r * NX + c) = Pn[r][c];
+      for (int c = 0; c < NX; ++c) A.C(T, CL::P + r * NX + c) = (r == c) ? A.qbarT[r] : F(0);
   }
 #pragma unroll
   for (int r = 0; r < NX; ++r) A.C(T, CL::p + r) = pn[r];
 
   for (int t = T - 1; t >= 0; --t) {
     const uint16_t mask = A.W(t);
-    F Pt[NX][NX], K[NU][NX], L[NU][NU];
-    if (t <= dirty) {
+    F K[NU][NX], L[NU][NU];
+    const bool refac = t <= dirty;
+    if (refac) {
+      F Pn[NX][NX], Pt[NX][NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int c = 0; c < NX; ++c) Pn[r][c] = A.C(t + 1, CL::P + r * NX + c);
       o.bad |= factor_stage<F, NX, NU>(Mo, Pn, mask, A.rbar, t >= 1 ? A.qbar : nullptr, Pt, K, L);
       ++nfact;
 #pragma unroll
@@ -340,14 +366,8 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
         for (int b = 0; b < NU; ++b) L[a][b] = (b <= a) ? A.C(t, CL::L + a * NU + b) : F(0);
       }
-      if (t >= 1) {
-#pragma unroll
-        for (int r = 0; r < NX; ++r)
-#pragma unroll
-          for (int c = 0; c < NX; ++c) Pt[r][c] = A.C(t, CL::P + r * NX + c);
-      }
     }
-    // affine pass: Pc + p with c = B_fixed u_fixed
+    // affine pass: P_{t+1} c + p_{t+1} with c = B_fixed u_fixed
     F Pcp[NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r) Pcp[r] = pn[r];
@@ -367,7 +387,7 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
       for (int r = 0; r < NX; ++r) {
         F acc = Pcp[r];
 #pragma unroll
-        for (int c = 0; c < NX; ++c) acc = fma(Pn[r][c], cv[c], acc);
+        for (int c = 0; c < NX; ++c) acc = fma(A.C(t + 1, CL::P + r * NX + c), cv[c], acc);
         Pcp[r] = acc;
       }
     }
@@ -399,7 +419,6 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
     for (int a = 0; a < NU; ++a) A.C(t, CL::k + a) = kk[a];
     if (t >= 1) {
-      F pt[NX];
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
         F acc = A.q(t, r);
@@ -407,19 +426,19 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
         for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], Pcp[k], acc);
 #pragma unroll
         for (int k = 0; k < NU; ++k) acc = fma(K[k][r], sv[k], acc);
-        pt[r] = acc;
-      }
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        A.C(t, CL::p + r) = pt[r];
-        pn[r] = pt[r];
-#pragma unroll
-        for (int c = 0; c < NX; ++c) Pn[r][c] = Pt[r][c];
+        A.C(t, CL::p + r) = acc;
+        pn[r] = acc;
       }
     }
   }
 
   // forward rollout
+  unsigned long long kmin[NU], kmax[NU];
+#pragma unroll
+  for (int a = 0; a < NU; ++a) {
+    kmin[a] = mono_key(Mo.umin[a]);
+    kmax[a] = mono_key(Mo.umax[a]);
+  }
   F xv[NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
@@ -438,6 +457,8 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
         for (int c = 0; c < NX; ++c) acc = fma(A.C(t, CL::K + a * NX + c), xv[c], acc);
         uv[a] = acc;
+        const unsigned long long ku = mono_key(acc);
+        o.out |= (ku < kmin[a]) | (ku > kmax[a]);
       }
     }
     F xn[NX];
@@ -450,42 +471,30 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
       for (int c = 0; c < NU; ++c) acc = fma(Mo.B[r][c], uv[c], acc);
       xn[r] = acc;
     }
-    F lam[NX];
+    if (mask) {
+      F lam[NX];
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      F acc = A.C(t + 1, CL::p + r);
+      for (int r = 0; r < NX; ++r) {
+        F acc = A.C(t + 1, CL::p + r);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) acc = fma(A.C(t + 1, CL::P + r * NX + c), xn[c], acc);
-      lam[r] = acc;
-    }
+        for (int c = 0; c < NX; ++c) acc = fma(A.C(t + 1, CL::P + r * NX + c), xn[c], acc);
+        lam[r] = acc;
+      }
 #pragma unroll
-    for (int a = 0; a < NU; ++a) {
-      const int idx = t * NU + a;
-      if (mask & (0x101u << a)) {
+      for (int a = 0; a < NU; ++a) {
+        if (!(mask & (0x101u << a))) continue;
         F g = A.rbar[a] * uv[a];
 #pragma unroll
         for (int r = 0; r < NX; ++r) g = fma(Mo.B[r][a], lam[r], g);
         const F mu = (mask & (1u << a)) ? g : -g;
         const F am = fabs_(mu);
         if (am > o.scale) o.scale = am;
-        if (mu < o.worst) { o.worst = mu; o.widx = idx; }
+        if (mu < o.worst) { o.worst = mu; o.widx = t * NU + a; }
         if (!(am == am)) o.bad = 1;
-      } else {
-        // ratio test: step p = us - u, blocking ratio num / den with den > 0
-        const F cu = A.u(t, a);
-        const F p = uv[a] - cu;
-        F num = 0, den = 0;
-        int side = 0;
-        if (p < F(0)) { num = cu - Mo.umin[a]; den = -p; side = 1; }
-        else if (p > F(0)) { num = Mo.umax[a] - cu; den = p; side = 2; }
-        if (side) {
-          if (num < F(0)) num = 0;
-          // num/den < anum/aden  <=>  num*aden < anum*den (both denominators > 0)
-          if (num * o.aden < o.anum * den) { o.anum = num; o.aden = den; o.blk = idx; o.bside = side; }
-        }
       }
-      A.us(t, a) = uv[a];
     }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) A.us(t, a) = uv[a];
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
       A.x(t + 1, r) = xn[r];
@@ -496,6 +505,31 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
   for (int r = 0; r < NX; ++r)
     if (!(xv[r] == xv[r]) || fabs_(xv[r]) > F(1e30)) o.bad = 1;
   return o;
+}
+
+// Ratio test of the primal active set (Nocedal & Wright Alg. 16.3) for the step
+// p = us - u over the free inputs: smallest blocking ratio (clamped at 0), ties
+// to the lowest (t, c) index, ratios compared as num*aden < anum*den.
+template <typename F, int NX, int NU, int DP>
+__device__ void ratio_test(const AgentCtx<F, NX, NU, DP>& A, EqpScan<F>& o) {
+  const Model<F, NX, NU>& Mo = *A.M;
+  for (int t = 0; t < A.T; ++t) {
+    const uint16_t mask = A.W(t);
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      if (mask & (0x101u << a)) continue;
+      const F cu = A.u(t, a);
+      const F p = A.us(t, a) - cu;
+      F num = 0, den = 0;
+      int side = 0;
+      if (p < F(0)) { num = cu - Mo.umin[a]; den = -p; side = 1; }
+      else if (p > F(0)) { num = Mo.umax[a] - cu; den = p; side = 2; }
+      if (side) {
+        if (num < F(0)) num = 0;
+        if (num * o.aden < o.anum * den) { o.anum = num; o.aden = den; o.blk = t * NU + a; o.bside = side; }
+      }
+    }
+  }
 }
 
 // Box-constrained local QP of agent i (Sec. IV.A) by the primal active-set
@@ -556,6 +590,7 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, i
       o = eqp_solve<F, NX, NU, DP>(A, dirty, nfact);
       if (o.bad) return ST_NUMERIC;
       dirty = -1;
+      if (o.out) ratio_test<F, NX, NU, DP>(A, o);
       if (o.blk >= 0) {
         const F alpha = o.anum / o.aden;
         for (int t = 0; t < T; ++t)
@@ -585,7 +620,6 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, i
     return ST_CONVERGED;
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Scenario-level phases
@@ -618,11 +652,9 @@ __device__ void init_phase(const Dev<F>& D, const ScenMeta& s, int64_t t0, int64
     D.Wm[s.as_off + idx] = 0;
     D.Cm[s.as_off + idx] = 0xFFFF;
   }
-  F* th0 = D.theta + s.ps_off;
-  F* th1 = D.theta + D.tot_ps + s.ps_off;
-  for (int64_t q = t0; q < (int64_t)P * T; q += stride) {
-    th0[q] = 0;
-    th1[q] = 0;
+  for (int l = 0; l < 3; ++l) {
+    F* th = D.theta + (size_t)l * D.tot_ps + s.ps_off;
+    for (int64_t q = t0; q < (int64_t)P * T; q += stride) th[q] = 0;
   }
 }
 
@@ -681,20 +713,18 @@ __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const S
   return st;
 }
 
-// Consensus projection + scaled dual update in theta form, residual maxima.
-// theta^{k+1} = max(0, theta^k + (d - a'(p_i - p_j)) / 2); the dual copies are
-// y_i = -theta a, y_j = +theta a; r = |theta^{k+1} - theta^k| max|a_c|;
-// s/rho = |Delta p +- (theta^{k+1} - 2 theta^k + theta^{k-1}) a|.
-// theta^{k-1} is read from the other level and overwritten with theta^{k+1}.
+// Consensus projection + scaled dual update in theta form and the primal
+// residual.  theta^{k+1} = max(0, theta^k + (d - a'(p_i - p_j)) / 2); the dual
+// copies are y_i = -theta a, y_j = +theta a; r = |theta^{k+1} - theta^k| max|a_c|.
+// X level xl holds p^k, xl^1 holds p^{k+1}; theta slots tk -> tkp1.
 template <typename F, int NX, int NU, int DP>
-__device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int cur, int64_t q0, int64_t stride,
-                           unsigned long long& rb, unsigned long long& sb) {
+__device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tk, int tkp1, int64_t q0,
+                           int64_t stride, unsigned long long& rb) {
   const int N = s.N, P = s.P;
   const int64_t PT = (int64_t)P * s.T;
-  const F* Xn = D.X + (size_t)(cur ^ 1) * D.tot_xs * NX + s.xs_off * NX;
-  const F* Xc = D.X + (size_t)cur * D.tot_xs * NX + s.xs_off * NX;
-  const F* thc = D.theta + (size_t)cur * D.tot_ps + s.ps_off;
-  F* tho = D.theta + (size_t)(cur ^ 1) * D.tot_ps + s.ps_off;
+  const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+  const F* thk = D.theta + (size_t)tk * D.tot_ps + s.ps_off;
+  F* thn = D.theta + (size_t)tkp1 * D.tot_ps + s.ps_off;
   const F* a = D.a + s.ps_off * DP;
   const int32_t* pr = D.pairs + s.pair_off;
   const F d = F(s.d);
@@ -703,35 +733,55 @@ __device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int cur, int64_t 
     const int pair = (int)(q - (int64_t)tm1 * P);
     const int pk = pr[pair];
     const int i = pk & 0xFFFF, j = pk >> 16;
-    F av[DP], dpi[DP], dpj[DP];
-    F sdot = 0, amax = 0;
+    F sdot = 0;
+    unsigned long long amax = 0;
 #pragma unroll
     for (int c = 0; c < DP; ++c) {
-      av[c] = a[((size_t)tm1 * DP + c) * P + pair];
-      const size_t oi = ((size_t)(tm1 + 1) * NX + c) * N + i;
-      const size_t oj = ((size_t)(tm1 + 1) * NX + c) * N + j;
-      const F pi = Xn[oi], pj = Xn[oj];
-      dpi[c] = pi - Xc[oi];
-      dpj[c] = pj - Xc[oj];
-      sdot = fma(av[c], pi - pj, sdot);
-      const F aa = fabs_(av[c]);
-      amax = aa > amax ? aa : amax;
+      const F av = a[((size_t)tm1 * DP + c) * P + pair];
+      const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
+      sdot = fma(av, Xn[ro + i] - Xn[ro + j], sdot);
+      const unsigned long long ab = abs_bits(av);
+      amax = ab > amax ? ab : amax;
     }
-    const F th = thc[q], thp = tho[q];
+    const F th = thk[q];
     F tn = fma(d - sdot, F(0.5), th);
-    if (tn < F(0)) tn = 0;
-    const F dth = tn - th;
-    const F e2 = dth - (th - thp);
-    unsigned long long v = ord_bits(fabs_(dth) * amax);
+    if (sign_set(tn)) tn = F(0);
+    thn[q] = tn;
+    const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
     rb = v > rb ? v : rb;
+  }
+}
+
+// Dual residual s / rho = max |Delta p +- (theta^{k+1} - 2 theta^k + theta^{k-1}) a|
+// over pairs, steps, sides and components (the change of the consensus copies).
+template <typename F, int NX, int NU, int DP>
+__device__ void dual_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tkm1, int tk, int tkp1, int64_t q0,
+                           int64_t stride, unsigned long long& sb) {
+  const int N = s.N, P = s.P;
+  const int64_t PT = (int64_t)P * s.T;
+  const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+  const F* Xc = D.X + (size_t)xl * D.tot_xs * NX + s.xs_off * NX;
+  const F* thm = D.theta + (size_t)tkm1 * D.tot_ps + s.ps_off;
+  const F* thk = D.theta + (size_t)tk * D.tot_ps + s.ps_off;
+  const F* thn = D.theta + (size_t)tkp1 * D.tot_ps + s.ps_off;
+  const F* a = D.a + s.ps_off * DP;
+  const int32_t* pr = D.pairs + s.pair_off;
+  for (int64_t q = q0; q < PT; q += stride) {
+    const int tm1 = (int)(q / P);
+    const int pair = (int)(q - (int64_t)tm1 * P);
+    const int pk = pr[pair];
+    const int i = pk & 0xFFFF, j = pk >> 16;
+    const F th = thk[q];
+    const F e2 = (thn[q] - th) - (th - thm[q]);
 #pragma unroll
     for (int c = 0; c < DP; ++c) {
-      v = ord_bits(fabs_(fma(e2, av[c], dpi[c])));
-      sb = v > sb ? v : sb;
-      v = ord_bits(fabs_(fma(-e2, av[c], dpj[c])));
-      sb = v > sb ? v : sb;
+      const F av = a[((size_t)tm1 * DP + c) * P + pair];
+      const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
+      const unsigned long long v1 = abs_bits(fma(e2, av, Xn[ro + i] - Xc[ro + i]));
+      const unsigned long long v2 = abs_bits(fma(-e2, av, Xn[ro + j] - Xc[ro + j]));
+      sb = v1 > sb ? v1 : sb;
+      sb = v2 > sb ? v2 : sb;
     }
-    tho[q] = tn;
   }
 }
 
@@ -739,11 +789,12 @@ __device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int cur, int64_t 
 // h_it = sum_{j != i} (w_i - y_i) = n_c p_it + sum_j sigma_ij (2 theta^{k+1} - theta^k) a_ijt,
 // sigma = +1 when i is the first agent of the pair, -1 otherwise.
 template <typename F, int NX, int NU, int DP>
-__device__ void gather_phase(const Dev<F>& D, const ScenMeta& s, int lvl_new, int64_t t0, int64_t stride) {
+__device__ void gather_phase(const Dev<F>& D, const ScenMeta& s, int xl_new, int tkp1, int tk, int64_t t0,
+                             int64_t stride) {
   const int N = s.N, P = s.P;
-  const F* Xn = D.X + (size_t)lvl_new * D.tot_xs * NX + s.xs_off * NX;
-  const F* thn = D.theta + (size_t)lvl_new * D.tot_ps + s.ps_off;
-  const F* tho = D.theta + (size_t)(lvl_new ^ 1) * D.tot_ps + s.ps_off;
+  const F* Xn = D.X + (size_t)xl_new * D.tot_xs * NX + s.xs_off * NX;
+  const F* thn = D.theta + (size_t)tkp1 * D.tot_ps + s.ps_off;
+  const F* tho = D.theta + (size_t)tk * D.tot_ps + s.ps_off;
   const F* a = D.a + s.ps_off * DP;
   F* h = D.h + s.as_off * DP;
   const F nc = F(N - 1);
@@ -767,27 +818,87 @@ __device__ void gather_phase(const Dev<F>& D, const ScenMeta& s, int lvl_new, in
   }
 }
 
-// Maximum of two non-negative bit-ordered values over the CTA; every thread
+// Maximum of a non-negative bit-ordered value over the CTA; every thread
 // receives the result.  Contains two barriers.
-__device__ __forceinline__ void block_max2(unsigned long long& a, unsigned long long& b,
-                                           unsigned long long (*red)[32]) {
+__device__ __forceinline__ unsigned long long block_max1(unsigned long long a, unsigned long long* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, o);
-    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
     a = oa > a ? oa : a;
-    b = ob > b ? ob : b;
   }
   const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  if ((threadIdx.x & 31) == 0) { red[0][w] = a; red[1][w] = b; }
+  if ((threadIdx.x & 31) == 0) red[w] = a;
   __syncthreads();
   a = 0;
-  b = 0;
-  for (int k = 0; k < nw; ++k) {
-    a = red[0][k] > a ? red[0][k] : a;
-    b = red[1][k] > b ? red[1][k] : b;
-  }
+  for (int k = 0; k < nw; ++k) a = red[k] > a ? red[k] : a;
   __syncthreads();
+  return a;
+}
+
+// Shared-memory scratch of one scenario CTA.
+struct CtaScratch {
+  unsigned long long red[32];
+  unsigned long long cnt[2];
+  int flag;
+};
+
+// Every ADMM iteration of scenario `sc` on one CTA (Sec. III.B): x-update of
+// all agents, consensus/dual update with the primal residual, the dual residual
+// when the primal test passes (or on the last iteration), convergence test,
+// then the aggregate coupling term of the next x-update.  Writes status,
+// iterations, residuals, work counters and the levels of the final iterate.
+template <typename F, int NX, int NU, int DP>
+__device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, int sc,
+                             CtaScratch& cs) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    cs.flag = 0;
+    cs.cnt[0] = 0;
+    cs.cnt[1] = 0;
+  }
+  init_phase<F, NX, NU, DP>(D, s, tid, nt);
+  __syncthreads();
+  int xl = 0, status = ST_NOT_CONVERGED, iters = 0, tfin = 0;
+  F r = F(0), sres = F(0);
+  unsigned long long neqp = 0, nfact = 0;
+  for (int k = 0; k < D.max_iter; ++k) {
+    const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
+    const int st = xupdate_phase<F, NX, NU, DP>(D, M, s, k, xl ^ 1, tid, nt, neqp, nfact);
+    if (st) atomicMax(&cs.flag, st);
+    __syncthreads();
+    iters = k + 1;
+    const int flag = cs.flag;
+    if (flag) { status = flag; tfin = tk; break; }
+    unsigned long long rb = 0;
+    pair_phase<F, NX, NU, DP>(D, s, xl, tk, tkp1, tid, nt, rb);
+    r = from_bits(block_max1(rb, cs.red), F(0));
+    tfin = tkp1;
+    if (!finite_(r)) { status = ST_NUMERIC; xl ^= 1; break; }
+    const bool last = (k + 1 == D.max_iter);
+    if (r <= F(D.tol) || last) {
+      unsigned long long sb = 0;
+      dual_phase<F, NX, NU, DP>(D, s, xl, tkm1, tk, tkp1, tid, nt, sb);
+      sres = F(s.rho) * from_bits(block_max1(sb, cs.red), F(0));
+      if (!finite_(sres)) { status = ST_NUMERIC; xl ^= 1; break; }
+      if (r <= F(D.tol) && sres <= F(D.tol)) { status = ST_CONVERGED; xl ^= 1; break; }
+      if (last) { xl ^= 1; break; }
+    }
+    gather_phase<F, NX, NU, DP>(D, s, xl ^ 1, tkp1, tk, tid, nt);
+    __syncthreads();
+    xl ^= 1;
+  }
+  if (neqp) atomicAdd(&cs.cnt[0], neqp);
+  if (nfact) atomicAdd(&cs.cnt[1], nfact);
+  __syncthreads();
+  if (tid == 0) {
+    D.status[sc] = status;
+    D.iters[sc] = iters;
+    D.cur_lvl[sc] = xl | (tfin << 1);
+    D.res[2 * sc] = double(r);
+    D.res[2 * sc + 1] = double(sres);
+    D.eqp[sc] = cs.cnt[0];
+    D.fact[sc] = cs.cnt[1];
+  }
 }
 
 }  // namespace tadmm

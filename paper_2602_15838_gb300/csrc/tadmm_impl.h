@@ -63,11 +63,11 @@ struct tadmm_handle {
   void* pinned = nullptr;                // host pinned readback buffer
 
   // batched mode launch shape and captured graph
-  int tpc = 0, cps = 0;
+  int tpc = 0, cps = 0, variant = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   double g_tol = -1.0;
-  int g_iter = -1, g_tpc = -1, g_cps = -1;
+  int g_iter = -1, g_tpc = -1, g_cps = -1, g_var = -1;
   int solved = 0;
   int64_t launches = 0;   // kernel launches enqueued by the last solve
 };
@@ -84,7 +84,7 @@ struct Impl {
   static int solve_plain(tadmm_handle* h, double tol, int max_iter, cudaStream_t st);
   static int export_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W,
                              cudaStream_t st);
-  static int max_ctas_per_sm(int tpc);
+  static int max_ctas_per_sm(int tpc, int variant);
 };
 
 }  // namespace tadmm

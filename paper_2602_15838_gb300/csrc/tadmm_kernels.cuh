@@ -14,63 +14,31 @@ namespace tadmm {
 // a work queue (largest estimated work first) and runs every ADMM iteration of
 // it on-chip, phases separated by CTA barriers.
 // ---------------------------------------------------------------------------
-template <typename F, int NX, int NU, int DP>
-__global__ void __launch_bounds__(256) k_batched(Dev<F> D) {
+// Register-budget variants of the persistent kernel (chosen by the autotuner):
+// (max threads per CTA, min resident CTAs per SM) for __launch_bounds__.
+template <int V> struct KVariant;
+template <> struct KVariant<0> { static constexpr int maxt = 256, minb = 1; };
+template <> struct KVariant<1> { static constexpr int maxt = 32, minb = 12; };
+template <> struct KVariant<2> { static constexpr int maxt = 32, minb = 16; };
+template <> struct KVariant<3> { static constexpr int maxt = 32, minb = 24; };
+template <> struct KVariant<4> { static constexpr int maxt = 64, minb = 8; };
+constexpr int kNumVariants = 5;
+
+template <typename F, int NX, int NU, int DP, int V>
+__global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batched(Dev<F> D) {
   __shared__ Model<F, NX, NU> M;
-  __shared__ unsigned long long red[2][32];
-  __shared__ unsigned long long cnt[2];
+  __shared__ CtaScratch cs;
   __shared__ int s_q;
-  __shared__ int s_flag;
   load_model<F, NX, NU>(M, D.model);
-  const int tid = threadIdx.x, nt = blockDim.x;
   for (;;) {
     __syncthreads();
-    if (tid == 0) {
-      s_q = atomicAdd(D.queue, 1);
-      s_flag = 0;
-      cnt[0] = 0;
-      cnt[1] = 0;
-    }
+    if (threadIdx.x == 0) s_q = atomicAdd(D.queue, 1);
     __syncthreads();
     const int qi = s_q;
     if (qi >= D.n_scen) return;
     const int sc = D.order[qi];
     const ScenMeta s = D.meta[sc];
-    init_phase<F, NX, NU, DP>(D, s, tid, nt);
-    __syncthreads();
-    int cur = 0, status = ST_NOT_CONVERGED, iters = 0;
-    F r = F(0), sres = F(0);
-    unsigned long long neqp = 0, nfact = 0;
-    for (int k = 0; k < D.max_iter; ++k) {
-      const int st = xupdate_phase<F, NX, NU, DP>(D, M, s, k, cur ^ 1, tid, nt, neqp, nfact);
-      if (st) atomicMax(&s_flag, st);
-      __syncthreads();
-      iters = k + 1;
-      const int flag = s_flag;
-      if (flag) { status = flag; break; }
-      unsigned long long rb = 0, sb = 0;
-      pair_phase<F, NX, NU, DP>(D, s, cur, tid, nt, rb, sb);
-      block_max2(rb, sb, red);
-      r = from_bits(rb, F(0));
-      sres = F(s.rho) * from_bits(sb, F(0));
-      if (!finite_(r) || !finite_(sres)) { status = ST_NUMERIC; cur ^= 1; break; }
-      if (r <= F(D.tol) && sres <= F(D.tol)) { status = ST_CONVERGED; cur ^= 1; break; }
-      gather_phase<F, NX, NU, DP>(D, s, cur ^ 1, tid, nt);
-      __syncthreads();
-      cur ^= 1;
-    }
-    if (neqp) atomicAdd(&cnt[0], neqp);
-    if (nfact) atomicAdd(&cnt[1], nfact);
-    __syncthreads();
-    if (tid == 0) {
-      D.status[sc] = status;
-      D.iters[sc] = iters;
-      D.cur_lvl[sc] = cur;
-      D.res[2 * sc] = double(r);
-      D.res[2 * sc + 1] = double(sres);
-      D.eqp[sc] = cnt[0];
-      D.fact[sc] = cnt[1];
-    }
+    run_scenario<F, NX, NU, DP>(D, M, s, sc, cs);
   }
 }
 
@@ -104,23 +72,32 @@ __global__ void __launch_bounds__(128) k_xupdate(Dev<F> D, int sc, int k, int lv
 }
 
 template <typename F, int NX, int NU, int DP>
-__global__ void __launch_bounds__(256) k_pair(Dev<F> D, int sc, int cur, unsigned long long* red2) {
-  __shared__ unsigned long long red[2][32];
+__global__ void __launch_bounds__(256) k_pair(Dev<F> D, int sc, int xl, int tk, int tkp1, unsigned long long* red1) {
+  __shared__ unsigned long long red[32];
   const ScenMeta s = D.meta[sc];
-  unsigned long long rb = 0, sb = 0;
-  pair_phase<F, NX, NU, DP>(D, s, cur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                            (int64_t)gridDim.x * blockDim.x, rb, sb);
-  block_max2(rb, sb, red);
-  if (threadIdx.x == 0) {
-    if (rb) atomicMax(&red2[0], rb);
-    if (sb) atomicMax(&red2[1], sb);
-  }
+  unsigned long long rb = 0;
+  pair_phase<F, NX, NU, DP>(D, s, xl, tk, tkp1, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                            (int64_t)gridDim.x * blockDim.x, rb);
+  rb = block_max1(rb, red);
+  if (threadIdx.x == 0 && rb) atomicMax(red1, rb);
 }
 
 template <typename F, int NX, int NU, int DP>
-__global__ void k_gather(Dev<F> D, int sc, int lvl_new) {
+__global__ void __launch_bounds__(256) k_dual(Dev<F> D, int sc, int xl, int tkm1, int tk, int tkp1,
+                                              unsigned long long* red1) {
+  __shared__ unsigned long long red[32];
   const ScenMeta s = D.meta[sc];
-  gather_phase<F, NX, NU, DP>(D, s, lvl_new, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+  unsigned long long sb = 0;
+  dual_phase<F, NX, NU, DP>(D, s, xl, tkm1, tk, tkp1, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                            (int64_t)gridDim.x * blockDim.x, sb);
+  sb = block_max1(sb, red);
+  if (threadIdx.x == 0 && sb) atomicMax(red1, sb);
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void k_gather(Dev<F> D, int sc, int xl_new, int tkp1, int tk) {
+  const ScenMeta s = D.meta[sc];
+  gather_phase<F, NX, NU, DP>(D, s, xl_new, tkp1, tk, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                               (int64_t)gridDim.x * blockDim.x);
 }
 
@@ -180,7 +157,7 @@ __global__ void k_export_agents(Dev<F> D, const int32_t* __restrict__ agent_scen
     const int sc = agent_scen[ga];
     const ScenMeta s = D.meta[sc];
     const int i = (int)(ga - s.agent_off), N = s.N, T = s.T;
-    const F* Xl = D.X + (size_t)D.cur_lvl[sc] * D.tot_xs * NX + s.xs_off * NX;
+    const F* Xl = D.X + (size_t)(D.cur_lvl[sc] & 1) * D.tot_xs * NX + s.xs_off * NX;
     if (X)
       for (int t = 0; t <= T; ++t)
 #pragma unroll
@@ -205,7 +182,7 @@ __global__ void k_export_theta(Dev<F> D, const int32_t* __restrict__ pair_scen, 
     const int sc = pair_scen[gp];
     const ScenMeta s = D.meta[sc];
     const int lp = (int)(gp - s.pair_off);
-    const F* tl = D.theta + (size_t)D.cur_lvl[sc] * D.tot_ps + s.ps_off;
+    const F* tl = D.theta + (size_t)(D.cur_lvl[sc] >> 1) * D.tot_ps + s.ps_off;
     for (int t = 0; t < s.T; ++t) th[s.ps_off + (int64_t)lp * s.T + t] = double(tl[(size_t)t * s.P + lp]);
   }
 }
@@ -277,20 +254,47 @@ int Impl<F, NX, NU, DP>::import_inputs(tadmm_handle* h, cudaStream_t st) {
 }
 
 template <typename F, int NX, int NU, int DP>
-int Impl<F, NX, NU, DP>::max_ctas_per_sm(int tpc) {
+static const void* batched_kernel(int v) {
+  switch (v) {
+    case 1: return (const void*)k_batched<F, NX, NU, DP, 1>;
+    case 2: return (const void*)k_batched<F, NX, NU, DP, 2>;
+    case 3: return (const void*)k_batched<F, NX, NU, DP, 3>;
+    case 4: return (const void*)k_batched<F, NX, NU, DP, 4>;
+    default: return (const void*)k_batched<F, NX, NU, DP, 0>;
+  }
+}
+
+static int variant_maxt(int v) {
+  switch (v) {
+    case 1: return KVariant<1>::maxt;
+    case 2: return KVariant<2>::maxt;
+    case 3: return KVariant<3>::maxt;
+    case 4: return KVariant<4>::maxt;
+    default: return KVariant<0>::maxt;
+  }
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::max_ctas_per_sm(int tpc, int variant) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<F, NX, NU, DP>, tpc, 0) != cudaSuccess)
-    return 1;
-  return n < 1 ? 1 : n;
+  if (tpc > variant_maxt(variant)) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<F, NX, NU, DP>(variant), tpc, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 template <typename F, int NX, int NU, int DP>
 int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter, cudaStream_t st) {
-  int tpc = h->tpc > 0 ? h->tpc : 128;
-  int cps = h->cps > 0 ? h->cps : max_ctas_per_sm(tpc);
-  cps = std::min(cps, max_ctas_per_sm(tpc));
+  const int var = (h->variant >= 0 && h->variant < kNumVariants) ? h->variant : 0;
+  int tpc = h->tpc > 0 ? h->tpc : std::min(128, variant_maxt(var));
+  const int occ = max_ctas_per_sm(tpc, var);
+  if (occ < 1) return set_error(TADMM_EINVAL, "launch shape does not fit the kernel variant");
+  int cps = h->cps > 0 ? std::min(h->cps, occ) : occ;
   const int grid = std::max(1, std::min(h->n_scen, h->sm_count * cps));
-  if (!h->gexec || h->g_tol != tol || h->g_iter != max_iter || h->g_tpc != tpc || h->g_cps != cps) {
+  if (!h->gexec || h->g_tol != tol || h->g_iter != max_iter || h->g_tpc != tpc || h->g_cps != cps ||
+      h->g_var != var) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
       h->gexec = nullptr;
@@ -302,7 +306,8 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
     int rc = cuda_check(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (rc) return rc;
     cudaMemsetAsync(h->queue, 0, sizeof(int32_t), h->cap_stream);
-    k_batched<F, NX, NU, DP><<<grid, tpc, 0, h->cap_stream>>>(D);
+    void* args[] = {&D};
+    cudaLaunchKernel(batched_kernel<F, NX, NU, DP>(var), dim3(grid), dim3(tpc), args, 0, h->cap_stream);
     cudaError_t le = cudaGetLastError();
     cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_check(le, "batched kernel launch"); }
@@ -314,6 +319,7 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
     h->g_iter = max_iter;
     h->g_tpc = tpc;
     h->g_cps = cps;
+    h->g_var = var;
   }
   h->launches = 1;
   return cuda_check(cudaGraphLaunch(h->gexec, st), "graph launch");
@@ -331,45 +337,56 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
     const int64_t PT = (int64_t)s.P * s.T, NT = (int64_t)s.N * s.T;
     k_init<F, NX, NU, DP><<<grid_for(std::max(PT, NT), 256, 4096), 256, 0, st>>>(D, sc);
     ++launches;
-    int cur = 0, status = ST_NOT_CONVERGED, iters = 0;
+    int xl = 0, status = ST_NOT_CONVERGED, iters = 0, tfin = 0;
     double r = 0, sres = 0;
+    auto read_bits = [&](unsigned long long b, double rho_scale) -> double {
+      if (sizeof(F) == 8) {
+        double v;
+        std::memcpy(&v, &b, 8);
+        return rho_scale * v;
+      }
+      float v;
+      const uint32_t b32 = (uint32_t)b;
+      std::memcpy(&v, &b32, 4);
+      return double(float(rho_scale) * v);
+    };
     for (int k = 0; k < max_iter; ++k) {
+      const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
       cudaMemsetAsync(h->flag, 0, sizeof(int32_t), st);
       cudaMemsetAsync(h->red2, 0, 2 * sizeof(unsigned long long), st);
-      k_xupdate<F, NX, NU, DP><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, cur ^ 1, h->flag);
-      k_pair<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, cur, h->red2);
+      k_xupdate<F, NX, NU, DP><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
+      k_pair<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, xl, tk, tkp1, h->red2);
       launches += 2;
       cudaMemcpyAsync(hb, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(hb + 1, h->red2, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(hb + 1, h->red2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
       int rc = cuda_check(cudaStreamSynchronize(st), "plain-mode residual readback");
       if (rc) return rc;
       iters = k + 1;
       const int flag = (int)(*(int32_t*)hb);
-      if (flag) { status = flag; break; }
-      if (sizeof(F) == 8) {
-        double rv, sv;
-        std::memcpy(&rv, &hb[1], 8);
-        std::memcpy(&sv, &hb[2], 8);
-        r = rv;
-        sres = s.rho * sv;
-        // the residual test is taken in the arithmetic type F
-        if (!std::isfinite(r) || !std::isfinite(sres)) { status = ST_NUMERIC; cur ^= 1; break; }
-        if (r <= tol && sres <= tol) { status = ST_CONVERGED; cur ^= 1; break; }
-      } else {
-        float rv, sv;
-        uint32_t rbits = (uint32_t)hb[1], sbits = (uint32_t)hb[2];
-        std::memcpy(&rv, &rbits, 4);
-        std::memcpy(&sv, &sbits, 4);
-        const float sf = float(s.rho) * sv;
-        r = rv;
-        sres = sf;
-        if (!std::isfinite(rv) || !std::isfinite(sf)) { status = ST_NUMERIC; cur ^= 1; break; }
-        if (rv <= float(tol) && sf <= float(tol)) { status = ST_CONVERGED; cur ^= 1; break; }
+      if (flag) { status = flag; tfin = tk; break; }
+      // the residual tests are taken in the arithmetic type F
+      r = read_bits(hb[1], 1.0);
+      tfin = tkp1;
+      if (!std::isfinite(r)) { status = ST_NUMERIC; xl ^= 1; break; }
+      const bool last = (k + 1 == max_iter);
+      const bool r_ok = (sizeof(F) == 8) ? (r <= tol) : (float(r) <= float(tol));
+      if (r_ok || last) {
+        k_dual<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, xl, tkm1, tk, tkp1,
+                                                                                h->red2 + 1);
+        ++launches;
+        cudaMemcpyAsync(hb + 2, h->red2 + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if ((rc = cuda_check(cudaStreamSynchronize(st), "plain-mode dual residual readback"))) return rc;
+        sres = read_bits(hb[2], s.rho);
+        if (!std::isfinite(sres)) { status = ST_NUMERIC; xl ^= 1; break; }
+        const bool s_ok = (sizeof(F) == 8) ? (sres <= tol) : (float(sres) <= float(tol));
+        if (r_ok && s_ok) { status = ST_CONVERGED; xl ^= 1; break; }
+        if (last) { xl ^= 1; break; }
       }
-      k_gather<F, NX, NU, DP><<<grid_for(NT, 128, h->sm_count * 8), 128, 0, st>>>(D, sc, cur ^ 1);
+      k_gather<F, NX, NU, DP><<<grid_for(NT, 128, h->sm_count * 8), 128, 0, st>>>(D, sc, xl ^ 1, tkp1, tk);
       ++launches;
-      cur ^= 1;
+      xl ^= 1;
     }
+    const int cur = xl | (tfin << 1);
     k_finish<F><<<1, 1, 0, st>>>(D, sc, status, iters, cur, r, sres);
     ++launches;
   }

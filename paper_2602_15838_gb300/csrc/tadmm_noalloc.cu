@@ -95,48 +95,11 @@ __global__ void k_noalloc_setup(ScenMeta* meta, int32_t* order, int32_t* pairs, 
 template <typename F, int NX, int NU, int DP>
 __global__ void __launch_bounds__(256) k_noalloc_solve(Dev<F> D) {
   __shared__ Model<F, NX, NU> M;
-  __shared__ unsigned long long red[2][32];
-  __shared__ unsigned long long cnt[2];
-  __shared__ int s_flag;
+  __shared__ CtaScratch cs;
   load_model<F, NX, NU>(M, D.model);
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) { s_flag = 0; cnt[0] = 0; cnt[1] = 0; }
+  __syncthreads();
   const ScenMeta s = D.meta[0];
-  init_phase<F, NX, NU, DP>(D, s, tid, nt);
-  __syncthreads();
-  int cur = 0, status = ST_NOT_CONVERGED, iters = 0;
-  F r = F(0), sres = F(0);
-  unsigned long long neqp = 0, nfact = 0;
-  for (int k = 0; k < D.max_iter; ++k) {
-    const int st = xupdate_phase<F, NX, NU, DP>(D, M, s, k, cur ^ 1, tid, nt, neqp, nfact);
-    if (st) atomicMax(&s_flag, st);
-    __syncthreads();
-    iters = k + 1;
-    const int flag = s_flag;
-    if (flag) { status = flag; break; }
-    unsigned long long rb = 0, sb = 0;
-    pair_phase<F, NX, NU, DP>(D, s, cur, tid, nt, rb, sb);
-    block_max2(rb, sb, red);
-    r = from_bits(rb, F(0));
-    sres = F(s.rho) * from_bits(sb, F(0));
-    if (!finite_(r) || !finite_(sres)) { status = ST_NUMERIC; cur ^= 1; break; }
-    if (r <= F(D.tol) && sres <= F(D.tol)) { status = ST_CONVERGED; cur ^= 1; break; }
-    gather_phase<F, NX, NU, DP>(D, s, cur ^ 1, tid, nt);
-    __syncthreads();
-    cur ^= 1;
-  }
-  if (neqp) atomicAdd(&cnt[0], neqp);
-  if (nfact) atomicAdd(&cnt[1], nfact);
-  __syncthreads();
-  if (tid == 0) {
-    D.status[0] = status;
-    D.iters[0] = iters;
-    D.cur_lvl[0] = cur;
-    D.res[0] = double(r);
-    D.res[1] = double(sres);
-    D.eqp[0] = cnt[0];
-    D.fact[0] = cnt[1];
-  }
+  run_scenario<F, NX, NU, DP>(D, M, s, 0, cs);
 }
 
 __global__ void k_noalloc_results(const int32_t* status, const int32_t* iters, const double* res,
@@ -189,7 +152,7 @@ static int noalloc_run(const tadmm_scenario_dev* sc, int start_mode, double tol,
     F* x_ref = cv.take<F>(sizeof(F) * N * NX);
     F* a = cv.take<F>(sizeof(F) * PT * DP);
     F* w0 = cv.take<F>(sizeof(F) * NT * DP);
-    F* th = cv.take<F>(sizeof(F) * 2 * PT);
+    F* th = cv.take<F>(sizeof(F) * 3 * PT);
     F* Xs = cv.take<F>(sizeof(F) * 2 * XS * NX);
     F* h = cv.take<F>(sizeof(F) * NT * DP);
     F* Us = cv.take<F>(sizeof(F) * NT * NU);
