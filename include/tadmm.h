@@ -91,9 +91,14 @@ typedef struct {
   int32_t mode;            /* TADMM_MODE_* */
   int32_t threads_per_cta; /* batched mode: threads per scenario CTA; 0 = tuned/default */
   int32_t ctas_per_sm;     /* batched mode: resident CTAs per SM; 0 = tuned/default */
-  int32_t kernel_variant;  /* batched mode: register-budget variant 0..4 of the persistent kernel
-                              (0: no cap; 1: 32 thr x 12 CTAs; 2: 32 x 16; 3: 32 x 24; 4: 64 x 8) */
+  int32_t kernel_variant;  /* batched mode: register-budget variant 0..2 of the persistent kernel
+                              (0: no cap; 1: 32 threads x 12 CTAs/SM; 2: 64 threads x 8 CTAs/SM) */
+  int32_t flags;           /* TADMM_FLAG_* bits; 0 = all optimizations on */
 } tadmm_options;
+
+/* option flags (results are the same either way; for testing and measurement) */
+#define TADMM_FLAG_NO_FUSED_PAIR_GATHER 1 /* separate pair and gather sweeps in the batched kernel */
+#define TADMM_FLAG_NO_STRUCTURE 2         /* dense A, B products even for a double integrator */
 
 typedef struct tadmm_handle tadmm_handle;
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtadmm.so")
 OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4
 CONVERGED, NOT_CONVERGED, QP_FAIL, NUMERIC = 0, 1, 2, 3
 START = {"cold": 0, "hot": 1, "turbo": 2}
+FLAG_NO_FUSED_PAIR_GATHER, FLAG_NO_STRUCTURE = 1, 2
 MODE = {"batched": 0, "plain": 1}
 
 _dp = C.POINTER(C.c_double)
@@ -36,7 +37,7 @@ class TadmmBatch(C.Structure):
 class TadmmOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("start_mode", C.c_int32), ("as_max", C.c_int32),
                 ("eps_rel", C.c_double), ("mode", C.c_int32), ("threads_per_cta", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("kernel_variant", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("kernel_variant", C.c_int32), ("flags", C.c_int32)]
 
 
 class TadmmError(RuntimeError):
@@ -117,7 +118,7 @@ class Solver:
 
     def __init__(self, batch, precision: int = 64, start: str = "turbo", mode: str = "batched",
                  as_max: int = 0, eps_rel: float = 0.0, threads_per_cta: int = 0, ctas_per_sm: int = 0,
-                 kernel_variant: int = 0):
+                 kernel_variant: int = 0, flags: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise TadmmError("no CUDA device: the solver has no CPU path")
@@ -125,7 +126,7 @@ class Solver:
         self.precision = precision
         self._hb = _HostBatch(batch)
         opt = TadmmOptions(precision, START[start], as_max, eps_rel, MODE[mode], threads_per_cta, ctas_per_sm,
-                           kernel_variant)
+                           kernel_variant, flags)
         h = C.c_void_p()
         _check(lib().tadmm_create(C.byref(self._hb.s), C.byref(opt), C.byref(h)), "tadmm_create")
         self.h = h

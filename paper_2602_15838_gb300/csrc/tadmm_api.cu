@@ -89,6 +89,28 @@ static int validate(const tadmm_batch* b, const tadmm_handle* shape) {
   return TADMM_OK;
 }
 
+// True when A = [[I, dt I], [0, I]] and B = [[b1 I], [b2 I]] exactly, the
+// pattern the structured kernel path assumes.
+static bool is_double_integrator(const tadmm_batch* b) {
+  const int nx = b->nx, nu = b->nu, H = nx / 2;
+  if (nu != H) return false;
+  const double dt = b->A[0 * nx + H], b1 = b->B[0], b2 = b->B[H * nu + 0];
+  for (int r = 0; r < nx; ++r)
+    for (int c = 0; c < nx; ++c) {
+      double want = (r == c) ? 1.0 : 0.0;
+      if (r < H && c == r + H) want = dt;
+      if (b->A[r * nx + c] != want) return false;
+    }
+  for (int r = 0; r < nx; ++r)
+    for (int c = 0; c < nu; ++c) {
+      double want = 0.0;
+      if (r < H && c == r) want = b1;
+      if (r >= H && c == r - H) want = b2;
+      if (b->B[r * nu + c] != want) return false;
+    }
+  return true;
+}
+
 static void free_all(tadmm_handle* h) {
   if (!h) return;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -163,7 +185,7 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   if (o.threads_per_cta != 0 && (o.threads_per_cta < 32 || o.threads_per_cta > 256 || o.threads_per_cta % 32))
     return set_error(TADMM_EINVAL, "threads_per_cta must be 0 or a multiple of 32 in [32, 256]");
   if (o.ctas_per_sm < 0) return set_error(TADMM_EINVAL, "ctas_per_sm must be >= 0");
-  if (o.kernel_variant < 0 || o.kernel_variant > 4) return set_error(TADMM_EINVAL, "kernel_variant must be in 0..4");
+  if (o.kernel_variant < 0 || o.kernel_variant > 2) return set_error(TADMM_EINVAL, "kernel_variant must be in 0..2");
 
   tadmm_handle* h = new tadmm_handle();
   h->prec = o.precision;
@@ -175,6 +197,7 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   h->tpc = o.threads_per_cta;
   h->cps = o.ctas_per_sm;
   h->variant = o.kernel_variant;
+  h->di = (!(o.flags & TADMM_FLAG_NO_STRUCTURE) && is_double_integrator(b)) ? 1 : 0;
   h->N.assign(b->N, b->N + b->n_scen);
   h->T.assign(b->T, b->T + b->n_scen);
   h->meta_h.resize(b->n_scen);
@@ -370,11 +393,11 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
   float best = 1e30f;
   int best_t = 128, best_c = 0, best_v = 0;
   struct Cand { int v, tpc; };
-  const Cand cands[] = {{0, 32}, {0, 64}, {0, 128}, {1, 32}, {2, 32}, {3, 32}, {4, 64}};
+  const Cand cands[] = {{0, 32}, {0, 64}, {0, 128}, {1, 32}, {2, 64}};
   int rc = TADMM_OK;
   for (const Cand& cd : cands) {
     const int tpc = cd.tpc;
-    auto occ = [&]() -> int { TADMM_DISPATCH(h, max_ctas_per_sm(tpc, cd.v)); };
+    auto occ = [&]() -> int { TADMM_DISPATCH(h, max_ctas_per_sm(tpc, cd.v, h)); };
     const int maxc = occ();
     if (maxc < 1) continue;
     std::vector<int> cps_list = {maxc};

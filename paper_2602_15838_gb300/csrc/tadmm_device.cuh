@@ -74,6 +74,7 @@ struct Dev {
   int32_t* queue;            // work-queue head of the persistent kernel
   double tol;
   int32_t max_iter;
+  int32_t sm_pairs;          // pairs per step that fit the fused pair/gather staging (0: unfused)
   int32_t start_mode;
   int32_t as_max;            // 0: 10*T*NU + 10
   double eps_rel;
@@ -205,26 +206,40 @@ struct AgentCtx {
 // recursion of Sec. IV.B restricted to the free inputs):
 //   S = Rbar + B'P B, M = B'P A (fixed rows/cols replaced by identity / zero),
 //   S = L L', K = -S^{-1} M, P_t = Qbar_t + A'P A + M'K.
-template <typename F, int NX, int NU>
+// DI: A = [[I, dt I], [0, I]], B = [[b1 I], [b2 I]] (double integrator, checked
+// exactly on the host); the products skip the structural zeros and ones but
+// accumulate the remaining terms in the order of the dense loops.
+template <typename F, int NX, int NU, bool DI>
 __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F (&Pn)[NX][NX],
                                             uint16_t mask, const F (&rbar)[NU], const F* qdiag,
                                             F (&Pt)[NX][NX], F (&K)[NU][NX], F (&L)[NU][NU]) {
+  constexpr int H = NX / 2;
   F PA[NX][NX], PB[NX][NU];
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
+    if constexpr (DI) {
+      const F dt = Mo.A[0][H], b1 = Mo.B[0][0], b2 = Mo.B[H][0];
 #pragma unroll
-    for (int c = 0; c < NX; ++c) {
-      F acc = 0;
+      for (int c = 0; c < H; ++c) {
+        PA[r][c] = Pn[r][c];
+        PA[r][H + c] = fma(Pn[r][H + c], F(1), Pn[r][c] * dt);
+        PB[r][c] = fma(Pn[r][H + c], b2, Pn[r][c] * b1);
+      }
+    } else {
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc = fma(Pn[r][k], Mo.A[k][c], acc);
-      PA[r][c] = acc;
-    }
+      for (int c = 0; c < NX; ++c) {
+        F acc = 0;
 #pragma unroll
-    for (int c = 0; c < NU; ++c) {
-      F acc = 0;
+        for (int k = 0; k < NX; ++k) acc = fma(Pn[r][k], Mo.A[k][c], acc);
+        PA[r][c] = acc;
+      }
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc = fma(Pn[r][k], Mo.B[k][c], acc);
-      PB[r][c] = acc;
+      for (int c = 0; c < NU; ++c) {
+        F acc = 0;
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc = fma(Pn[r][k], Mo.B[k][c], acc);
+        PB[r][c] = acc;
+      }
     }
   }
   F S[NU][NU], Mm[NU][NX];
@@ -235,15 +250,25 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
     for (int b = 0; b < NU; ++b) {
       const bool fb = (mask >> b) & 0x101;
       F acc = (a == b) ? rbar[a] : F(0);
+      if constexpr (DI) {
+        acc = fma(Mo.B[0][0], PB[a][b], acc);
+        acc = fma(Mo.B[H][0], PB[H + a][b], acc);
+      } else {
 #pragma unroll
-      for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], PB[r][b], acc);
+        for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], PB[r][b], acc);
+      }
       S[a][b] = (fa || fb) ? F(a == b ? 1 : 0) : acc;
     }
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
       F acc = 0;
+      if constexpr (DI) {
+        acc = fma(Mo.B[0][0], PA[a][c], acc);
+        acc = fma(Mo.B[H][0], PA[H + a][c], acc);
+      } else {
 #pragma unroll
-      for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], PA[r][c], acc);
+        for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], PA[r][c], acc);
+      }
       Mm[a][c] = fa ? F(0) : acc;
     }
   }
@@ -293,8 +318,17 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
 #pragma unroll
       for (int c = r; c < NX; ++c) {
         F acc = (r == c) ? qdiag[r] : F(0);
+        if constexpr (DI) {
+          if (r < H) {
+            acc = acc + PA[r][c];
+          } else {
+            acc = fma(Mo.A[0][H], PA[r - H][c], acc);
+            acc = acc + PA[r][c];
+          }
+        } else {
 #pragma unroll
-        for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], PA[k][c], acc);
+          for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], PA[k][c], acc);
+        }
 #pragma unroll
         for (int k = 0; k < NU; ++k) acc = fma(Mm[k][r], K[k][c], acc);
         Pt[r][c] = acc;
@@ -312,8 +346,9 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
 // P_{t+1} x_{t+1} + p_{t+1} (Sec. IV.B dual recovery), evaluated only at stages
 // that hold fixed inputs, and flags free inputs that left the box (integer
 // keys); the exact ratio test runs only when such an input exists.
-template <typename F, int NX, int NU, int DP>
+template <typename F, int NX, int NU, int DP, bool DI>
 __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, unsigned long long& nfact) {
+  constexpr int H = NX / 2;
   using CL = CacheLayout<NX, NU>;
   const Model<F, NX, NU>& Mo = *A.M;
   const int T = A.T;
@@ -342,7 +377,7 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
       for (int r = 0; r < NX; ++r)
 #pragma unroll
         for (int c = 0; c < NX; ++c) Pn[r][c] = A.C(t + 1, CL::P + r * NX + c);
-      o.bad |= factor_stage<F, NX, NU>(Mo, Pn, mask, A.rbar, t >= 1 ? A.qbar : nullptr, Pt, K, L);
+      o.bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, A.rbar, t >= 1 ? A.qbar : nullptr, Pt, K, L);
       ++nfact;
 #pragma unroll
       for (int a = 0; a < NU; ++a) {
@@ -373,15 +408,24 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
     for (int r = 0; r < NX; ++r) Pcp[r] = pn[r];
     if (mask) {
       F cv[NX];
+      if constexpr (DI) {
 #pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        F acc = 0;
-#pragma unroll
-        for (int c = 0; c < NU; ++c) {
-          if (mask & (1u << c)) acc = fma(Mo.B[r][c], Mo.umin[c], acc);
-          else if (mask & (0x100u << c)) acc = fma(Mo.B[r][c], Mo.umax[c], acc);
+        for (int c = 0; c < H; ++c) {
+          const F ub = (mask & (1u << c)) ? Mo.umin[c] : ((mask & (0x100u << c)) ? Mo.umax[c] : F(0));
+          cv[c] = Mo.B[0][0] * ub;
+          cv[H + c] = Mo.B[H][0] * ub;
         }
-        cv[r] = acc;
+      } else {
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+          F acc = 0;
+#pragma unroll
+          for (int c = 0; c < NU; ++c) {
+            if (mask & (1u << c)) acc = fma(Mo.B[r][c], Mo.umin[c], acc);
+            else if (mask & (0x100u << c)) acc = fma(Mo.B[r][c], Mo.umax[c], acc);
+          }
+          cv[r] = acc;
+        }
       }
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
@@ -395,8 +439,13 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
       F acc = 0;
+      if constexpr (DI) {
+        acc = fma(Mo.B[0][0], Pcp[a], acc);
+        acc = fma(Mo.B[H][0], Pcp[H + a], acc);
+      } else {
 #pragma unroll
-      for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], Pcp[r], acc);
+        for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], Pcp[r], acc);
+      }
       sv[a] = (mask & (0x101u << a)) ? F(0) : acc;
     }
     {
@@ -422,8 +471,17 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
         F acc = A.q(t, r);
+        if constexpr (DI) {
+          if (r < H) {
+            acc = acc + Pcp[r];
+          } else {
+            acc = fma(Mo.A[0][H], Pcp[r - H], acc);
+            acc = acc + Pcp[r];
+          }
+        } else {
 #pragma unroll
-        for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], Pcp[k], acc);
+          for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], Pcp[k], acc);
+        }
 #pragma unroll
         for (int k = 0; k < NU; ++k) acc = fma(K[k][r], sv[k], acc);
         A.C(t, CL::p + r) = acc;
@@ -462,14 +520,22 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
       }
     }
     F xn[NX];
+    if constexpr (DI) {
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      F acc = 0;
+      for (int c = 0; c < H; ++c) {
+        xn[c] = fma(Mo.B[0][0], uv[c], fma(Mo.A[0][H], xv[H + c], xv[c]));
+        xn[H + c] = fma(Mo.B[H][0], uv[c], xv[H + c]);
+      }
+    } else {
 #pragma unroll
-      for (int c = 0; c < NX; ++c) acc = fma(Mo.A[r][c], xv[c], acc);
+      for (int r = 0; r < NX; ++r) {
+        F acc = 0;
 #pragma unroll
-      for (int c = 0; c < NU; ++c) acc = fma(Mo.B[r][c], uv[c], acc);
-      xn[r] = acc;
+        for (int c = 0; c < NX; ++c) acc = fma(Mo.A[r][c], xv[c], acc);
+#pragma unroll
+        for (int c = 0; c < NU; ++c) acc = fma(Mo.B[r][c], uv[c], acc);
+        xn[r] = acc;
+      }
     }
     if (mask) {
       F lam[NX];
@@ -484,8 +550,13 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
       for (int a = 0; a < NU; ++a) {
         if (!(mask & (0x101u << a))) continue;
         F g = A.rbar[a] * uv[a];
+        if constexpr (DI) {
+          g = fma(Mo.B[0][0], lam[a], g);
+          g = fma(Mo.B[H][0], lam[H + a], g);
+        } else {
 #pragma unroll
-        for (int r = 0; r < NX; ++r) g = fma(Mo.B[r][a], lam[r], g);
+          for (int r = 0; r < NX; ++r) g = fma(Mo.B[r][a], lam[r], g);
+        }
         const F mu = (mask & (1u << a)) ? g : -g;
         const F am = fabs_(mu);
         if (am > o.scale) o.scale = am;
@@ -537,7 +608,7 @@ __device__ void ratio_test(const AgentCtx<F, NX, NU, DP>& A, EqpScan<F>& o) {
 // start_kind: QP_COLD (u = clip(0), W empty), QP_LQR (clipped affine-LQR warm
 // start, Sec. IV.B-C) or QP_GIVEN (hot start from the stored u, W and factors).
 // Returns ST_CONVERGED, ST_QP_FAIL or ST_NUMERIC.
-template <typename F, int NX, int NU, int DP>
+template <typename F, int NX, int NU, int DP, bool DI>
 __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, int as_max, F eps_rel,
                              unsigned long long& neqp, unsigned long long& nfact) {
   const int T = A.T;
@@ -562,7 +633,7 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, i
     if (A.CM(t) != A.W(t)) dirty = t;
 
   if (start_kind == QP_LQR) {
-    EqpScan<F> o = eqp_solve<F, NX, NU, DP>(A, dirty, nfact);
+    EqpScan<F> o = eqp_solve<F, NX, NU, DP, DI>(A, dirty, nfact);
     if (o.bad) return ST_NUMERIC;
     dirty = -1;
     bool clipped = false;
@@ -587,7 +658,7 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, i
       if (as_max <= 0) return ST_QP_FAIL;
       --as_max;
       ++neqp;
-      o = eqp_solve<F, NX, NU, DP>(A, dirty, nfact);
+      o = eqp_solve<F, NX, NU, DP, DI>(A, dirty, nfact);
       if (o.bad) return ST_NUMERIC;
       dirty = -1;
       if (o.out) ratio_test<F, NX, NU, DP>(A, o);
@@ -697,7 +768,7 @@ __device__ __forceinline__ int start_kind_of(const Dev<F>& D, int k) {
   return QP_GIVEN;
 }
 
-template <typename F, int NX, int NU, int DP>
+template <typename F, int NX, int NU, int DP, bool DI>
 __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, int k,
                              int lvl_out, int i0, int stride, unsigned long long& neqp,
                              unsigned long long& nfact) {
@@ -707,7 +778,7 @@ __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const S
   int st = ST_CONVERGED;
   for (int i = i0; i < s.N; i += stride) {
     AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, i, lvl_out);
-    const int r = xupdate_agent<F, NX, NU, DP>(A, kind, as_max, eps, neqp, nfact);
+    const int r = xupdate_agent<F, NX, NU, DP, DI>(A, kind, as_max, eps, neqp, nfact);
     if (r > st) st = r;
   }
   return st;
@@ -818,6 +889,70 @@ __device__ void gather_phase(const Dev<F>& D, const ScenMeta& s, int xl_new, int
   }
 }
 
+// Pair phase and gather fused per time step for a CTA-resident scenario: the
+// projection steps of step t are computed for all pairs (coalesced), the
+// coupling weights e = 2 theta^{k+1} - theta^k and the normals of step t are
+// staged in shared memory, then each agent sums its partners' terms from
+// shared memory.  Same arithmetic, in the same order, as pair_phase followed by
+// gather_phase.  sm holds (DP + 1) * P values.
+template <typename F, int NX, int NU, int DP>
+__device__ void pair_gather_fused(const Dev<F>& D, const ScenMeta& s, int xl, int tk, int tkp1, F* sm,
+                                  unsigned long long& rb) {
+  const int N = s.N, P = s.P, tid = threadIdx.x, nt = blockDim.x;
+  const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+  const F* thk = D.theta + (size_t)tk * D.tot_ps + s.ps_off;
+  F* thn = D.theta + (size_t)tkp1 * D.tot_ps + s.ps_off;
+  const F* a = D.a + s.ps_off * DP;
+  const int32_t* pr = D.pairs + s.pair_off;
+  F* h = D.h + s.as_off * DP;
+  F* smE = sm;
+  F* smA = sm + P;
+  const F d = F(s.d), nc = F(N - 1);
+  for (int tm1 = 0; tm1 < s.T; ++tm1) {
+    const size_t qb = (size_t)tm1 * P;
+    for (int pair = tid; pair < P; pair += nt) {
+      const int pk = pr[pair];
+      const int i = pk & 0xFFFF, j = pk >> 16;
+      F sdot = 0;
+      unsigned long long amax = 0;
+#pragma unroll
+      for (int c = 0; c < DP; ++c) {
+        const F av = a[((size_t)tm1 * DP + c) * P + pair];
+        smA[c * P + pair] = av;
+        const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
+        sdot = fma(av, Xn[ro + i] - Xn[ro + j], sdot);
+        const unsigned long long ab = abs_bits(av);
+        amax = ab > amax ? ab : amax;
+      }
+      const F th = thk[qb + pair];
+      F tn = fma(d - sdot, F(0.5), th);
+      if (sign_set(tn)) tn = F(0);
+      thn[qb + pair] = tn;
+      smE[pair] = fma(F(2), tn, -th);
+      const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
+      rb = v > rb ? v : rb;
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) {
+      F acc[DP];
+#pragma unroll
+      for (int c = 0; c < DP; ++c) acc[c] = nc * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
+      for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const bool first = i < j;
+        const int pair = first ? pair_index(N, i, j) : pair_index(N, j, i);
+        F e = smE[pair];
+        if (!first) e = -e;
+#pragma unroll
+        for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * P + pair], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+    }
+    __syncthreads();
+  }
+}
+
 // Maximum of a non-negative bit-ordered value over the CTA; every thread
 // receives the result.  Contains two barriers.
 __device__ __forceinline__ unsigned long long block_max1(unsigned long long a, unsigned long long* red) {
@@ -847,9 +982,10 @@ struct CtaScratch {
 // when the primal test passes (or on the last iteration), convergence test,
 // then the aggregate coupling term of the next x-update.  Writes status,
 // iterations, residuals, work counters and the levels of the final iterate.
-template <typename F, int NX, int NU, int DP>
+template <typename F, int NX, int NU, int DP, bool DI>
 __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, int sc,
-                             CtaScratch& cs) {
+                             CtaScratch& cs, F* sm, int sm_pairs) {
+  const bool fused = sm != nullptr && s.P <= sm_pairs;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
     cs.flag = 0;
@@ -863,14 +999,15 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
   unsigned long long neqp = 0, nfact = 0;
   for (int k = 0; k < D.max_iter; ++k) {
     const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
-    const int st = xupdate_phase<F, NX, NU, DP>(D, M, s, k, xl ^ 1, tid, nt, neqp, nfact);
+    const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, xl ^ 1, tid, nt, neqp, nfact);
     if (st) atomicMax(&cs.flag, st);
     __syncthreads();
     iters = k + 1;
     const int flag = cs.flag;
     if (flag) { status = flag; tfin = tk; break; }
     unsigned long long rb = 0;
-    pair_phase<F, NX, NU, DP>(D, s, xl, tk, tkp1, tid, nt, rb);
+    if (fused) pair_gather_fused<F, NX, NU, DP>(D, s, xl, tk, tkp1, sm, rb);
+    else pair_phase<F, NX, NU, DP>(D, s, xl, tk, tkp1, tid, nt, rb);
     r = from_bits(block_max1(rb, cs.red), F(0));
     tfin = tkp1;
     if (!finite_(r)) { status = ST_NUMERIC; xl ^= 1; break; }
@@ -883,8 +1020,10 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
       if (r <= F(D.tol) && sres <= F(D.tol)) { status = ST_CONVERGED; xl ^= 1; break; }
       if (last) { xl ^= 1; break; }
     }
-    gather_phase<F, NX, NU, DP>(D, s, xl ^ 1, tkp1, tk, tid, nt);
-    __syncthreads();
+    if (!fused) {
+      gather_phase<F, NX, NU, DP>(D, s, xl ^ 1, tkp1, tk, tid, nt);
+      __syncthreads();
+    }
     xl ^= 1;
   }
   if (neqp) atomicAdd(&cs.cnt[0], neqp);

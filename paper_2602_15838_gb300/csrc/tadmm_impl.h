@@ -64,6 +64,7 @@ struct tadmm_handle {
 
   // batched mode launch shape and captured graph
   int tpc = 0, cps = 0, variant = 0;
+  int di = 0;               // model is an exact double integrator (structured kernel path)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   double g_tol = -1.0;
@@ -84,7 +85,7 @@ struct Impl {
   static int solve_plain(tadmm_handle* h, double tol, int max_iter, cudaStream_t st);
   static int export_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W,
                              cudaStream_t st);
-  static int max_ctas_per_sm(int tpc, int variant);
+  static int max_ctas_per_sm(int tpc, int variant, const tadmm_handle* h);
 };
 
 }  // namespace tadmm

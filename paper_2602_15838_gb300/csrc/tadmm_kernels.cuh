@@ -19,16 +19,16 @@ namespace tadmm {
 template <int V> struct KVariant;
 template <> struct KVariant<0> { static constexpr int maxt = 256, minb = 1; };
 template <> struct KVariant<1> { static constexpr int maxt = 32, minb = 12; };
-template <> struct KVariant<2> { static constexpr int maxt = 32, minb = 16; };
-template <> struct KVariant<3> { static constexpr int maxt = 32, minb = 24; };
-template <> struct KVariant<4> { static constexpr int maxt = 64, minb = 8; };
-constexpr int kNumVariants = 5;
+template <> struct KVariant<2> { static constexpr int maxt = 64, minb = 8; };
+constexpr int kNumVariants = 3;
 
-template <typename F, int NX, int NU, int DP, int V>
+template <typename F, int NX, int NU, int DP, int V, bool DI>
 __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batched(Dev<F> D) {
   __shared__ Model<F, NX, NU> M;
   __shared__ CtaScratch cs;
   __shared__ int s_q;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  F* sm = D.sm_pairs > 0 ? (F*)dyn_smem : nullptr;
   load_model<F, NX, NU>(M, D.model);
   for (;;) {
     __syncthreads();
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batche
     if (qi >= D.n_scen) return;
     const int sc = D.order[qi];
     const ScenMeta s = D.meta[sc];
-    run_scenario<F, NX, NU, DP>(D, M, s, sc, cs);
+    run_scenario<F, NX, NU, DP, DI>(D, M, s, sc, cs, sm, D.sm_pairs);
   }
 }
 
@@ -56,7 +56,7 @@ __global__ void k_init(Dev<F> D, int sc) {
   }
 }
 
-template <typename F, int NX, int NU, int DP>
+template <typename F, int NX, int NU, int DP, bool DI>
 __global__ void __launch_bounds__(128) k_xupdate(Dev<F> D, int sc, int k, int lvl_out, int32_t* flag) {
   __shared__ Model<F, NX, NU> M;
   load_model<F, NX, NU>(M, D.model);
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_xupdate(Dev<F> D, int sc, int k, int lv
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.N) return;
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP>(D, M, s, k, lvl_out, i, s.N, neqp, nfact);
+  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, lvl_out, i, s.N, neqp, nfact);
   if (st) atomicMax(flag, st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
@@ -254,13 +254,18 @@ int Impl<F, NX, NU, DP>::import_inputs(tadmm_handle* h, cudaStream_t st) {
 }
 
 template <typename F, int NX, int NU, int DP>
-static const void* batched_kernel(int v) {
+static const void* batched_kernel(int v, bool di) {
+  if (di) {
+    switch (v) {
+      case 1: return (const void*)k_batched<F, NX, NU, DP, 1, true>;
+      case 2: return (const void*)k_batched<F, NX, NU, DP, 2, true>;
+      default: return (const void*)k_batched<F, NX, NU, DP, 0, true>;
+    }
+  }
   switch (v) {
-    case 1: return (const void*)k_batched<F, NX, NU, DP, 1>;
-    case 2: return (const void*)k_batched<F, NX, NU, DP, 2>;
-    case 3: return (const void*)k_batched<F, NX, NU, DP, 3>;
-    case 4: return (const void*)k_batched<F, NX, NU, DP, 4>;
-    default: return (const void*)k_batched<F, NX, NU, DP, 0>;
+    case 1: return (const void*)k_batched<F, NX, NU, DP, 1, false>;
+    case 2: return (const void*)k_batched<F, NX, NU, DP, 2, false>;
+    default: return (const void*)k_batched<F, NX, NU, DP, 0, false>;
   }
 }
 
@@ -268,17 +273,34 @@ static int variant_maxt(int v) {
   switch (v) {
     case 1: return KVariant<1>::maxt;
     case 2: return KVariant<2>::maxt;
-    case 3: return KVariant<3>::maxt;
-    case 4: return KVariant<4>::maxt;
     default: return KVariant<0>::maxt;
   }
 }
 
+// Dynamic shared memory of the fused pair/gather staging: (DP + 1) values per
+// pair of the largest scenario, if that fits the per-CTA budget.
+template <typename F, int DP>
+static size_t fused_smem_bytes(const tadmm_handle* h, int* pairs_out) {
+  int pmax = 0;
+  for (const ScenMeta& m : h->meta_h) pmax = std::max(pmax, m.P);
+  const size_t bytes = (size_t)(DP + 1) * pmax * sizeof(F);
+  const size_t budget = 96 * 1024;
+  if ((h->opt.flags & TADMM_FLAG_NO_FUSED_PAIR_GATHER) || pmax == 0 || bytes > budget) {
+    if (pairs_out) *pairs_out = 0;
+    return 0;
+  }
+  if (pairs_out) *pairs_out = pmax;
+  return bytes;
+}
+
 template <typename F, int NX, int NU, int DP>
-int Impl<F, NX, NU, DP>::max_ctas_per_sm(int tpc, int variant) {
+int Impl<F, NX, NU, DP>::max_ctas_per_sm(int tpc, int variant, const tadmm_handle* h) {
   int n = 0;
   if (tpc > variant_maxt(variant)) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<F, NX, NU, DP>(variant), tpc, 0) != cudaSuccess) {
+  const size_t smem = h ? fused_smem_bytes<F, DP>(h, nullptr) : 0;
+  const void* kfn = batched_kernel<F, NX, NU, DP>(variant, h ? h->di != 0 : false);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kfn, tpc, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -289,7 +311,7 @@ template <typename F, int NX, int NU, int DP>
 int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter, cudaStream_t st) {
   const int var = (h->variant >= 0 && h->variant < kNumVariants) ? h->variant : 0;
   int tpc = h->tpc > 0 ? h->tpc : std::min(128, variant_maxt(var));
-  const int occ = max_ctas_per_sm(tpc, var);
+  const int occ = max_ctas_per_sm(tpc, var, h);
   if (occ < 1) return set_error(TADMM_EINVAL, "launch shape does not fit the kernel variant");
   int cps = h->cps > 0 ? std::min(h->cps, occ) : occ;
   const int grid = std::max(1, std::min(h->n_scen, h->sm_count * cps));
@@ -302,12 +324,15 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
     Dev<F> D = make_dev<F>(h);
     D.tol = tol;
     D.max_iter = max_iter;
+    int smp = 0;
+    const size_t smem = fused_smem_bytes<F, DP>(h, &smp);
+    D.sm_pairs = smp;
     cudaGraph_t g = nullptr;
     int rc = cuda_check(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (rc) return rc;
     cudaMemsetAsync(h->queue, 0, sizeof(int32_t), h->cap_stream);
     void* args[] = {&D};
-    cudaLaunchKernel(batched_kernel<F, NX, NU, DP>(var), dim3(grid), dim3(tpc), args, 0, h->cap_stream);
+    cudaLaunchKernel(batched_kernel<F, NX, NU, DP>(var, h->di != 0), dim3(grid), dim3(tpc), args, smem, h->cap_stream);
     cudaError_t le = cudaGetLastError();
     cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_check(le, "batched kernel launch"); }
@@ -354,7 +379,10 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
       const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
       cudaMemsetAsync(h->flag, 0, sizeof(int32_t), st);
       cudaMemsetAsync(h->red2, 0, 2 * sizeof(unsigned long long), st);
-      k_xupdate<F, NX, NU, DP><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
+      if (h->di)
+        k_xupdate<F, NX, NU, DP, true><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
+      else
+        k_xupdate<F, NX, NU, DP, false><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
       k_pair<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, xl, tk, tkp1, h->red2);
       launches += 2;
       cudaMemcpyAsync(hb, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_noalloc_solve(Dev<F> D) {
   load_model<F, NX, NU>(M, D.model);
   __syncthreads();
   const ScenMeta s = D.meta[0];
-  run_scenario<F, NX, NU, DP>(D, M, s, 0, cs);
+  run_scenario<F, NX, NU, DP, false>(D, M, s, 0, cs, nullptr, 0);
 }
 
 __global__ void k_noalloc_results(const int32_t* status, const int32_t* iters, const double* res,

@@ -45,7 +45,7 @@ def test_version_and_last_error(libtadmm):
 
 def _create_rc(tg, batch, **opt):
     hb = tg._HostBatch(batch)
-    o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0, 0)
+    o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0, 0, 0)
     h = C.c_void_p()
     rc = tg.lib().tadmm_create(C.byref(hb.s), C.byref(o), C.byref(h))
     return rc, tg.lib().tadmm_last_error().decode()

@@ -181,3 +181,34 @@ def test_as_max_one_reports_qp_fail(tg):
     b = make_config(2)
     g, _ = gpu_run(tg, b, 1e-4, 20, start="cold", as_max=1)
     assert g[0]["status"] == tg.QP_FAIL
+
+
+def test_fused_and_structured_paths_equal_plain_paths(tg):
+    """The shared-memory fused pair/gather sweep and the double-integrator
+    structured products give the same iterates as the separate sweeps and the
+    dense products."""
+    b = make_config(3, n_scen=24)
+    ref, _ = gpu_run(tg, b, 0.0, 8, flags=tg.FLAG_NO_FUSED_PAIR_GATHER | tg.FLAG_NO_STRUCTURE)
+    for fl in (0, tg.FLAG_NO_FUSED_PAIR_GATHER, tg.FLAG_NO_STRUCTURE):
+        g, _ = gpu_run(tg, b, 0.0, 8, flags=fl)
+        for k in range(b.n_scen):
+            assert rel(g[k]["X"], ref[k]["X"]) <= 1e-12, (fl, k)
+            assert rel(g[k]["theta"], ref[k]["theta"]) <= 1e-12, (fl, k)
+            assert np.array_equal(g[k]["W"], ref[k]["W"]), (fl, k)
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_general_dynamics_fp64(tg, k):
+    """Dynamics that are not a double integrator (damped velocity, skewed input)
+    take the dense-product path; iterates match the oracle."""
+    b = make_config(1)
+    b.A = b.A.copy()
+    b.A[2, 2] = b.A[3, 3] = 0.95
+    b.A[0, 1] = 0.01
+    b.B = b.B.copy()
+    b.B[1, 0] = 0.002
+    g, _ = gpu_run(tg, b, 0.0, k)
+    o = oracle.admm(b, 0, tol=0.0, max_iter=k)
+    assert rel(g[0]["X"], o["X"]) <= 1e-9
+    assert rel(g[0]["U"], o["U"]) <= 1e-9
+    assert rel(g[0]["theta"], o["theta"]) <= 1e-9
