@@ -141,6 +141,29 @@ int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pa
 int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* threads_out,
                    int32_t* ctas_out, int32_t* variant_out);
 
+/* Implicit-KKT gradients of a loss l(X) at the final active set of the last
+ * solve (spec differentiation pattern; the paper has no gradient).  The
+ * active set is the final bound working set of every agent plus the halfspaces
+ * whose projection step exceeds theta_eps.  At that active set the
+ * centralized QP of Eq. (1) (Sec. III.A) with linearized halfspaces is an
+ * equality-constrained QP; its KKT system is solved exactly (the polished
+ * solution) and differentiated implicitly: per-agent Riccati solves of the
+ * block-tridiagonal LQ problems (Sec. IV.B) coupled through a dense Schur
+ * complement over the active halfspaces.
+ *   grad_X      dl/dX in the layout of X (host or device), entries at t = 0 are
+ *               ignored (x_0 is data)
+ *   gQ, gQf     [sum N][nx] dl/d diag(Q_i) (stages t < T) and dl/d diag(Qf_i);
+ *               for a tie Qf_i = c Q_i the total is gQ + c gQf
+ *   gR          [sum N][nu] dl/d diag(R_i)
+ *   gGoal       [sum N][nx] dl/d x_ref_i
+ *   X_polished  polished states in the layout of X
+ *   status      [n_scen] TADMM_CONVERGED, or TADMM_NUMERIC when the Schur
+ *               complement is not positive definite (dependent active rows)
+ * Outputs may be host or device pointers, any may be NULL.  Horizons T <= 64.
+ * Allocates its scratch on first use; synchronizes `stream`. */
+int tadmm_backward(tadmm_handle* h, const double* grad_X, double theta_eps, double* gQ, double* gQf,
+                   double* gR, double* gGoal, double* X_polished, int32_t* status, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free single-scenario solve.
  *

@@ -61,6 +61,8 @@ def lib():
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_get_counters.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
         L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p, _i32p]
+        L.tadmm_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_destroy.argtypes = [C.c_void_p]
         L.tadmm_destroy.restype = None
         L.tadmm_last_error.restype = C.c_char_p
@@ -185,6 +187,31 @@ class Solver:
                "tadmm_get_solution")
         return dict(X=X, U=U, theta=th[:self.sizes["theta"]], W=W, status=st, iters=it, res=res)
 
+    def backward(self, grad_X, theta_eps: float = 1e-9, polished: bool = True, stream=None):
+        """Implicit-KKT gradients of a loss at the final active set of the last solve.
+
+        grad_X: dl/dX in the packed layout of X (numpy array or CUDA tensor).
+        Returns numpy arrays gQ, gQf, gR, gGoal (per agent), the polished
+        states X_polished and the per-scenario status."""
+        b = self.batch
+        na = int(b.N.sum())
+        if hasattr(grad_X, "data_ptr"):
+            g = grad_X.detach().to(dtype=__import__("torch").float64).contiguous()
+            gptr = C.c_void_p(g.data_ptr())
+            keep = g
+        else:
+            keep = np.ascontiguousarray(grad_X, dtype=np.float64).reshape(-1)
+            assert keep.size == self.sizes["X"]
+            gptr = C.c_void_p(keep.ctypes.data)
+        gQ = np.zeros((na, b.nx)); gQf = np.zeros((na, b.nx)); gR = np.zeros((na, b.nu)); gG = np.zeros((na, b.nx))
+        Xp = np.zeros(self.sizes["X"]) if polished else None
+        st = np.zeros(self.n_scen, dtype=np.int32)
+        p = lambda a: C.c_void_p(a.ctypes.data) if a is not None else None
+        _check(lib().tadmm_backward(self.h, gptr, float(theta_eps), p(gQ), p(gQf), p(gR), p(gG), p(Xp),
+                                    p(st), C.c_void_p(_stream_ptr(stream))), "tadmm_backward")
+        del keep
+        return dict(gQ=gQ, gQf=gQf, gR=gR, gGoal=gG, X_polished=Xp, status=st)
+
     def counters(self):
         eqp = np.zeros(self.n_scen, dtype=np.int64)
         fact = np.zeros(self.n_scen, dtype=np.int64)
@@ -220,3 +247,48 @@ def solve(batch, tol: float = 1e-4, max_iter: int = 500, **kw):
     s = Solver(batch, **kw)
     s.solve(tol, max_iter)
     return s.split(s.solution()), s
+
+
+class TADMMFunction:
+    """Differentiable solve: X = TADMMFunction.apply(Qd, Rd, goal, solver, ...).
+
+    Qd [sum N, nx] (diag Q per agent, with Qf = qf_tie * Q), Rd [sum N, nu] and
+    goal [sum N, nx] (the goal state x_ref) are float64 torch tensors.  The
+    forward pass uploads them into `solver`'s batch, solves to `tol` and returns
+    the polished states at the final active set (packed layout of X, float64 on
+    the GPU).  The backward pass runs the implicit-KKT adjoint kernel.
+    """
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Qd, Rd, goal, solver, tol, max_iter, qf_tie, theta_eps):
+                b = solver.batch
+                b.Qd = np.ascontiguousarray(Qd.detach().cpu().numpy(), dtype=np.float64)
+                b.Qfd = qf_tie * b.Qd
+                b.Rd = np.ascontiguousarray(Rd.detach().cpu().numpy(), dtype=np.float64)
+                b.x_ref = np.ascontiguousarray(goal.detach().cpu().numpy(), dtype=np.float64)
+                solver.update(b)
+                solver.solve(tol, max_iter)
+                out = solver.backward(np.zeros(solver.sizes["X"]), theta_eps=theta_eps)
+                ctx.solver, ctx.qf_tie, ctx.theta_eps = solver, qf_tie, theta_eps
+                ctx.status = out["status"]
+                return torch.from_numpy(out["X_polished"]).to(Qd.device)
+
+            @staticmethod
+            def backward(ctx, grad_X):
+                g = ctx.solver.backward(grad_X.detach().to("cuda", dtype=torch.float64).contiguous(),
+                                        theta_eps=ctx.theta_eps, polished=False)
+                dev = grad_X.device
+                gQ = torch.from_numpy(g["gQ"] + ctx.qf_tie * g["gQf"]).to(dev)
+                return gQ, torch.from_numpy(g["gR"]).to(dev), torch.from_numpy(g["gGoal"]).to(dev), \
+                    None, None, None, None, None
+
+        return _F
+
+    @classmethod
+    def apply(cls, Qd, Rd, goal, solver, tol=1e-4, max_iter=500, qf_tie=10.0, theta_eps=1e-9):
+        return cls._fn().apply(Qd, Rd, goal, solver, tol, max_iter, qf_tie, theta_eps)

@@ -121,6 +121,11 @@ static void free_all(tadmm_handle* h) {
                   h->ex_buf, h->flag,  h->red2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  void* bptrs[] = {h->bwd.act, h->bwd.cnt, h->bwd.amask, h->bwd.psi, h->bwd.kks, h->bwd.pos0, h->bwd.force,
+                   h->bwd.Xp,  h->bwd.Up,  h->bwd.Wx,    h->bwd.Wu,  h->bwd.bstat, h->bwd.bs, h->bwd.S,
+                   h->bwd.vec, h->bwd.gX,  h->bwd.gout,  h->bwd.xpol};
+  for (void* p : bptrs)
+    if (p) cudaFree(p);
   if (h->pinned) cudaFreeHost(h->pinned);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -434,6 +439,59 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
   if (ctas_out) *ctas_out = best_c;
   if (variant_out) *variant_out = best_v;
   return TADMM_OK;
+}
+
+extern "C" int tadmm_backward(tadmm_handle* h, const double* grad_X, double theta_eps, double* gQ, double* gQf,
+                              double* gR, double* gGoal, double* X_polished, int32_t* status, void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!h->solved) return set_error(TADMM_ESTATE, "backward before solve");
+  if (!grad_X) return set_error(TADMM_EINVAL, "grad_X is NULL");
+  if (!(theta_eps >= 0.0) || !std::isfinite(theta_eps)) return set_error(TADMM_EINVAL, "theta_eps must be >= 0");
+  for (const auto& m : h->meta_h)
+    if (m.T > 64) return set_error(TADMM_EINVAL, "backward supports horizons T <= 64");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nx = h->nx, nu = h->nu;
+  const int64_t na = h->tot_agents;
+  auto grow = [&](void** p, size_t& cap, size_t bytes) -> int {
+    if (bytes <= cap && *p) return TADMM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(TADMM_ENOMEM, "backward staging allocation failed");
+    }
+    cap = bytes;
+    return TADMM_OK;
+  };
+  int rc;
+  const size_t gx_bytes = sizeof(double) * h->tot_xs * nx;
+  const size_t gout_n = (size_t)na * (3 * nx + nu);
+  if ((rc = grow(&h->bwd.gX, h->bwd.gX_cap, gx_bytes)) ||
+      (rc = grow(&h->bwd.gout, h->bwd.gout_cap, sizeof(double) * gout_n)) ||
+      (rc = grow(&h->bwd.xpol, h->bwd.xpol_cap, gx_bytes)))
+    return rc;
+  if ((rc = cuda_check(cudaMemcpyAsync(h->bwd.gX, grad_X, gx_bytes, cudaMemcpyDefault, st), "grad_X copy")))
+    return rc;
+  double* gout = (double*)h->bwd.gout;
+  auto run = [&]() -> int {
+    TADMM_DISPATCH(h, backward(h, (const double*)h->bwd.gX, theta_eps, gout, X_polished ? (double*)h->bwd.xpol : nullptr, st));
+  };
+  if ((rc = run())) return rc;
+  struct Out { void* dst; size_t off, n; };
+  const Out outs[4] = {{gQ, 0, (size_t)na * nx}, {gQf, (size_t)na * nx, (size_t)na * nx},
+                       {gR, 2 * (size_t)na * nx, (size_t)na * nu}, {gGoal, 2 * (size_t)na * nx + na * nu, (size_t)na * nx}};
+  for (const Out& o : outs)
+    if (o.dst && (rc = cuda_check(cudaMemcpyAsync(o.dst, gout + o.off, sizeof(double) * o.n, cudaMemcpyDefault, st),
+                                  "gradient copy")))
+      return rc;
+  if (X_polished && (rc = cuda_check(cudaMemcpyAsync(X_polished, h->bwd.xpol, gx_bytes, cudaMemcpyDefault, st),
+                                     "polished X copy")))
+    return rc;
+  if (status && (rc = cuda_check(cudaMemcpyAsync(status, h->bwd.bstat, 4 * h->n_scen, cudaMemcpyDefault, st),
+                                 "backward status copy")))
+    return rc;
+  return cuda_check(cudaStreamSynchronize(st), "backward sync");
 }
 
 extern "C" void tadmm_destroy(tadmm_handle* h) {

@@ -11,6 +11,16 @@
 #include "../../include/tadmm.h"
 #include "tadmm_device.cuh"
 
+// Scratch of the implicit-KKT backward pass (grown on demand).
+struct BwdBufs {
+  void *act = nullptr, *cnt = nullptr, *amask = nullptr, *psi = nullptr, *kks = nullptr, *pos0 = nullptr,
+       *force = nullptr, *Xp = nullptr, *Up = nullptr, *Wx = nullptr, *Wu = nullptr, *bstat = nullptr,
+       *bs = nullptr, *S = nullptr, *vec = nullptr, *gX = nullptr, *gout = nullptr, *xpol = nullptr;
+  size_t act_cap = 0, cnt_cap = 0, amask_cap = 0, psi_cap = 0, kks_cap = 0, pos0_cap = 0, force_cap = 0,
+         Xp_cap = 0, Up_cap = 0, Wx_cap = 0, Wu_cap = 0, bstat_cap = 0, bs_cap = 0, S_cap = 0, vec_cap = 0,
+         gX_cap = 0, gout_cap = 0, xpol_cap = 0;
+};
+
 struct tadmm_handle {
   int prec = 64, nx = 0, nu = 0, dp = 0, n_scen = 0;
   int64_t tot_agents = 0, tot_as = 0, tot_ps = 0, tot_xs = 0, tot_pairs = 0;
@@ -71,6 +81,7 @@ struct tadmm_handle {
   int g_iter = -1, g_tpc = -1, g_cps = -1, g_var = -1;
   int solved = 0;
   int64_t launches = 0;   // kernel launches enqueued by the last solve
+  BwdBufs bwd;
 };
 
 namespace tadmm {
@@ -86,6 +97,8 @@ struct Impl {
   static int export_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W,
                              cudaStream_t st);
   static int max_ctas_per_sm(int tpc, int variant, const tadmm_handle* h);
+  static int backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev, double* xpol_dev,
+                      cudaStream_t st);
 };
 
 }  // namespace tadmm

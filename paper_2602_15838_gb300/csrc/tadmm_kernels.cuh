@@ -434,4 +434,100 @@ int Impl<F, NX, NU, DP>::export_solution(tadmm_handle* h, double* X, double* U, 
   return cuda_check(cudaGetLastError(), "export kernels");
 }
 
+
+}  // namespace tadmm
+
+#include "tadmm_adjoint.cuh"
+
+namespace tadmm {
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev,
+                                  double* xpol_dev, cudaStream_t st) {
+  const int64_t na = h->tot_agents;
+  int tmax = 0;
+  for (const ScenMeta& m : h->meta_h) tmax = std::max(tmax, m.T);
+  auto grow = [&](void** p, size_t& cap, size_t bytes) -> int {
+    if (bytes <= cap && *p) return TADMM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(TADMM_ENOMEM, "backward scratch allocation failed");
+    }
+    cap = bytes;
+    return TADMM_OK;
+  };
+  int64_t psi_total = 0;
+  std::vector<BwdScen> bs(h->n_scen);
+  for (int s = 0; s < h->n_scen; ++s) {
+    const ScenMeta& m = h->meta_h[s];
+    bs[s].psi_off = psi_total;
+    psi_total += (int64_t)m.N * m.T * m.T * DP * DP;
+  }
+  int rc;
+  BwdBufs& b = h->bwd;
+  if ((rc = grow(&b.act, b.act_cap, 4 * std::max<int64_t>(h->tot_ps, 1))) ||
+      (rc = grow(&b.cnt, b.cnt_cap, 4 * h->n_scen)) || (rc = grow(&b.amask, b.amask_cap, 8 * na)) ||
+      (rc = grow(&b.psi, b.psi_cap, sizeof(F) * std::max<int64_t>(psi_total, 1))) ||
+      (rc = grow(&b.kks, b.kks_cap, sizeof(F) * na * DP * tmax * NU)) ||
+      (rc = grow(&b.pos0, b.pos0_cap, sizeof(F) * h->tot_as * DP)) ||
+      (rc = grow(&b.force, b.force_cap, sizeof(F) * h->tot_as * DP)) ||
+      (rc = grow(&b.Xp, b.Xp_cap, sizeof(F) * h->tot_xs * NX)) || (rc = grow(&b.Up, b.Up_cap, sizeof(F) * h->tot_as * NU)) ||
+      (rc = grow(&b.Wx, b.Wx_cap, sizeof(F) * h->tot_xs * NX)) || (rc = grow(&b.Wu, b.Wu_cap, sizeof(F) * h->tot_as * NU)) ||
+      (rc = grow(&b.bstat, b.bstat_cap, 4 * h->n_scen)) || (rc = grow(&b.bs, b.bs_cap, sizeof(BwdScen) * h->n_scen)))
+    return rc;
+  Dev<F> D = make_dev<F>(h);
+  BwdDev<F> B;
+  std::memset(&B, 0, sizeof(B));
+  B.act = (int32_t*)b.act;
+  B.act_cnt = (int32_t*)b.cnt;
+  B.amask = (unsigned long long*)b.amask;
+  B.psi = (F*)b.psi;
+  B.kks = (F*)b.kks;
+  B.pos0 = (F*)b.pos0;
+  B.force = (F*)b.force;
+  B.Xp = (F*)b.Xp;
+  B.Up = (F*)b.Up;
+  B.Wx = (F*)b.Wx;
+  B.Wu = (F*)b.Wu;
+  B.gX = gX_dev;
+  B.gQ = gout_dev;
+  B.gQf = gout_dev + na * NX;
+  B.gR = gout_dev + 2 * na * NX;
+  B.gGoal = gout_dev + 2 * na * NX + na * NU;
+  B.bstatus = (int32_t*)b.bstat;
+  B.theta_eps = theta_eps;
+  B.kk_stride = (int64_t)tmax * NU;
+  k_bwd_count<F, NX, NU, DP><<<h->n_scen, 32, 0, st>>>(D, B);
+  if ((rc = cuda_check(cudaGetLastError(), "backward count launch"))) return rc;
+  std::vector<int32_t> cnt(h->n_scen);
+  if ((rc = cuda_check(cudaMemcpyAsync(cnt.data(), b.cnt, 4 * h->n_scen, cudaMemcpyDeviceToHost, st), "counts")) ||
+      (rc = cuda_check(cudaStreamSynchronize(st), "backward count sync")))
+    return rc;
+  int64_t s_total = 0, v_total = 0;
+  for (int s = 0; s < h->n_scen; ++s) {
+    bs[s].m = cnt[s];
+    bs[s].s_off = s_total;
+    bs[s].v_off = v_total;
+    s_total += (int64_t)cnt[s] * cnt[s];
+    v_total += 3 * (int64_t)cnt[s];
+  }
+  if ((rc = grow(&b.S, b.S_cap, sizeof(F) * std::max<int64_t>(s_total, 1))) ||
+      (rc = grow(&b.vec, b.vec_cap, sizeof(F) * std::max<int64_t>(v_total, 1))))
+    return rc;
+  B.S = (F*)b.S;
+  B.vec = (F*)b.vec;
+  B.bs = (const BwdScen*)b.bs;
+  cudaMemcpyAsync(b.bs, bs.data(), sizeof(BwdScen) * h->n_scen, cudaMemcpyHostToDevice, st);
+  if (h->di)
+    k_bwd_main<F, NX, NU, DP, true><<<h->n_scen, 128, 0, st>>>(D, B);
+  else
+    k_bwd_main<F, NX, NU, DP, false><<<h->n_scen, 128, 0, st>>>(D, B);
+  if ((rc = cuda_check(cudaGetLastError(), "backward launch"))) return rc;
+  if (xpol_dev) k_bwd_export_x<F><<<grid_for(h->tot_xs * NX, 256), 256, 0, st>>>(B.Xp, h->tot_xs * NX, xpol_dev);
+  return cuda_check(cudaGetLastError(), "backward export");
+}
+
 }  // namespace tadmm
