@@ -55,6 +55,8 @@ extern "C" {
 #define TADMM_MODE_BATCHED 0 /* all scenarios, all iterations in one persistent, graph-captured launch */
 #define TADMM_MODE_PLAIN 1   /* one scenario at a time, one launch per phase and a host
                                 read of the residuals after every iteration */
+#define TADMM_MODE_GRAPH 2   /* grid-wide phase kernels over all scenarios repeated by a CUDA
+                                graph conditional WHILE node (for scenarios too large for one CTA) */
 
 /* A batch of independent scenarios sharing (nx, nu, dp), the dynamics (A, B)
  * and the input box.  All pointers are HOST pointers, row-major float64, read

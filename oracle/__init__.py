@@ -69,6 +69,8 @@ def lib():
         _LIB.orc_agent_bruteforce.argtypes = [C.POINTER(AgentQP), C.c_double, _dp, _i8p]
         _LIB.orc_halfspace_project.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp]
         _LIB.orc_halfspace_project.restype = C.c_double
+        _LIB.orc_agent_xupdate.argtypes = [C.POINTER(Scenario), C.c_int, _dp, C.c_int, C.c_int, C.c_double, _dp,
+                                           _i8p, _dp, _dp, C.POINTER(C.c_int)]
         _LIB.orc_admm.argtypes = [C.POINTER(Scenario), C.POINTER(Options), C.POINTER(Result)]
         _LIB.orc_admm_batch.argtypes = [C.POINTER(Scenario), C.c_int, C.POINTER(Options),
                                         C.POINTER(Result), C.c_int]
@@ -187,6 +189,18 @@ class _ResultData:
 
 def _options(start_mode, as_max, eps_rel, tol, max_iter, nthreads):
     return Options(start_mode, as_max, eps_rel, tol, max_iter, nthreads)
+
+
+def agent_xupdate(batch, k: int, i: int, h, start=QP_LQR, as_max=None, eps_rel=1e-12):
+    """First-principles x-update of agent i of scenario k for a coupling term h [T, dp]."""
+    sd = _ScenarioData(batch, k)
+    T, nx, nu = sd.T, sd.nx, sd.nu
+    hh = _f64(h).reshape(T, sd.dp)
+    u = np.zeros((T, nu)); W = np.zeros((T, nu), dtype=np.int8); x = np.zeros((T + 1, nx)); mu = np.zeros((T, nu))
+    n = C.c_int(0)
+    st = lib().orc_agent_xupdate(C.byref(sd.s), i, _d(hh), start, as_max or 10 * T * nu + 10, eps_rel, _d(u),
+                                 W.ctypes.data_as(_i8p), _d(x), _d(mu), C.byref(n))
+    return dict(status=st, u=u, W=W, x=x, mu=mu, n_eqp=n.value)
 
 
 def admm(batch, k: int = 0, start_mode=START_TURBO, tol=1e-4, max_iter=500, as_max=None,

@@ -336,6 +336,41 @@ double orc_halfspace_project(int dp, const double* a, double d, const double* vi
   return th;
 }
 
+/* Local QP of agent i (Sec. IV.A) for a given coupling term
+ * h_t = sum_{j != i} (w_ij,t - y_ij,t), t = 1..T, assembled in the compact form
+ * (Hessian 2Q, 2Q_T, 2R plus rho n_c C'C on positions; linear term
+ * -2 Q_t x_ref - rho C' h_t) and solved by the active-set method. */
+int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, int as_max, double eps_rel,
+                      double* u, int8_t* W, double* x, double* mu, int* n_eqp) {
+  const int N = s->N, T = s->T, nx = s->nx, nu = s->nu, dp = s->dp;
+  double* Hx = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double* gx = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double Hu[16];
+  const int nc = N - 1;
+  const double* Qi = s->Qd + (size_t)i * nx;
+  const double* Qfi = s->Qfd + (size_t)i * nx;
+  const double* xr = s->x_ref + (size_t)i * nx;
+  for (int t = 1; t <= T; ++t) {
+    const double* Qt = (t < T) ? Qi : Qfi;
+    for (int r = 0; r < nx; ++r) {
+      double hx = 2.0 * Qt[r];
+      double g = -2.0 * Qt[r] * xr[r];
+      if (r < dp) {
+        hx += s->rho * nc;
+        g -= s->rho * h[(t - 1) * dp + r];
+      }
+      Hx[(size_t)(t - 1) * nx + r] = hx;
+      gx[(size_t)(t - 1) * nx + r] = g;
+    }
+  }
+  for (int c = 0; c < nu; ++c) Hu[c] = 2.0 * s->Rd[(size_t)i * nu + c];
+  orc_agent_qp q = {T, nx, nu, s->A, s->B, Hx, gx, Hu, s->x_init + (size_t)i * nx, s->umin, s->umax};
+  int st = orc_agent_qp_solve(&q, start, as_max, eps_rel, u, W, x, mu, n_eqp);
+  free(Hx);
+  free(gx);
+  return st;
+}
+
 int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   const int N = s->N, T = s->T, nx = s->nx, nu = s->nu, dp = s->dp;
   const int P = N * (N - 1) / 2;
@@ -377,9 +412,6 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
     reduction(+ : as_total) reduction(max : fail)
     for (int i = 0; i < N; ++i) {
       double* h = (double*)calloc((size_t)T * dp, sizeof(double));
-      double* Hx = (double*)malloc(sizeof(double) * (size_t)T * nx);
-      double* gx = (double*)malloc(sizeof(double) * (size_t)T * nx);
-      double Hu[16];
       for (int j = 0; j < N; ++j) {
         if (j == i) continue;
         int pk = (i < j) ? pair_index(N, i, j) : pair_index(N, j, i);
@@ -389,36 +421,17 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
           for (int c = 0; c < dp; ++c)
             h[t * dp + c] += w[((size_t)pk * T + t) * dp + c] - y[((size_t)pk * T + t) * dp + c];
       }
-      const int nc = N - 1;
-      const double* Qi = s->Qd + (size_t)i * nx;
-      const double* Qfi = s->Qfd + (size_t)i * nx;
-      const double* xr = s->x_ref + (size_t)i * nx;
-      for (int t = 1; t <= T; ++t) {
-        const double* Qt = (t < T) ? Qi : Qfi;
-        for (int r = 0; r < nx; ++r) {
-          double hx = 2.0 * Qt[r];
-          double g = -2.0 * Qt[r] * xr[r];
-          if (r < dp) {
-            hx += s->rho * nc;
-            g -= s->rho * h[(t - 1) * dp + r];
-          }
-          Hx[(size_t)(t - 1) * nx + r] = hx;
-          gx[(size_t)(t - 1) * nx + r] = g;
-        }
-      }
-      for (int c = 0; c < nu; ++c) Hu[c] = 2.0 * s->Rd[(size_t)i * nu + c];
-      orc_agent_qp q = {T, nx, nu, s->A, s->B, Hx, gx, Hu, s->x_init + (size_t)i * nx, s->umin, s->umax};
       int start;
       if (o->start_mode == ORC_START_COLD) start = ORC_QP_COLD;
       else if (k == 0) start = (o->start_mode == ORC_START_TURBO) ? ORC_QP_LQR : ORC_QP_COLD;
       else start = ORC_QP_GIVEN;
       int neqp = 0;
-      int st = orc_agent_qp_solve(&q, start, o->as_max, o->eps_rel, res->U + (size_t)i * T * nu,
-                                  res->W + (size_t)i * T * nu, res->X + (size_t)i * (T + 1) * nx,
-                                  res->mu + (size_t)i * T * nu, &neqp);
+      int st = orc_agent_xupdate(s, i, h, start, o->as_max, o->eps_rel, res->U + (size_t)i * T * nu,
+                                 res->W + (size_t)i * T * nu, res->X + (size_t)i * (T + 1) * nx,
+                                 res->mu + (size_t)i * T * nu, &neqp);
       as_total += neqp;
       if (st > fail) fail = st;
-      free(h); free(Hx); free(gx);
+      free(h);
     }
     res->iters = k + 1;
     if (fail) { res->status = fail; break; }

@@ -101,6 +101,11 @@ typedef struct {
 double orc_halfspace_project(int dp, const double* a, double d, const double* vi, const double* vj,
                              double* wi, double* wj);
 
+/* x-update of agent i alone for a given coupling term h [T][dp] (the sum over
+ * partners of consensus copy minus scaled dual); start is an ORC_QP_* kind. */
+int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, int as_max, double eps_rel,
+                      double* u, int8_t* W, double* x, double* mu, int* n_eqp);
+
 int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res);
 /* Scenarios in parallel (OpenMP dynamic schedule); returns number of threads used. */
 int orc_admm_batch(const orc_scenario* s, int n_scen, const orc_options* o, orc_result* res,

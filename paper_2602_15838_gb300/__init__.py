@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4
 CONVERGED, NOT_CONVERGED, QP_FAIL, NUMERIC = 0, 1, 2, 3
 START = {"cold": 0, "hot": 1, "turbo": 2}
 FLAG_NO_FUSED_PAIR_GATHER, FLAG_NO_STRUCTURE = 1, 2
-MODE = {"batched": 0, "plain": 1}
+MODE = {"batched": 0, "plain": 1, "graph": 2}
 
 _dp = C.POINTER(C.c_double)
 _i32p = C.POINTER(C.c_int32)

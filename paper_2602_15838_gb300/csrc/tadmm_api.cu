@@ -114,6 +114,10 @@ static bool is_double_integrator(const tadmm_batch* b) {
 static void free_all(tadmm_handle* h) {
   if (!h) return;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->wexec) cudaGraphExecDestroy(h->wexec);
+  void* gptrs[] = {h->gs_iter, h->gs_active, h->gs_need, h->gs_fail, h->gs_rb, h->gs_sb};
+  for (void* p : gptrs)
+    if (p) cudaFree(p);
   void* ptrs[] = {h->meta,   h->order, h->pairs, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
                   h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->X,      h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
@@ -185,7 +189,8 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   if (opt) o = *opt;
   if (o.precision != 64 && o.precision != 32) return set_error(TADMM_EINVAL, "precision must be 64 or 32");
   if (o.start_mode < 0 || o.start_mode > 2) return set_error(TADMM_EINVAL, "start_mode must be 0, 1 or 2");
-  if (o.mode != TADMM_MODE_BATCHED && o.mode != TADMM_MODE_PLAIN) return set_error(TADMM_EINVAL, "bad mode");
+  if (o.mode != TADMM_MODE_BATCHED && o.mode != TADMM_MODE_PLAIN && o.mode != TADMM_MODE_GRAPH)
+    return set_error(TADMM_EINVAL, "bad mode");
   if (o.as_max < 0 || o.eps_rel < 0 || !std::isfinite(o.eps_rel)) return set_error(TADMM_EINVAL, "bad as_max / eps_rel");
   if (o.threads_per_cta != 0 && (o.threads_per_cta < 32 || o.threads_per_cta > 256 || o.threads_per_cta % 32))
     return set_error(TADMM_EINVAL, "threads_per_cta must be 0 or a multiple of 32 in [32, 256]");
@@ -317,6 +322,9 @@ extern "C" int tadmm_solve(tadmm_handle* h, double tol, int32_t max_iter, void* 
   int rc;
   if (h->opt.mode == TADMM_MODE_PLAIN) {
     auto run = [&]() -> int { TADMM_DISPATCH(h, solve_plain(h, tol, max_iter, st)); };
+    rc = run();
+  } else if (h->opt.mode == TADMM_MODE_GRAPH) {
+    auto run = [&]() -> int { TADMM_DISPATCH(h, solve_graph(h, tol, max_iter, st)); };
     rc = run();
   } else {
     auto run = [&]() -> int { TADMM_DISPATCH(h, solve_batched(h, tol, max_iter, st)); };

@@ -82,6 +82,13 @@ struct tadmm_handle {
   int solved = 0;
   int64_t launches = 0;   // kernel launches enqueued by the last solve
   BwdBufs bwd;
+
+  // graph mode (conditional WHILE node over the per-iteration phase kernels)
+  void *gs_iter = nullptr, *gs_active = nullptr, *gs_need = nullptr, *gs_fail = nullptr, *gs_rb = nullptr,
+       *gs_sb = nullptr;
+  cudaGraphExec_t wexec = nullptr;
+  double w_tol = -1.0;
+  int w_iter = -1;
 };
 
 namespace tadmm {
@@ -94,6 +101,7 @@ struct Impl {
   static int import_inputs(tadmm_handle* h, cudaStream_t st);
   static int solve_batched(tadmm_handle* h, double tol, int max_iter, cudaStream_t st);
   static int solve_plain(tadmm_handle* h, double tol, int max_iter, cudaStream_t st);
+  static int solve_graph(tadmm_handle* h, double tol, int max_iter, cudaStream_t st);
   static int export_solution(tadmm_handle* h, double* X, double* U, double* theta, int8_t* W,
                              cudaStream_t st);
   static int max_ctas_per_sm(int tpc, int variant, const tadmm_handle* h);

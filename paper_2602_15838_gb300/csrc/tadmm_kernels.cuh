@@ -111,6 +111,188 @@ __global__ void k_finish(Dev<F> D, int sc, int status, int iters, int cur, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Graph mode: every phase is a grid-wide kernel over all scenarios' units and
+// one CUDA graph with a conditional WHILE node repeats the iteration on the
+// device until every scenario has stopped (no host round trip per iteration).
+// Scenario k's iteration parity fixes its levels: X level (k & 1) holds p^k,
+// theta slot k % 3 holds theta^k.
+// ---------------------------------------------------------------------------
+struct GState {
+  int32_t* iter;
+  int32_t* active;
+  int32_t* need;
+  int32_t* fail;
+  unsigned long long* rb;
+  unsigned long long* sb;
+};
+
+__device__ __forceinline__ void scen_max(unsigned long long* arr, int sc, unsigned long long v, bool valid) {
+  const unsigned full = __activemask();
+  const int lead_sc = __shfl_sync(full, sc, __ffs(full) - 1);
+  if (__all_sync(full, valid && sc == lead_sc)) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(full, v, o);
+      v = w > v ? w : v;
+    }
+    if ((threadIdx.x & 31) == __ffs(full) - 1 && v) atomicMax(&arr[sc], v);
+  } else if (valid && v) {
+    atomicMax(&arr[sc], v);
+  }
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void k_g_init(Dev<F> D, GState G) {
+  const int sc = blockIdx.x;
+  const ScenMeta s = D.meta[sc];
+  init_phase<F, NX, NU, DP>(D, s, threadIdx.x, blockDim.x);
+  if (threadIdx.x == 0) {
+    G.iter[sc] = 0;
+    G.active[sc] = 1;
+    G.need[sc] = 0;
+    G.fail[sc] = 0;
+    G.rb[sc] = 0;
+    G.sb[sc] = 0;
+    D.eqp[sc] = 0;
+    D.fact[sc] = 0;
+    D.status[sc] = ST_NOT_CONVERGED;
+    D.iters[sc] = 0;
+  }
+}
+
+template <typename F, int NX, int NU, int DP, bool DI>
+__global__ void __launch_bounds__(128) k_g_xupdate(Dev<F> D, GState G, const int32_t* __restrict__ agent_scen,
+                                                   int64_t tot_agents) {
+  __shared__ Model<F, NX, NU> M;
+  load_model<F, NX, NU>(M, D.model);
+  __syncthreads();
+  const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ga >= tot_agents) return;
+  const int sc = agent_scen[ga];
+  if (!G.active[sc]) return;
+  const ScenMeta s = D.meta[sc];
+  const int i = (int)(ga - s.agent_off), k = G.iter[sc];
+  unsigned long long neqp = 0, nfact = 0;
+  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, (k + 1) & 1, i, s.N, neqp, nfact);
+  if (st) atomicMax(&G.fail[sc], st);
+  if (neqp) atomicAdd(&D.eqp[sc], neqp);
+  if (nfact) atomicAdd(&D.fact[sc], nfact);
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void __launch_bounds__(128) k_g_pair(Dev<F> D, GState G, const int32_t* __restrict__ pair_scen,
+                                                int64_t tot_pairs) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tm1 = blockIdx.y;
+  int sc = 0;
+  bool valid = gp < tot_pairs;
+  if (valid) sc = pair_scen[gp];
+  ScenMeta s;
+  if (valid) {
+    s = D.meta[sc];
+    valid = tm1 < s.T && G.active[sc] && !G.fail[sc];
+  }
+  unsigned long long rb = 0;
+  if (valid) {
+    const int k = G.iter[sc];
+    const int64_t q = (int64_t)tm1 * s.P + (gp - s.pair_off);
+    pair_phase<F, NX, NU, DP>(D, s, k & 1, k % 3, (k + 1) % 3, q, (int64_t)s.P * s.T, rb);
+  }
+  scen_max(G.rb, sc, rb, valid);
+}
+
+template <typename F>
+__global__ void k_g_check1(Dev<F> D, GState G) {
+  for (int sc = blockIdx.x * blockDim.x + threadIdx.x; sc < D.n_scen; sc += gridDim.x * blockDim.x) {
+    G.need[sc] = 0;
+    if (!G.active[sc] || G.fail[sc]) continue;
+    const F r = from_bits(G.rb[sc], F(0));
+    if (finite_(r) && (r <= F(D.tol) || G.iter[sc] + 1 == D.max_iter)) G.need[sc] = 1;
+  }
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void __launch_bounds__(128) k_g_dual(Dev<F> D, GState G, const int32_t* __restrict__ pair_scen,
+                                                int64_t tot_pairs) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tm1 = blockIdx.y;
+  int sc = 0;
+  bool valid = gp < tot_pairs;
+  if (valid) sc = pair_scen[gp];
+  ScenMeta s;
+  if (valid) {
+    s = D.meta[sc];
+    valid = tm1 < s.T && G.need[sc];
+  }
+  unsigned long long sb = 0;
+  if (valid) {
+    const int k = G.iter[sc];
+    const int64_t q = (int64_t)tm1 * s.P + (gp - s.pair_off);
+    dual_phase<F, NX, NU, DP>(D, s, k & 1, (k + 2) % 3, k % 3, (k + 1) % 3, q, (int64_t)s.P * s.T, sb);
+  }
+  scen_max(G.sb, sc, sb, valid);
+}
+
+// Convergence decisions (in the arithmetic type F), then the WHILE condition.
+template <typename F>
+__global__ void k_g_check2(Dev<F> D, GState G, cudaGraphConditionalHandle cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int sc = threadIdx.x; sc < D.n_scen; sc += blockDim.x) {
+    if (!G.active[sc]) continue;
+    const int k = G.iter[sc];
+    const double rho = D.meta[sc].rho;
+    int stop = 0, status = ST_NOT_CONVERGED, cur = ((k + 1) & 1) | (((k + 1) % 3) << 1);
+    const F r = from_bits(G.rb[sc], F(0));
+    if (G.fail[sc]) {
+      stop = 1;
+      status = G.fail[sc];
+      cur = (k & 1) | ((k % 3) << 1);
+    } else if (!finite_(r)) {
+      stop = 1;
+      status = ST_NUMERIC;
+    } else if (G.need[sc]) {
+      const F sres = F(rho) * from_bits(G.sb[sc], F(0));
+      D.res[2 * sc + 1] = double(sres);
+      if (!finite_(sres)) { stop = 1; status = ST_NUMERIC; }
+      else if (r <= F(D.tol) && sres <= F(D.tol)) { stop = 1; status = ST_CONVERGED; }
+      else if (k + 1 == D.max_iter) stop = 1;
+    }
+    D.res[2 * sc] = double(r);
+    D.iters[sc] = k + 1;
+    if (stop) {
+      G.active[sc] = 0;
+      D.status[sc] = status;
+      D.cur_lvl[sc] = cur;
+    } else {
+      G.iter[sc] = k + 1;
+      mine = 1;
+    }
+    G.rb[sc] = 0;
+    G.sb[sc] = 0;
+  }
+  if (mine) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+
+template <typename F, int NX, int NU, int DP>
+__global__ void __launch_bounds__(128) k_g_gather(Dev<F> D, GState G, const int32_t* __restrict__ agent_scen,
+                                                  int64_t tot_agents) {
+  const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tm1 = blockIdx.y;
+  if (ga >= tot_agents) return;
+  const int sc = agent_scen[ga];
+  if (!G.active[sc]) return;
+  const ScenMeta s = D.meta[sc];
+  if (tm1 >= s.T) return;
+  const int k1 = G.iter[sc];  // already advanced: levels of iterate k1 = k + 1
+  const int64_t idx = (int64_t)tm1 * s.N + (ga - s.agent_off);
+  gather_phase<F, NX, NU, DP>(D, s, k1 & 1, k1 % 3, (k1 + 2) % 3, idx, (int64_t)s.N * s.T);
+}
+
+// ---------------------------------------------------------------------------
 // Import (caller layouts, float64) and export kernels
 // ---------------------------------------------------------------------------
 template <typename F>
@@ -420,6 +602,83 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
   }
   h->launches = launches;
   return cuda_check(cudaGetLastError(), "plain-mode launches");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::solve_graph(tadmm_handle* h, double tol, int max_iter, cudaStream_t st) {
+  int rc;
+  if (!h->gs_iter) {
+    const size_t n = (size_t)h->n_scen;
+    if (cudaMalloc(&h->gs_iter, 4 * n) != cudaSuccess || cudaMalloc(&h->gs_active, 4 * n) != cudaSuccess ||
+        cudaMalloc(&h->gs_need, 4 * n) != cudaSuccess || cudaMalloc(&h->gs_fail, 4 * n) != cudaSuccess ||
+        cudaMalloc(&h->gs_rb, 8 * n) != cudaSuccess || cudaMalloc(&h->gs_sb, 8 * n) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(TADMM_ENOMEM, "graph-mode state allocation failed");
+    }
+  }
+  GState G{(int32_t*)h->gs_iter, (int32_t*)h->gs_active, (int32_t*)h->gs_need, (int32_t*)h->gs_fail,
+           (unsigned long long*)h->gs_rb, (unsigned long long*)h->gs_sb};
+  Dev<F> D = make_dev<F>(h);
+  D.tol = tol;
+  D.max_iter = max_iter;
+  int tmax = 0;
+  for (const ScenMeta& m : h->meta_h) tmax = std::max(tmax, m.T);
+  if (!h->wexec || h->w_tol != tol || h->w_iter != max_iter) {
+    if (h->wexec) {
+      cudaGraphExecDestroy(h->wexec);
+      h->wexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if ((rc = cuda_check(cudaGraphCreate(&g, 0), "graph create"))) return rc;
+    cudaGraphConditionalHandle cond;
+    if ((rc = cuda_check(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault), "cond handle"))) {
+      cudaGraphDestroy(g);
+      return rc;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((rc = cuda_check(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node"))) {
+      cudaGraphDestroy(g);
+      return rc;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((rc = cuda_check(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal), "body capture"))) {
+      cudaGraphDestroy(g);
+      return rc;
+    }
+    const dim3 gx(grid_for(h->tot_agents, 128, 1 << 30));
+    const dim3 gp(grid_for(h->tot_pairs, 128, 1 << 30), tmax);
+    const dim3 gg(grid_for(h->tot_agents, 128, 1 << 30), tmax);
+    if (h->di)
+      k_g_xupdate<F, NX, NU, DP, true><<<gx, 128, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+    else
+      k_g_xupdate<F, NX, NU, DP, false><<<gx, 128, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+    if (h->tot_pairs > 0) k_g_pair<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);
+    k_g_check1<F><<<grid_for(h->n_scen, 128), 128, 0, h->cap_stream>>>(D, G);
+    if (h->tot_pairs > 0) k_g_dual<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);
+    k_g_check2<F><<<1, 1024, 0, h->cap_stream>>>(D, G, cond);
+    k_g_gather<F, NX, NU, DP><<<gg, 128, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &body);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_check(le != cudaSuccess ? le : ee, "graph body capture");
+    }
+    rc = cuda_check(cudaGraphInstantiate(&h->wexec, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    if (rc) return rc;
+    h->w_tol = tol;
+    h->w_iter = max_iter;
+  }
+  k_g_init<F, NX, NU, DP><<<h->n_scen, 128, 0, st>>>(D, G);
+  if ((rc = cuda_check(cudaGetLastError(), "graph-mode init"))) return rc;
+  h->launches = 1;
+  return cuda_check(cudaGraphLaunch(h->wexec, st), "graph launch");
 }
 
 template <typename F, int NX, int NU, int DP>
