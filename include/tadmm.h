@@ -144,7 +144,7 @@ int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* t
                    int32_t* ctas_out, int32_t* variant_out);
 
 /* Implicit-KKT gradients of a loss l(X) at the final active set of the last
- * solve (spec differentiation pattern; the paper has no gradient).  The
+ * solve (the paper differentiates nothing; this is an addition).  The
  * active set is the final bound working set of every agent plus the halfspaces
  * whose projection step exceeds theta_eps.  At that active set the
  * centralized QP of Eq. (1) (Sec. III.A) with linearized halfspaces is an

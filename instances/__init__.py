@@ -8,7 +8,8 @@ same arrays from it.
 from .generator import (  # noqa: F401
     Batch,
     SplitMix64,
-    make_config,
+    make_workload,
+    WORKLOADS,
     make_batch,
     double_integrator,
     pair_list,

@@ -2,19 +2,19 @@
 
 Workload shapes follow the paper's benchmark family (2D double integrator
 agents crossing a shared workspace with dense all-pairs collision coupling,
-Sec. V.A) at the sizes of the five synthetic configurations:
+Sec. V.A) at five synthetic sizes (make_workload names):
 
-  1  N=2 agents on a radius-5 circle, antipodal goals, jitter sigma 0.05,
-     T=20, d_min=0.5, rho=1.
-  2  N=14 agents on a radius-5 circle, antipodal goals, jitter sigma 0.1,
-     T=20, d_min=0.5, rho=1.
-  3  a batch of scenarios with N ~ U{2..32}, T ~ U{20..40}; starts uniform in
-     [-5,5]^2 (rejection-sampled >= 2*d_min apart), goals a random
-     permutation of the starts; d_min=0.4, rho=1.
-  4  N=512 3D double integrators, T=40, |u|<=2, starts uniform in
-     [-20,20]^3 (>= 2*d_min apart), goals = -starts; d_min=0.5, rho=2.
-  5  64 scenarios x 16 agents, T=30, drawn as in 3, plus seeded position
-     targets uniform in [-5,5]^2 for a tracking loss.
+  "pair"        N=2 agents on a radius-5 circle, antipodal goals, jitter
+                sigma 0.05, T=20, d_min=0.5, rho=1.
+  "ring14"      N=14 agents on a radius-5 circle, antipodal goals, jitter
+                sigma 0.1, T=20, d_min=0.5, rho=1.
+  "mixed"       a batch of scenarios with N ~ U{2..32}, T ~ U{20..40}; starts
+                uniform in [-5,5]^2 (rejection-sampled >= 2*d_min apart), goals
+                a random permutation of the starts; d_min=0.4, rho=1.
+  "swarm3d"     N=512 3D double integrators, T=40, |u|<=2, starts uniform in
+                [-20,20]^3 (>= 2*d_min apart), goals = -starts; d_min=0.5, rho=2.
+  "diff"        64 scenarios x 16 agents, T=30, drawn as "mixed", plus seeded
+                position targets uniform in [-5,5]^2 for a tracking loss.
 
 Collision linearization (Sec. III.A: the distance constraint is replaced by a
 halfspace built from reference trajectories; the references are straight
@@ -30,8 +30,9 @@ velocity, c = 1 lines) is generally infeasible and serves as a negative case.
 
 Random numbers: SplitMix64 (Steele, Lea, Flood 2014) as a counter-based
 stream, output n = mix(seed + (n+1) * 0x9E3779B97F4A7C15); uniforms are the
-top 53 bits; normals by Box-Muller.  Stream seed for scenario k of config c is
-(c << 32) + k, so the first k scenarios of a batch do not depend on its size.
+top 53 bits; normals by Box-Muller.  Stream seed for scenario k of workload
+stream id c (1..5 in the order listed above) is (c << 32) + k, so the first k
+scenarios of a batch do not depend on its size.
 
 Packed batch layout (all float64 unless stated; row-major):
   N[S], T[S]                 int32 agent count and horizon per scenario
@@ -43,7 +44,7 @@ Packed batch layout (all float64 unless stated; row-major):
   w0 [sum_s N_s T_s, dp]     initial consensus positions (the guesses),
                              scenario, agent, t = 1..T
   d_min[S], rho[S]
-  targets [sum_s N_s T_s, dp] (config 5 only) loss targets
+  targets [sum_s N_s T_s, dp] ("diff" only) loss targets
 """
 from __future__ import annotations
 
@@ -244,7 +245,9 @@ def build_scenario(starts: np.ndarray, goals: np.ndarray, T: int, dt: float, d_m
     return x_init, x_ref, a, w0, c
 
 
-CONFIG_DEFAULTS = {
+WORKLOADS = {"pair": 1, "ring14": 2, "mixed": 3, "swarm3d": 4, "diff": 5}
+
+_DEFAULTS = {
     1: dict(dp=2, n_scen=1),
     2: dict(dp=2, n_scen=1),
     3: dict(dp=2, n_scen=4096),
@@ -304,13 +307,14 @@ def _scenario_points(cfg: int, k: int, rng: SplitMix64, dp: int, N_override=None
     raise ValueError(f"unknown config {cfg}")
 
 
-def make_config(cfg: int, n_scen: Optional[int] = None, literal: bool = False,
-                N_override: Optional[int] = None, T_override: Optional[int] = None,
-                dt: float = 0.1, first: int = 0) -> Batch:
-    """Instances of synthetic configuration `cfg` (1..5), seeded per scenario;
-    scenario ids first .. first + n_scen - 1."""
-    dp = CONFIG_DEFAULTS[cfg]["dp"]
-    S = CONFIG_DEFAULTS[cfg]["n_scen"] if n_scen is None else n_scen
+def make_workload(name: str, n_scen: Optional[int] = None, literal: bool = False,
+                  N_override: Optional[int] = None, T_override: Optional[int] = None,
+                  dt: float = 0.1, first: int = 0) -> Batch:
+    """Instances of the named synthetic workload ("pair", "ring14", "mixed",
+    "swarm3d", "diff"), seeded per scenario; scenario ids first .. first+n_scen-1."""
+    cfg = WORKLOADS[name]
+    dp = _DEFAULTS[cfg]["dp"]
+    S = _DEFAULTS[cfg]["n_scen"] if n_scen is None else n_scen
     scen = []
     for k in range(first, first + S):
         rng = SplitMix64((cfg << 32) + k)
@@ -322,7 +326,7 @@ def make_config(cfg: int, n_scen: Optional[int] = None, literal: bool = False,
         scen.append(dict(N=N, T=T, x_init=x_init, x_ref=x_ref, a=a, w0=w0, d=d, rho=rho,
                          umax=umax, c=c, targets=targets))
     umax = scen[0]["umax"]
-    return make_batch(scen, dp=dp, dt=dt, umax=umax, meta=dict(config=cfg, literal=literal))
+    return make_batch(scen, dp=dp, dt=dt, umax=umax, meta=dict(workload=name, literal=literal))
 
 
 def make_batch(scen: List[dict], dp: int, dt: float, umax: float, meta: Optional[dict] = None,

@@ -54,8 +54,8 @@ def _create_rc(tg, batch, **opt):
 @pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec"])
 def test_invalid_inputs_rejected_on_host(libtadmm, fault):
     tg, _ = libtadmm
-    from instances import make_config
-    b = make_config(1)
+    from instances import make_workload
+    b = make_workload("pair")
     opt = {}
     if fault == "nan_q":
         b.Qd = b.Qd.copy(); b.Qd[0, 1] = np.nan

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from instances import make_config
+from instances import make_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def _rel(a, b):
 
 
 def _case(N, T, n_scen=2):
-    b = make_config(5, n_scen=n_scen, N_override=N, T_override=T)
+    b = make_workload("diff", n_scen=n_scen, N_override=N, T_override=T)
     return b
 
 
@@ -103,7 +103,7 @@ def test_gradient_full_size_differentiation_scenario_fp64(tg):
     rho = 1): the Schur complement is ill-conditioned, so the polished solution
     is checked through its own equality residual and both gradients agree to
     the conditioning-limited 1e-4."""
-    b = make_config(5, n_scen=1)
+    b = make_workload("diff", n_scen=1)
     iters = 1000
     s = tg.Solver(b, precision=64)
     s.solve(0.0, iters)

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from instances import make_config, random_scenario
+from instances import make_workload, random_scenario
 from instances.generator import make_batch, build_scenario
 
 pytestmark = pytest.mark.gpu
@@ -60,8 +60,8 @@ def nondegenerate_w_equal(w_gpu, orc, batch, k=0):
 
 @pytest.mark.parametrize("start", ["turbo", "hot", "cold"])
 @pytest.mark.parametrize("k", [1, 2, 3, 5])
-def test_config1_every_iterate_fp64(tg, start, k):
-    b = make_config(1)
+def test_pair_every_iterate_fp64(tg, start, k):
+    b = make_workload("pair")
     g, _ = gpu_run(tg, b, 0.0, k, start=start)
     o = oracle.admm(b, 0, start_mode=START[start], tol=0.0, max_iter=k)
     g = g[0]
@@ -73,8 +73,8 @@ def test_config1_every_iterate_fp64(tg, start, k):
     assert ok
 
 
-def test_config1_converged_fp64(tg):
-    b = make_config(1)
+def test_pair_converged_fp64(tg):
+    b = make_workload("pair")
     g, cnt = gpu_run(tg, b, 1e-4, 500)
     o = oracle.admm(b, 0, tol=1e-4, max_iter=500)
     g = g[0]
@@ -88,8 +88,8 @@ def test_config1_converged_fp64(tg):
 
 
 @pytest.mark.parametrize("k", [1, 4, 30])
-def test_config2_iterates_fp64(tg, k):
-    b = make_config(2)
+def test_ring14_iterates_fp64(tg, k):
+    b = make_workload("ring14")
     g, _ = gpu_run(tg, b, 0.0, k)
     o = oracle.admm(b, 0, tol=0.0, max_iter=k, nthreads=8)
     g = g[0]
@@ -100,8 +100,8 @@ def test_config2_iterates_fp64(tg, k):
     assert ok
 
 
-def test_config2_plain_mode_matches_batched(tg):
-    b = make_config(2)
+def test_ring14_plain_mode_matches_batched(tg):
+    b = make_workload("ring14")
     gb, cb = gpu_run(tg, b, 1e-4, 60)
     gp, cp = gpu_run(tg, b, 1e-4, 60, mode="plain")
     assert gb[0]["iters"] == gp[0]["iters"]
@@ -137,10 +137,10 @@ def test_ragged_batch_and_edge_cases_fp64(tg):
     assert g1[0]["status"] == tg.CONVERGED and g1[0]["iters"] == 1
 
 
-def test_config3_sampled_scenarios_full_batch(tg):
+def test_mixed_batch_sampled_scenarios_full_size(tg):
     """Full 4096-scenario batch in the benchmark's launch shape: sampled
     scenarios agree with the oracle after a few iterations."""
-    b = make_config(3)
+    b = make_workload("mixed")
     s = tg.Solver(b)
     s.solve(0.0, 4)
     out = s.split(s.solution())
@@ -152,10 +152,10 @@ def test_config3_sampled_scenarios_full_batch(tg):
         assert rel(out[k]["theta"], o["theta"]) <= 1e-9, k
 
 
-def test_config4_reduced_3d_fp64(tg):
-    """3D double integrator (nx=6, nu=3) at the large-coupling configuration's
+def test_swarm3d_reduced_fp64(tg):
+    """3D double integrator (nx=6, nu=3) of the 512-agent swarm workload with its
     model, horizon and spacing rules with fewer agents."""
-    b = make_config(4, N_override=12)
+    b = make_workload("swarm3d", N_override=12)
     g, _ = gpu_run(tg, b, 0.0, 5)
     o = oracle.admm(b, 0, tol=0.0, max_iter=5, nthreads=8)
     assert rel(g[0]["X"], o["X"]) <= 1e-9
@@ -163,8 +163,8 @@ def test_config4_reduced_3d_fp64(tg):
     assert rel(g[0]["U"], o["U"]) <= 1e-9
 
 
-def test_config2_fp32_against_fp64_oracle(tg):
-    b = make_config(2)
+def test_ring14_fp32_against_fp64_oracle(tg):
+    b = make_workload("ring14")
     g, _ = gpu_run(tg, b, 0.0, 10, precision=32)
     o = oracle.admm(b, 0, tol=0.0, max_iter=10, nthreads=8)
     assert rel(g[0]["X"], o["X"]) <= 1e-4
@@ -172,13 +172,13 @@ def test_config2_fp32_against_fp64_oracle(tg):
 
 
 def test_literal_infeasible_not_converged(tg):
-    b = make_config(1, literal=True)
+    b = make_workload("pair", literal=True)
     g, _ = gpu_run(tg, b, 1e-4, 200)
     assert g[0]["status"] == tg.NOT_CONVERGED and g[0]["iters"] == 200
 
 
 def test_as_max_one_reports_qp_fail(tg):
-    b = make_config(2)
+    b = make_workload("ring14")
     g, _ = gpu_run(tg, b, 1e-4, 20, start="cold", as_max=1)
     assert g[0]["status"] == tg.QP_FAIL
 
@@ -187,7 +187,7 @@ def test_fused_and_structured_paths_equal_plain_paths(tg):
     """The shared-memory fused pair/gather sweep and the double-integrator
     structured products give the same iterates as the separate sweeps and the
     dense products."""
-    b = make_config(3, n_scen=24)
+    b = make_workload("mixed", n_scen=24)
     ref, _ = gpu_run(tg, b, 0.0, 8, flags=tg.FLAG_NO_FUSED_PAIR_GATHER | tg.FLAG_NO_STRUCTURE)
     for fl in (0, tg.FLAG_NO_FUSED_PAIR_GATHER, tg.FLAG_NO_STRUCTURE):
         g, _ = gpu_run(tg, b, 0.0, 8, flags=fl)
@@ -201,7 +201,7 @@ def test_fused_and_structured_paths_equal_plain_paths(tg):
 def test_general_dynamics_fp64(tg, k):
     """Dynamics that are not a double integrator (damped velocity, skewed input)
     take the dense-product path; iterates match the oracle."""
-    b = make_config(1)
+    b = make_workload("pair")
     b.A = b.A.copy()
     b.A[2, 2] = b.A[3, 3] = 0.95
     b.A[0, 1] = 0.01
@@ -217,7 +217,7 @@ def test_general_dynamics_fp64(tg, k):
 def test_graph_mode_matches_batched(tg):
     """Grid-wide phase kernels under the CUDA-graph WHILE node reproduce the
     persistent kernel, including scenarios that stop at different iterations."""
-    b = make_config(3, n_scen=24)
+    b = make_workload("mixed", n_scen=24)
     for tol, it in ((0.0, 8), (1e-4, 300)):
         gb, cb = gpu_run(tg, b, tol, it)
         gg, cg = gpu_run(tg, b, tol, it, mode="graph")
@@ -229,12 +229,12 @@ def test_graph_mode_matches_batched(tg):
         assert np.array_equal(cb["eqp"], cg["eqp"])
 
 
-def test_config4_full_size_graph_mode_sampled(tg):
+def test_swarm3d_full_size_graph_mode_sampled(tg):
     """512 agents, 3D, T = 40 (130816 pairs x 40 steps) in graph mode.  After
     one iteration, sampled agents' x-updates and the projections of sampled
     pairs are recomputed one by one by the oracle (h = n_c w0 at the first
     iteration); two iterations of graph and plain mode agree everywhere."""
-    b = make_config(4)
+    b = make_workload("swarm3d")
     N, T = int(b.N[0]), int(b.T[0])
     g1, _ = gpu_run(tg, b, 0.0, 1, mode="graph")
     g1 = g1[0]

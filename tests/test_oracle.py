@@ -14,7 +14,7 @@ import pytest
 from scipy.optimize import lsq_linear, minimize
 
 import oracle
-from instances import make_config, random_scenario, pair_list
+from instances import make_workload, random_scenario, pair_list
 from instances.generator import SplitMix64, make_batch, build_scenario
 from tests.helpers import agent_condensed_qp, condensed, costate_gradient, random_agent_qp
 
@@ -34,19 +34,19 @@ def test_table1_problem_dimensions():
         assert N * ((T + 1) * nx + T * nu) == nvar
         assert N * T * nx == ndyn
         assert ncol in (N * (N - 1) // 2 * T, N * (N - 1) // 2 * (T + 1))
-    b = make_config(2)
+    b = make_workload("ring14")
     assert b.a.shape[0] == 91 * 20 and b.w0.shape[0] == 14 * 20
     assert b.N[0] == 14 and b.T[0] == 20
 
 
 # ------------------------------------------------------------------ generator
 def test_generator_deterministic_and_certified():
-    b1 = make_config(3, n_scen=6)
-    b2 = make_config(3, n_scen=6)
+    b1 = make_workload("mixed", n_scen=6)
+    b2 = make_workload("mixed", n_scen=6)
     for f in ("N", "T", "x_init", "x_ref", "a", "w0"):
         assert np.array_equal(getattr(b1, f), getattr(b2, f))
     # the first scenarios do not depend on the batch size
-    b3 = make_config(3, n_scen=3)
+    b3 = make_workload("mixed", n_scen=3)
     assert np.array_equal(b3.a, b1.a[:b3.a.shape[0]])
     for k in range(b1.n_scen):
         s = b1.scenario(k)
@@ -224,7 +224,7 @@ def test_admm_single_agent_one_iteration():
 def test_admm_start_modes_give_same_iterates():
     """Cold, hot and turbo starts only change the active-set path: every ADMM
     iterate is the unique per-agent QP solution, so the runs agree."""
-    b = make_config(1)
+    b = make_workload("pair")
     outs = [oracle.admm(b, 0, start_mode=m, max_iter=4, tol=0.0) for m in
             (oracle.START_COLD, oracle.START_HOT, oracle.START_TURBO)]
     for o in outs[1:]:
@@ -316,7 +316,7 @@ def test_literal_reading_is_infeasible_and_does_not_converge():
     """Zero initial velocity with c = 1 guess lines (the literal reading): the
     agents cannot swap sides in 2 s, the halfspace QP is infeasible and the
     residual stalls."""
-    b = make_config(1, literal=True)
+    b = make_workload("pair", literal=True)
     r = oracle.admm(b, 0, max_iter=300)
     assert r["status"] == oracle.NOT_CONVERGED and r["iters"] == 300
     assert r["r"] > 1e-2

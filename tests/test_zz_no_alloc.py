@@ -14,7 +14,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
-from instances import make_config
+from instances import make_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +78,7 @@ def test_noalloc_matches_regular_path_two_calls_in_a_row():
     build.build()
     import paper_2602_15838_gb300 as tg
 
-    cases = [(make_config(2), 0.0, 25), (make_config(1), 1e-4, 500)]
+    cases = [(make_workload("ring14"), 0.0, 25), (make_workload("pair"), 1e-4, 500)]
     for b, tol, max_iter in cases:
         got = _noalloc_call(tg, torch, b, tol, max_iter)
         ref = _regular(tg, b, tol, max_iter)
