@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--tpc", type=int, default=0, help="threads per CTA (with --no-autotune)")
+    p.add_argument("--variant", type=int, default=0, help="kernel register variant (with --no-autotune)")
     return p.parse_args()
 
 
@@ -232,8 +234,9 @@ def run_ours(args, rank, world):
             dist.barrier()
 
     batch = workload_batch(args.n_scen, rank)
-    solver = tg.Solver(batch, precision=args.precision, start="turbo", mode="batched")
-    tpc, cps, var = (0, 0, 0) if args.no_autotune else solver.autotune(probe_iter=10)
+    solver = tg.Solver(batch, precision=args.precision, start="turbo", mode="batched",
+                       threads_per_cta=args.tpc, kernel_variant=args.variant)
+    tpc, cps, var = (args.tpc, 0, args.variant) if args.no_autotune else solver.autotune(probe_iter=10)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
