@@ -101,6 +101,7 @@ typedef struct {
 /* option flags (results are the same either way; for testing and measurement) */
 #define TADMM_FLAG_NO_FUSED_PAIR_GATHER 1 /* separate pair and gather sweeps in the batched kernel */
 #define TADMM_FLAG_NO_STRUCTURE 2         /* dense A, B products even for a double integrator */
+#define TADMM_FLAG_NO_GROUPING 4          /* one scenario per CTA (no packing of small scenarios) */
 
 typedef struct tadmm_handle tadmm_handle;
 

@@ -118,6 +118,9 @@ static void free_all(tadmm_handle* h) {
   void* gptrs[] = {h->gs_iter, h->gs_active, h->gs_need, h->gs_fail, h->gs_rb, h->gs_sb};
   for (void* p : gptrs)
     if (p) cudaFree(p);
+  void* ptrs0[] = {h->goff, h->gmem, h->gorder};
+  for (void* p : ptrs0)
+    if (p) cudaFree(p);
   void* ptrs[] = {h->meta,   h->order, h->pairs, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
                   h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->X,      h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
@@ -246,6 +249,63 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
     work[s] = double(h->meta_h[s].P) * h->meta_h[s].T * 30.0 + double(h->meta_h[s].N) * h->meta_h[s].T * 400.0;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
 
+  // Scenario groups for the persistent kernel: scenarios of equal horizon packed
+  // first-fit-decreasing into groups of at most 32 agents (one lane per agent);
+  // scenarios with more than 32 agents stay alone.  Groups run largest work first.
+  std::vector<int32_t> goff, gmem;
+  {
+    const bool group = !(o.flags & (TADMM_FLAG_NO_GROUPING | TADMM_FLAG_NO_FUSED_PAIR_GATHER));
+    std::vector<int32_t> idx(b->n_scen);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+      if (h->T[x] != h->T[y]) return h->T[x] > h->T[y];
+      return h->N[x] > h->N[y];
+    });
+    std::vector<std::vector<int32_t>> groups;
+    std::vector<int> load;
+    size_t first_open = 0;
+    int cur_T = -1;
+    for (int sc : idx) {
+      const int n = h->N[sc];
+      if (h->T[sc] != cur_T) {
+        cur_T = h->T[sc];
+        first_open = groups.size();
+      }
+      int placed = -1;
+      if (group && n <= 32)
+        for (size_t g = first_open; g < groups.size(); ++g)
+          if (load[g] + n <= 32 && load[g] > 0 && h->N[groups[g][0]] <= 32) { placed = (int)g; break; }
+      if (placed < 0) {
+        groups.push_back({});
+        load.push_back(0);
+        placed = (int)groups.size() - 1;
+      }
+      groups[placed].push_back(sc);
+      load[placed] += n;
+    }
+    std::vector<double> gw(groups.size());
+    for (size_t g = 0; g < groups.size(); ++g) {
+      double pairs = 0;
+      int gp = 0;
+      for (int sc : groups[g]) {
+        pairs += h->meta_h[sc].P;
+        gp += h->meta_h[sc].P;
+      }
+      h->max_group_pairs = std::max(h->max_group_pairs, gp);
+      gw[g] = double(h->T[groups[g][0]]) * (600.0 + 30.0 * pairs / 32.0);
+    }
+    std::vector<int32_t> gord(groups.size());
+    std::iota(gord.begin(), gord.end(), 0);
+    std::stable_sort(gord.begin(), gord.end(), [&](int x, int y) { return gw[x] > gw[y]; });
+    goff.push_back(0);
+    for (size_t g = 0; g < groups.size(); ++g) {
+      for (int sc : groups[g]) gmem.push_back(sc);
+      goff.push_back((int32_t)gmem.size());
+    }
+    h->n_groups = (int)groups.size();
+    order = gord;
+  }
+
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   const size_t fs = h->prec == 64 ? 8 : 4;
@@ -253,7 +313,9 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   const int64_t na = h->tot_agents;
   const size_t ex_doubles = (size_t)std::max<int64_t>({h->tot_xs * nx, h->tot_as * nu, h->tot_ps, 1});
   h->ex_bytes = ex_doubles * sizeof(double);
-  if ((rc = dmalloc(&h->meta, sizeof(tadmm::ScenMeta) * h->n_scen)) || (rc = dmalloc(&h->order, 4 * order.size())) ||
+  if ((rc = dmalloc(&h->goff, 4 * goff.size())) || (rc = dmalloc(&h->gmem, 4 * gmem.size())) ||
+      (rc = dmalloc(&h->gorder, 4 * order.size())) ||
+      (rc = dmalloc(&h->meta, sizeof(tadmm::ScenMeta) * h->n_scen)) || (rc = dmalloc(&h->order, 4 * order.size())) ||
       (rc = dmalloc(&h->pairs, 4 * pairs.size())) || (rc = dmalloc(&h->pair_scen, 4 * pair_scen.size())) ||
       (rc = dmalloc(&h->agent_scen, 4 * agent_scen.size())) ||
       (rc = dmalloc(&h->model, fs * (nx * nx + nx * nu + 2 * nu))) || (rc = dmalloc(&h->Qd, fs * na * nx)) ||
@@ -286,6 +348,9 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   }
   cudaStream_t st = h->cap_stream;
   cudaMemcpyAsync(h->order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->gorder, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->goff, goff.data(), 4 * goff.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->gmem, gmem.data(), 4 * gmem.size(), cudaMemcpyHostToDevice, st);
   if (!pairs.empty()) {
     cudaMemcpyAsync(h->pairs, pairs.data(), 4 * pairs.size(), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->pair_scen, pair_scen.data(), 4 * pair_scen.size(), cudaMemcpyHostToDevice, st);

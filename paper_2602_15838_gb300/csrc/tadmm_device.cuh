@@ -72,6 +72,9 @@ struct Dev {
   unsigned long long* eqp;   // [n_scen]
   unsigned long long* fact;  // [n_scen]
   int32_t* queue;            // work-queue head of the persistent kernel
+  const int32_t* goff;       // [n_groups + 1] member offsets of the scenario groups
+  const int32_t* gmem;       // [n_scen] member scenario ids, group by group
+  int32_t n_groups;
   double tol;
   int32_t max_iter;
   int32_t sm_pairs;          // pairs per step that fit the fused pair/gather staging (0: unfused)
@@ -1038,6 +1041,235 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
     D.eqp[sc] = cs.cnt[0];
     D.fact[sc] = cs.cnt[1];
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Scenario groups: several same-horizon scenarios with at most 32 agents in
+// total share one CTA; each lane of the x-update owns one agent of one member,
+// the pair and gather sweeps run over the members' flattened units, and every
+// decision (residuals, convergence, outputs) stays per scenario.
+// ---------------------------------------------------------------------------
+constexpr int kGroupMax = 32;
+
+struct GroupSm {
+  ScenMeta meta[kGroupMax];
+  int sid[kGroupMax];
+  int aoff[kGroupMax + 1];
+  int poff[kGroupMax + 1];
+  int active[kGroupMax];
+  int flag[kGroupMax];
+  int need[kGroupMax];
+  unsigned long long rb[kGroupMax];
+  unsigned long long sb[kGroupMax];
+  unsigned long long cnt[kGroupMax][2];
+  int G, nA, nP, T, any;
+};
+
+// Member owning flattened index u given exclusive prefix sums off[0..G].
+__device__ __forceinline__ int member_of(const int* off, int G, int u) {
+  int m = 0;
+  while (m + 1 < G && off[m + 1] <= u) ++m;
+  return m;
+}
+
+template <typename F, int NX, int NU, int DP, bool DI>
+__device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int* members, int G, GroupSm& gs,
+                          F* sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < G) {
+    const int sc = members[tid];
+    gs.sid[tid] = sc;
+    gs.meta[tid] = D.meta[sc];
+    gs.active[tid] = 1;
+    gs.flag[tid] = 0;
+    gs.need[tid] = 0;
+    gs.rb[tid] = 0;
+    gs.sb[tid] = 0;
+    gs.cnt[tid][0] = 0;
+    gs.cnt[tid][1] = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int a = 0, p = 0;
+    for (int m = 0; m < G; ++m) {
+      gs.aoff[m] = a;
+      gs.poff[m] = p;
+      a += gs.meta[m].N;
+      p += gs.meta[m].P;
+    }
+    gs.aoff[G] = a;
+    gs.poff[G] = p;
+    gs.G = G;
+    gs.nA = a;
+    gs.nP = p;
+    gs.T = gs.meta[0].T;
+  }
+  __syncthreads();
+  for (int m = 0; m < G; ++m) init_phase<F, NX, NU, DP>(D, gs.meta[m], tid, nt);
+  __syncthreads();
+  const int nA = gs.nA, nP = gs.nP, T = gs.T;
+  // the lane's agent (fixed for the whole run)
+  const int my_m = tid < nA ? member_of(gs.aoff, G, tid) : -1;
+  const int my_i = tid < nA ? tid - gs.aoff[my_m] : 0;
+  unsigned long long neqp = 0, nfact = 0;
+  F* smE = sm;
+  F* smA = sm + nP;
+  int xl = 0;
+  for (int k = 0; k < D.max_iter; ++k) {
+    const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
+    const bool last = (k + 1 == D.max_iter);
+    // x-update
+    if (my_m >= 0 && gs.active[my_m]) {
+      const ScenMeta& s = gs.meta[my_m];
+      AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1);
+      const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
+      const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
+      const int st = xupdate_agent<F, NX, NU, DP, DI>(A, start_kind_of(D, k), as_max, eps, neqp, nfact);
+      if (st) atomicMax(&gs.flag[my_m], st);
+    }
+    __syncthreads();
+    if (tid < G && gs.active[tid] && gs.flag[tid]) {
+      const int sc = gs.sid[tid];
+      gs.active[tid] = 0;
+      D.status[sc] = gs.flag[tid];
+      D.iters[sc] = k + 1;
+      D.cur_lvl[sc] = xl | (tk << 1);
+    }
+    __syncthreads();
+    // fused consensus projection / dual update and gather, step by step
+    for (int tm1 = 0; tm1 < T; ++tm1) {
+      for (int u = tid; u < nP; u += nt) {
+        const int m = member_of(gs.poff, G, u);
+        if (!gs.active[m]) continue;
+        const ScenMeta& s = gs.meta[m];
+        const int P = s.P, N = s.N, pair = u - gs.poff[m];
+        const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+        const F* a = D.a + s.ps_off * DP;
+        const size_t q = (size_t)tm1 * P + pair;
+        const int pk = D.pairs[s.pair_off + pair];
+        const int i = pk & 0xFFFF, j = pk >> 16;
+        F sdot = 0;
+        unsigned long long amax = 0;
+#pragma unroll
+        for (int c = 0; c < DP; ++c) {
+          const F av = a[((size_t)tm1 * DP + c) * P + pair];
+          smA[c * nP + u] = av;
+          const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
+          sdot = fma(av, Xn[ro + i] - Xn[ro + j], sdot);
+          const unsigned long long ab = abs_bits(av);
+          amax = ab > amax ? ab : amax;
+        }
+        const F th = D.theta[(size_t)tk * D.tot_ps + s.ps_off + q];
+        F tn = fma(F(s.d) - sdot, F(0.5), th);
+        if (sign_set(tn)) tn = F(0);
+        D.theta[(size_t)tkp1 * D.tot_ps + s.ps_off + q] = tn;
+        smE[u] = fma(F(2), tn, -th);
+        const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
+        if (v > gs.rb[m]) atomicMax(&gs.rb[m], v);
+      }
+      __syncthreads();
+      if (my_m >= 0 && gs.active[my_m]) {
+        const ScenMeta& s = gs.meta[my_m];
+        const int N = s.N, i = my_i, base = gs.poff[my_m];
+        const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+        F acc[DP];
+#pragma unroll
+        for (int c = 0; c < DP; ++c) acc[c] = F(N - 1) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
+        for (int j = 0; j < N; ++j) {
+          if (j == i) continue;
+          const bool first = i < j;
+          const int pair = base + (first ? pair_index(N, i, j) : pair_index(N, j, i));
+          F e = smE[pair];
+          if (!first) e = -e;
+#pragma unroll
+          for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * nP + pair], acc[c]);
+        }
+        F* h = D.h + s.as_off * DP;
+#pragma unroll
+        for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+      }
+      __syncthreads();
+    }
+    // primal residual tests, then the dual residual only where it decides
+    if (tid < G) {
+      gs.need[tid] = 0;
+      if (gs.active[tid]) {
+        const F r = from_bits(gs.rb[tid], F(0));
+        if (!finite_(r)) {
+          const int sc = gs.sid[tid];
+          gs.active[tid] = 0;
+          D.status[sc] = ST_NUMERIC;
+          D.iters[sc] = k + 1;
+          D.cur_lvl[sc] = (xl ^ 1) | (tkp1 << 1);
+          D.res[2 * sc] = double(r);
+        } else if (r <= F(D.tol) || last) {
+          gs.need[tid] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int any = 0;
+      for (int m = 0; m < G; ++m) any |= gs.need[m];
+      gs.any = any;
+    }
+    __syncthreads();
+    if (gs.any) {
+      for (int tm1 = 0; tm1 < T; ++tm1) {
+        for (int u = tid; u < nP; u += nt) {
+          const int m = member_of(gs.poff, G, u);
+          if (!gs.need[m]) continue;
+          const ScenMeta& s = gs.meta[m];
+          unsigned long long sb = 0;
+          dual_phase<F, NX, NU, DP>(D, s, xl, tkm1, tk, tkp1, (int64_t)tm1 * s.P + (u - gs.poff[m]),
+                                    (int64_t)s.P * s.T, sb);
+          if (sb > gs.sb[m]) atomicMax(&gs.sb[m], sb);
+        }
+      }
+      __syncthreads();
+    }
+    if (tid < G && gs.active[tid]) {
+      const int sc = gs.sid[tid];
+      const F r = from_bits(gs.rb[tid], F(0));
+      D.res[2 * sc] = double(r);
+      if (gs.need[tid]) {
+        const F sres = F(gs.meta[tid].rho) * from_bits(gs.sb[tid], F(0));
+        D.res[2 * sc + 1] = double(sres);
+        int stop = 0, status = ST_NOT_CONVERGED;
+        if (!finite_(sres)) { stop = 1; status = ST_NUMERIC; }
+        else if (r <= F(D.tol) && sres <= F(D.tol)) { stop = 1; status = ST_CONVERGED; }
+        else if (last) stop = 1;
+        if (stop) {
+          gs.active[tid] = 0;
+          D.status[sc] = status;
+          D.iters[sc] = k + 1;
+          D.cur_lvl[sc] = (xl ^ 1) | (tkp1 << 1);
+        }
+      }
+      gs.rb[tid] = 0;
+      gs.sb[tid] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int any = 0;
+      for (int m = 0; m < G; ++m) any |= gs.active[m];
+      gs.any = any;
+    }
+    __syncthreads();
+    xl ^= 1;
+    if (!gs.any) break;
+  }
+  if (my_m >= 0) {
+    if (neqp) atomicAdd(&gs.cnt[my_m][0], neqp);
+    if (nfact) atomicAdd(&gs.cnt[my_m][1], nfact);
+  }
+  __syncthreads();
+  if (tid < G) {
+    D.eqp[gs.sid[tid]] = gs.cnt[tid][0];
+    D.fact[gs.sid[tid]] = gs.cnt[tid][1];
+  }
+  __syncthreads();
 }
 
 }  // namespace tadmm

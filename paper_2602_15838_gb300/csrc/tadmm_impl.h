@@ -32,6 +32,11 @@ struct tadmm_handle {
   // device state
   tadmm::ScenMeta* meta = nullptr;
   int32_t* order = nullptr;
+  int32_t* goff = nullptr;      // scenario groups of the persistent kernel
+  int32_t* gmem = nullptr;
+  int32_t* gorder = nullptr;
+  int n_groups = 0;
+  int max_group_pairs = 0;
   int32_t* pairs = nullptr;
   int32_t* pair_scen = nullptr;
   int32_t* agent_scen = nullptr;

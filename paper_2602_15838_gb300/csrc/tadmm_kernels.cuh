@@ -26,6 +26,7 @@ template <typename F, int NX, int NU, int DP, int V, bool DI>
 __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batched(Dev<F> D) {
   __shared__ Model<F, NX, NU> M;
   __shared__ CtaScratch cs;
+  __shared__ GroupSm gs;
   __shared__ int s_q;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   F* sm = D.sm_pairs > 0 ? (F*)dyn_smem : nullptr;
@@ -35,10 +36,16 @@ __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batche
     if (threadIdx.x == 0) s_q = atomicAdd(D.queue, 1);
     __syncthreads();
     const int qi = s_q;
-    if (qi >= D.n_scen) return;
-    const int sc = D.order[qi];
-    const ScenMeta s = D.meta[sc];
-    run_scenario<F, NX, NU, DP, DI>(D, M, s, sc, cs, sm, D.sm_pairs);
+    if (qi >= D.n_groups) return;
+    const int g = D.order[qi];
+    const int b0 = D.goff[g], G = D.goff[g + 1] - b0;
+    if (G == 1) {
+      const int sc = D.gmem[b0];
+      const ScenMeta s = D.meta[sc];
+      run_scenario<F, NX, NU, DP, DI>(D, M, s, sc, cs, sm, D.sm_pairs);
+    } else {
+      run_group<F, NX, NU, DP, DI>(D, M, D.gmem + b0, G, gs, sm);
+    }
   }
 }
 
@@ -377,7 +384,6 @@ static Dev<F> make_dev(tadmm_handle* h) {
   Dev<F> D;
   std::memset(&D, 0, sizeof(D));
   D.meta = h->meta;
-  D.order = h->order;
   D.pairs = h->pairs;
   D.model = (const F*)h->model;
   D.Qd = (const F*)h->Qd;
@@ -406,6 +412,10 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.fact = h->fact;
   D.queue = h->queue;
   D.start_mode = h->opt.start_mode;
+  D.goff = h->goff;
+  D.gmem = h->gmem;
+  D.n_groups = h->n_groups;
+  D.order = h->gorder;
   D.as_max = h->opt.as_max;
   D.eps_rel = h->opt.eps_rel;
   return D;
@@ -463,7 +473,7 @@ static int variant_maxt(int v) {
 // pair of the largest scenario, if that fits the per-CTA budget.
 template <typename F, int DP>
 static size_t fused_smem_bytes(const tadmm_handle* h, int* pairs_out) {
-  int pmax = 0;
+  int pmax = h->max_group_pairs;
   for (const ScenMeta& m : h->meta_h) pmax = std::max(pmax, m.P);
   const size_t bytes = (size_t)(DP + 1) * pmax * sizeof(F);
   const size_t budget = 96 * 1024;
@@ -496,7 +506,7 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
   const int occ = max_ctas_per_sm(tpc, var, h);
   if (occ < 1) return set_error(TADMM_EINVAL, "launch shape does not fit the kernel variant");
   int cps = h->cps > 0 ? std::min(h->cps, occ) : occ;
-  const int grid = std::max(1, std::min(h->n_scen, h->sm_count * cps));
+  const int grid = std::max(1, std::min(h->n_groups, h->sm_count * cps));
   if (!h->gexec || h->g_tol != tol || h->g_iter != max_iter || h->g_tpc != tpc || h->g_cps != cps ||
       h->g_var != var) {
     if (h->gexec) {

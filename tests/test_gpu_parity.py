@@ -259,3 +259,21 @@ def test_swarm3d_full_size_graph_mode_sampled(tg):
     assert rel(gg[0]["X"], gp[0]["X"]) <= 1e-12
     assert rel(gg[0]["theta"], gp[0]["theta"]) <= 1e-12
     assert (gg[0]["theta"] >= 0).all()
+
+
+def test_scenario_groups_equal_one_scenario_per_cta(tg):
+    """Packing several same-horizon scenarios into one CTA changes nothing in
+    any scenario's arithmetic: iterates, statuses and counters are equal to the
+    one-scenario-per-CTA run, for fixed and converging runs."""
+    b = make_workload("mixed", n_scen=64)
+    for tol, it in ((0.0, 6), (1e-4, 400)):
+        ref, cr = gpu_run(tg, b, tol, it, flags=tg.FLAG_NO_GROUPING)
+        for tpc in (32, 64):
+            g, cg = gpu_run(tg, b, tol, it, threads_per_cta=tpc)
+            for k in range(b.n_scen):
+                assert g[k]["status"] == ref[k]["status"] and g[k]["iters"] == ref[k]["iters"], k
+                assert rel(g[k]["X"], ref[k]["X"]) <= 1e-12, k
+                assert rel(g[k]["theta"], ref[k]["theta"]) <= 1e-12, k
+                assert np.array_equal(g[k]["W"], ref[k]["W"]), k
+                assert abs(g[k]["r"] - ref[k]["r"]) <= 1e-12 and abs(g[k]["s"] - ref[k]["s"]) <= 1e-12, k
+            assert np.array_equal(cg["eqp"], cr["eqp"]) and np.array_equal(cg["fact"], cr["fact"])
