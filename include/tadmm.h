@@ -102,6 +102,10 @@ typedef struct {
 #define TADMM_FLAG_NO_FUSED_PAIR_GATHER 1 /* separate pair and gather sweeps in the batched kernel */
 #define TADMM_FLAG_NO_STRUCTURE 2         /* dense A, B products even for a double integrator */
 #define TADMM_FLAG_NO_GROUPING 4          /* one scenario per CTA (no packing of small scenarios) */
+#define TADMM_FLAG_DOUBLE_FLOAT 8         /* with precision 64 and the 2D model (4, 2, 2): arithmetic in
+                                             double-float (pairs of floats, 48-bit significand) on the
+                                             FP32 pipe instead of the FP64 pipe; results agree with
+                                             float64 to about 1e-13 relative */
 
 typedef struct tadmm_handle tadmm_handle;
 

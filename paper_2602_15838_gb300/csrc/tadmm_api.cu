@@ -37,6 +37,7 @@ using tadmm::set_error;
     if ((h)->prec == 64 && (h)->nx == 6) return tadmm::Impl<double, 6, 3, 3>::CALL;  \
     if ((h)->prec == 32 && (h)->nx == 4) return tadmm::Impl<float, 4, 2, 2>::CALL;   \
     if ((h)->prec == 32 && (h)->nx == 6) return tadmm::Impl<float, 6, 3, 3>::CALL;   \
+    if ((h)->prec == 128 && (h)->nx == 4) return tadmm::Impl<tadmm::df64, 4, 2, 2>::CALL; \
     return set_error(TADMM_EINVAL, "unsupported precision / dimensions");            \
   } while (0)
 
@@ -200,8 +201,10 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   if (o.ctas_per_sm < 0) return set_error(TADMM_EINVAL, "ctas_per_sm must be >= 0");
   if (o.kernel_variant < 0 || o.kernel_variant > 2) return set_error(TADMM_EINVAL, "kernel_variant must be in 0..2");
 
+  if ((o.flags & TADMM_FLAG_DOUBLE_FLOAT) && (o.precision != 64 || b->nx != 4))
+    return set_error(TADMM_EINVAL, "TADMM_FLAG_DOUBLE_FLOAT needs precision 64 and (nx, nu, dp) = (4, 2, 2)");
   tadmm_handle* h = new tadmm_handle();
-  h->prec = o.precision;
+  h->prec = (o.flags & TADMM_FLAG_DOUBLE_FLOAT) ? 128 : o.precision;
   h->nx = b->nx;
   h->nu = b->nu;
   h->dp = b->dp;
@@ -308,7 +311,7 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
 
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-  const size_t fs = h->prec == 64 ? 8 : 4;
+  const size_t fs = h->prec == 32 ? 4 : 8;
   const int nx = h->nx, nu = h->nu, dp = h->dp;
   const int64_t na = h->tot_agents;
   const size_t ex_doubles = (size_t)std::max<int64_t>({h->tot_xs * nx, h->tot_as * nu, h->tot_ps, 1});

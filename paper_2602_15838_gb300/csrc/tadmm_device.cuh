@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tadmm_df64.cuh"
+
 namespace tadmm {
 
 enum { ST_CONVERGED = 0, ST_NOT_CONVERGED = 1, ST_QP_FAIL = 2, ST_NUMERIC = 3 };

@@ -421,6 +421,32 @@ static Dev<F> make_dev(tadmm_handle* h) {
   return D;
 }
 
+// Host decoding of a residual maximum from its bit-ordered key (see ord_bits).
+template <typename F>
+static double host_decode_bits(unsigned long long b);
+template <>
+double host_decode_bits<double>(unsigned long long b) {
+  double v;
+  std::memcpy(&v, &b, 8);
+  return v;
+}
+template <>
+double host_decode_bits<float>(unsigned long long b) {
+  const uint32_t b32 = (uint32_t)b;
+  float v;
+  std::memcpy(&v, &b32, 4);
+  return v;
+}
+template <>
+double host_decode_bits<df64>(unsigned long long b) {
+  const uint32_t h32 = (uint32_t)(b >> 32), k = (uint32_t)b;
+  const uint32_t l32 = (k & 0x80000000u) ? (k ^ 0x80000000u) : ~k;
+  float hi, lo;
+  std::memcpy(&hi, &h32, 4);
+  std::memcpy(&lo, &l32, 4);
+  return (double)hi + (double)lo;
+}
+
 static inline int grid_for(int64_t n, int threads, int cap = 65535) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -557,15 +583,7 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
     int xl = 0, status = ST_NOT_CONVERGED, iters = 0, tfin = 0;
     double r = 0, sres = 0;
     auto read_bits = [&](unsigned long long b, double rho_scale) -> double {
-      if (sizeof(F) == 8) {
-        double v;
-        std::memcpy(&v, &b, 8);
-        return rho_scale * v;
-      }
-      float v;
-      const uint32_t b32 = (uint32_t)b;
-      std::memcpy(&v, &b32, 4);
-      return double(float(rho_scale) * v);
+      return rho_scale * host_decode_bits<F>(b);
     };
     for (int k = 0; k < max_iter; ++k) {
       const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
@@ -589,7 +607,7 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
       tfin = tkp1;
       if (!std::isfinite(r)) { status = ST_NUMERIC; xl ^= 1; break; }
       const bool last = (k + 1 == max_iter);
-      const bool r_ok = (sizeof(F) == 8) ? (r <= tol) : (float(r) <= float(tol));
+      const bool r_ok = (sizeof(F) == 8) ? (r <= tol) : (float(r) <= float(tol));  // in the type F
       if (r_ok || last) {
         k_dual<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, xl, tkm1, tk, tkp1,
                                                                                 h->red2 + 1);

@@ -277,3 +277,37 @@ def test_scenario_groups_equal_one_scenario_per_cta(tg):
                 assert np.array_equal(g[k]["W"], ref[k]["W"]), k
                 assert abs(g[k]["r"] - ref[k]["r"]) <= 1e-12 and abs(g[k]["s"] - ref[k]["s"]) <= 1e-12, k
             assert np.array_equal(cg["eqp"], cr["eqp"]) and np.array_equal(cg["fact"], cr["fact"])
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_double_float_arithmetic_matches_oracle(tg, k):
+    """Double-float arithmetic on the FP32 pipe (TADMM_FLAG_DOUBLE_FLOAT) keeps the
+    FP64 parity bar: iterates within 1e-9 of the float64 oracle."""
+    for name in ("pair", "ring14"):
+        b = make_workload(name)
+        g, _ = gpu_run(tg, b, 0.0, k, flags=tg.FLAG_DOUBLE_FLOAT)
+        o = oracle.admm(b, 0, tol=0.0, max_iter=k, nthreads=8)
+        assert rel(g[0]["X"], o["X"]) <= 1e-9, name
+        assert rel(g[0]["U"], o["U"]) <= 1e-9, name
+        assert rel(g[0]["theta"], o["theta"]) <= 1e-9, name
+        ok, _ = nondegenerate_w_equal(g[0]["W"], o, b)
+        assert ok, name
+
+
+def test_double_float_mixed_batch_sampled(tg):
+    """Double-float on the full mixed batch: sampled scenarios within 1e-9 of the
+    oracle after 30 iterations, converged run agrees with native float64."""
+    b = make_workload("mixed")
+    g, _ = gpu_run(tg, b, 0.0, 30, flags=tg.FLAG_DOUBLE_FLOAT)
+    for k in (0, 7, 1234, b.n_scen - 1):
+        o = oracle.admm(b, k, tol=0.0, max_iter=30)
+        assert rel(g[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(g[k]["theta"], o["theta"]) <= 1e-9, k
+    sub = b.subset(list(range(48)))
+    gd, _ = gpu_run(tg, sub, 1e-4, 300, flags=tg.FLAG_DOUBLE_FLOAT)
+    gn, _ = gpu_run(tg, sub, 1e-4, 300)
+    same = sum(gd[k]["iters"] == gn[k]["iters"] and gd[k]["status"] == gn[k]["status"] for k in range(48))
+    assert same >= 46
+    for k in range(48):
+        if gd[k]["iters"] == gn[k]["iters"]:
+            assert rel(gd[k]["X"], gn[k]["X"]) <= 1e-9, k
