@@ -41,13 +41,15 @@ class Scenario(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("start_mode", C.c_int), ("as_max", C.c_int), ("eps_rel", C.c_double),
-                ("tol", C.c_double), ("max_iter", C.c_int), ("nthreads", C.c_int)]
+                ("tol", C.c_double), ("max_iter", C.c_int), ("nthreads", C.c_int),
+                ("adapt_every", C.c_int), ("adapt_mu", C.c_double), ("adapt_tau", C.c_double)]
 
 
 class Result(C.Structure):
     _fields_ = [("X", _dp), ("U", _dp), ("theta", _dp), ("W", _i8p), ("mu", _dp), ("trace", _dp),
                 ("iters", C.c_int), ("status", C.c_int), ("r", C.c_double), ("s", C.c_double),
-                ("as_iters", C.c_int64), ("inv_dev", C.c_double)]
+                ("as_iters", C.c_int64), ("inv_dev", C.c_double), ("rho_final", C.c_double),
+                ("rho_changes", C.c_int)]
 
 
 class GlobalResult(C.Structure):
@@ -174,21 +176,22 @@ class _ResultData:
         self.mu = np.zeros((N, T, nu))
         self.trace = np.zeros((max(max_iter, 1), 2)) if trace else None
         self.r = Result(_d(self.X), _d(self.U), _d(self.theta), self.W.ctypes.data_as(_i8p), _d(self.mu),
-                        _d(self.trace) if trace else None, 0, 0, 0.0, 0.0, 0, 0.0)
+                        _d(self.trace) if trace else None, 0, 0, 0.0, 0.0, 0, 0.0, 0.0, 0)
         self.P = sd.P
 
     def to_dict(self):
         r = self.r
         out = dict(X=self.X, U=self.U, theta=self.theta[:self.P], W=self.W, mu=self.mu,
                    iters=r.iters, status=r.status, r=r.r, s=r.s, as_iters=int(r.as_iters),
-                   inv_dev=r.inv_dev)
+                   inv_dev=r.inv_dev, rho_final=r.rho_final, rho_changes=r.rho_changes)
         if self.trace is not None:
             out["trace"] = self.trace[:r.iters]
         return out
 
 
-def _options(start_mode, as_max, eps_rel, tol, max_iter, nthreads):
-    return Options(start_mode, as_max, eps_rel, tol, max_iter, nthreads)
+def _options(start_mode, as_max, eps_rel, tol, max_iter, nthreads, adapt=None):
+    ae, am, at = (0, 10.0, 2.0) if adapt is None else adapt
+    return Options(start_mode, as_max, eps_rel, tol, max_iter, nthreads, ae, am, at)
 
 
 def agent_xupdate(batch, k: int, i: int, h, start=QP_LQR, as_max=None, eps_rel=1e-12):
@@ -204,19 +207,20 @@ def agent_xupdate(batch, k: int, i: int, h, start=QP_LQR, as_max=None, eps_rel=1
 
 
 def admm(batch, k: int = 0, start_mode=START_TURBO, tol=1e-4, max_iter=500, as_max=None,
-         eps_rel=1e-12, nthreads=0, trace=False):
-    """Literal vector-form ADMM on scenario k of `batch`."""
+         eps_rel=1e-12, nthreads=0, trace=False, adapt=None):
+    """Literal vector-form ADMM on scenario k of `batch`; adapt = (every, mu, tau)
+    turns on residual balancing of rho."""
     sd = _ScenarioData(batch, k)
     if as_max is None:
         as_max = 10 * sd.T * sd.nu + 10
     rd = _ResultData(sd, max_iter, trace)
-    o = _options(start_mode, as_max, eps_rel, tol, max_iter, nthreads)
+    o = _options(start_mode, as_max, eps_rel, tol, max_iter, nthreads, adapt)
     lib().orc_admm(C.byref(sd.s), C.byref(o), C.byref(rd.r))
     return rd.to_dict()
 
 
 def admm_batch(batch, idx: Optional[List[int]] = None, start_mode=START_TURBO, tol=1e-4, max_iter=500,
-               as_max=None, eps_rel=1e-12, nthreads=None):
+               as_max=None, eps_rel=1e-12, nthreads=None, adapt=None):
     """ADMM on several scenarios in parallel over host cores. Returns (results, threads used)."""
     idx = list(range(batch.n_scen)) if idx is None else list(idx)
     sds = [_ScenarioData(batch, k) for k in idx]
@@ -225,7 +229,7 @@ def admm_batch(batch, idx: Optional[List[int]] = None, start_mode=START_TURBO, t
     sarr = (Scenario * S)(*[sd.s for sd in sds])
     rarr = (Result * S)(*[rd.r for rd in rds])
     am = as_max if as_max is not None else 10 * int(batch.T.max()) * batch.nu + 10
-    o = _options(start_mode, am, eps_rel, tol, max_iter, 0)
+    o = _options(start_mode, am, eps_rel, tol, max_iter, 0, adapt)
     nt = os.cpu_count() if nthreads is None else nthreads
     used = lib().orc_admm_batch(sarr, S, C.byref(o), rarr, nt)
     out = []

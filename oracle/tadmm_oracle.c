@@ -381,6 +381,9 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   double* yj = (double*)calloc(PS + 1, sizeof(double));
   double* pos = (double*)malloc(sizeof(double) * ((size_t)N * T * dp + 1));
   int64_t as_total = 0;
+  orc_scenario sc = *s; /* the penalty changes under residual balancing */
+  res->rho_final = s->rho;
+  res->rho_changes = 0;
   res->status = ORC_NOT_CONVERGED;
   res->iters = 0;
   res->r = INFINITY;
@@ -426,7 +429,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
       else if (k == 0) start = (o->start_mode == ORC_START_TURBO) ? ORC_QP_LQR : ORC_QP_COLD;
       else start = ORC_QP_GIVEN;
       int neqp = 0;
-      int st = orc_agent_xupdate(s, i, h, start, o->as_max, o->eps_rel, res->U + (size_t)i * T * nu,
+      int st = orc_agent_xupdate(&sc, i, h, start, o->as_max, o->eps_rel, res->U + (size_t)i * T * nu,
                                  res->W + (size_t)i * T * nu, res->X + (size_t)i * (T + 1) * nx,
                                  res->mu + (size_t)i * T * nu, &neqp);
       as_total += neqp;
@@ -471,14 +474,31 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
           res->theta[(size_t)pk * T + t] = th;
         }
       }
-    double sres = s->rho * sd;
+    double sres = sc.rho * sd;
     res->r = r;
     res->s = sres;
     res->inv_dev = dev;
     if (res->trace) { res->trace[2 * k] = r; res->trace[2 * k + 1] = sres; }
     if (!isfinite(r) || !isfinite(sres)) { res->status = ORC_NUMERIC; break; }
     if (r <= o->tol && sres <= o->tol) { res->status = ORC_CONVERGED; break; }
+    /* residual balancing (Boyd et al. 2011, Sec. 3.4.1): raise rho when the
+     * primal residual dominates, lower it when the dual one does; the scaled
+     * duals y = lambda / rho are rescaled so that lambda is unchanged */
+    if (o->adapt_every > 0 && (k + 1) % o->adapt_every == 0) {
+      double scale = 1.0;
+      if (r > o->adapt_mu * sres) scale = o->adapt_tau;
+      else if (sres > o->adapt_mu * r) scale = 1.0 / o->adapt_tau;
+      if (scale != 1.0) {
+        for (size_t q = 0; q < PS; ++q) {
+          yi[q] /= scale;
+          yj[q] /= scale;
+        }
+        sc.rho *= scale;
+        res->rho_changes++;
+      }
+    }
   }
+  res->rho_final = sc.rho;
   res->as_iters = as_total;
   free(wi); free(wj); free(yi); free(yj); free(pos);
   return 0;

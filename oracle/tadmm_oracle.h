@@ -80,6 +80,9 @@ typedef struct {
   double tol;         /* residual tolerance */
   int max_iter;       /* ADMM iteration cap */
   int nthreads;       /* OpenMP threads over agents (<=0: serial) */
+  int adapt_every;    /* residual balancing of rho every this many iterations (0: fixed rho) */
+  double adapt_mu;    /* imbalance ratio that triggers a change */
+  double adapt_tau;   /* factor of a change */
 } orc_options;
 
 typedef struct {
@@ -94,6 +97,8 @@ typedef struct {
   double r, s;
   int64_t as_iters;   /* EQP solves summed over agents and iterations */
   double inv_dev;     /* max |y_i + theta a| and |y_j - theta a| over the run */
+  double rho_final;   /* penalty at the end of the run */
+  int rho_changes;    /* number of penalty changes */
 } orc_result;
 
 /* Projection of (v_i, v_j) onto {a'(w_i - w_j) >= d}; returns theta >= 0 with

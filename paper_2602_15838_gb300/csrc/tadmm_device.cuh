@@ -1054,6 +1054,15 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
 // ---------------------------------------------------------------------------
 constexpr int kGroupMax = 32;
 
+constexpr int kGroupPairs = kGroupMax * (kGroupMax - 1) / 2;
+
+template <typename F, int DP>
+struct GroupStage {
+  uint32_t pair[kGroupPairs];   // flattened agent indices fi | fj << 8 of every member pair
+  uint8_t mem[kGroupPairs];     // member of every flattened pair
+  F pos[DP][kGroupMax];         // positions p^{k+1} of the group's agents at the current step
+};
+
 struct GroupSm {
   ScenMeta meta[kGroupMax];
   int sid[kGroupMax];
@@ -1077,7 +1086,7 @@ __device__ __forceinline__ int member_of(const int* off, int G, int u) {
 
 template <typename F, int NX, int NU, int DP, bool DI>
 __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int* members, int G, GroupSm& gs,
-                          F* sm) {
+                          GroupStage<F, DP>& st, F* sm) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid < G) {
     const int sc = members[tid];
@@ -1109,8 +1118,14 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
   }
   __syncthreads();
   for (int m = 0; m < G; ++m) init_phase<F, NX, NU, DP>(D, gs.meta[m], tid, nt);
-  __syncthreads();
   const int nA = gs.nA, nP = gs.nP, T = gs.T;
+  for (int u = tid; u < nP; u += nt) {
+    const int m = member_of(gs.poff, G, u);
+    const int pk = D.pairs[gs.meta[m].pair_off + (u - gs.poff[m])];
+    st.mem[u] = (uint8_t)m;
+    st.pair[u] = (uint32_t)(gs.aoff[m] + (pk & 0xFFFF)) | ((uint32_t)(gs.aoff[m] + (pk >> 16)) << 8);
+  }
+  __syncthreads();
   // the lane's agent (fixed for the whole run)
   const int my_m = tid < nA ? member_of(gs.aoff, G, tid) : -1;
   const int my_i = tid < nA ? tid - gs.aoff[my_m] : 0;
@@ -1139,26 +1154,32 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
       D.cur_lvl[sc] = xl | (tk << 1);
     }
     __syncthreads();
-    // fused consensus projection / dual update and gather, step by step
+    // fused consensus projection / dual update and gather, step by step; the
+    // step's positions and the pair table are read from shared memory
     for (int tm1 = 0; tm1 < T; ++tm1) {
+      if (my_m >= 0 && gs.active[my_m]) {
+        const ScenMeta& s = gs.meta[my_m];
+        const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+#pragma unroll
+        for (int c = 0; c < DP; ++c) st.pos[c][tid] = Xn[((size_t)(tm1 + 1) * NX + c) * s.N + my_i];
+      }
+      __syncthreads();
       for (int u = tid; u < nP; u += nt) {
-        const int m = member_of(gs.poff, G, u);
+        const int m = st.mem[u];
         if (!gs.active[m]) continue;
         const ScenMeta& s = gs.meta[m];
-        const int P = s.P, N = s.N, pair = u - gs.poff[m];
-        const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+        const int P = s.P, pair = u - gs.poff[m];
         const F* a = D.a + s.ps_off * DP;
         const size_t q = (size_t)tm1 * P + pair;
-        const int pk = D.pairs[s.pair_off + pair];
-        const int i = pk & 0xFFFF, j = pk >> 16;
+        const uint32_t fij = st.pair[u];
+        const int fi = fij & 0xFF, fj = fij >> 8;
         F sdot = 0;
         unsigned long long amax = 0;
 #pragma unroll
         for (int c = 0; c < DP; ++c) {
           const F av = a[((size_t)tm1 * DP + c) * P + pair];
           smA[c * nP + u] = av;
-          const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
-          sdot = fma(av, Xn[ro + i] - Xn[ro + j], sdot);
+          sdot = fma(av, st.pos[c][fi] - st.pos[c][fj], sdot);
           const unsigned long long ab = abs_bits(av);
           amax = ab > amax ? ab : amax;
         }
@@ -1174,10 +1195,9 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
       if (my_m >= 0 && gs.active[my_m]) {
         const ScenMeta& s = gs.meta[my_m];
         const int N = s.N, i = my_i, base = gs.poff[my_m];
-        const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
         F acc[DP];
 #pragma unroll
-        for (int c = 0; c < DP; ++c) acc[c] = F(N - 1) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
+        for (int c = 0; c < DP; ++c) acc[c] = F(N - 1) * st.pos[c][tid];
         for (int j = 0; j < N; ++j) {
           if (j == i) continue;
           const bool first = i < j;
@@ -1220,7 +1240,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     if (gs.any) {
       for (int tm1 = 0; tm1 < T; ++tm1) {
         for (int u = tid; u < nP; u += nt) {
-          const int m = member_of(gs.poff, G, u);
+          const int m = st.mem[u];
           if (!gs.need[m]) continue;
           const ScenMeta& s = gs.meta[m];
           unsigned long long sb = 0;

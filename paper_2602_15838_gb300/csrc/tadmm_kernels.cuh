@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batche
   __shared__ Model<F, NX, NU> M;
   __shared__ CtaScratch cs;
   __shared__ GroupSm gs;
+  __shared__ GroupStage<F, DP> gst;
   __shared__ int s_q;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   F* sm = D.sm_pairs > 0 ? (F*)dyn_smem : nullptr;
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batche
       const ScenMeta s = D.meta[sc];
       run_scenario<F, NX, NU, DP, DI>(D, M, s, sc, cs, sm, D.sm_pairs);
     } else {
-      run_group<F, NX, NU, DP, DI>(D, M, D.gmem + b0, G, gs, sm);
+      run_group<F, NX, NU, DP, DI>(D, M, D.gmem + b0, G, gs, gst, sm);
     }
   }
 }
