@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the FP32 / double-float / swarm timings")
     p.add_argument("--tpc", type=int, default=0, help="threads per CTA (with --no-autotune)")
     p.add_argument("--variant", type=int, default=0, help="kernel register variant (with --no-autotune)")
     return p.parse_args()
@@ -335,6 +336,7 @@ def run_ours(args, rank, world):
         cpu = None
         if not args.no_cpu:
             cpu = cpu_baseline(batch, args, solves_local / max(1, scen_iters))
+        ext = None if args.no_extras else extras(tg, torch, batch, args)
         clk = clocks.summary()
         launches = args.steps * solver_launches(solver)
         out = {
@@ -359,6 +361,7 @@ def run_ours(args, rank, world):
                          "algorithmic_units": units, "algorithmic_flops_per_step": flops},
             "plain_gpu": plain,
             "cpu_baseline": cpu,
+            "extras": ext,
             "e2e": e2e,
             "gpu_launches": launches,
         }
@@ -366,6 +369,52 @@ def run_ours(args, rank, world):
     solver.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def timed_solves(tg, torch, batch, args, reps=2, **kw):
+    """Device time and solves of one solve of `batch` (after one untimed solve)."""
+    do_tune = kw.pop("autotune", True)
+    s = tg.Solver(batch, start="turbo", mode=kw.pop("mode", "batched"), **kw)
+    tuned = s.autotune(probe_iter=10) if do_tune else None
+    s.solve(args.tol, args.max_iter)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.solve(args.tol, args.max_iter)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    sol = s.solution()
+    s.close()
+    conv = int((sol["status"] == 0).sum())
+    m = statistics.median(ms)
+    return dict(value=conv / (m / 1e3), unit=UNIT, ms_per_step=m, solves_per_step=conv, launch=tuned)
+
+
+def extras(tg, torch, batch, args):
+    out = {}
+    out["fp32"] = timed_solves(tg, torch, batch, args, precision=32)
+    out["fp32"]["note"] = "float32 arithmetic, same workload; parity 1e-4 against the float64 oracle"
+    out["double_float"] = timed_solves(tg, torch, batch, args, precision=64, flags=tg.FLAG_DOUBLE_FLOAT)
+    out["double_float"]["note"] = "float64-grade double-float arithmetic on the FP32 pipe (parity 1e-9)"
+    # one 512-agent 3D scenario (130816 pairs x 40 steps): graph mode vs plain mode per iteration
+    from instances import make_workload
+    sw = make_workload("swarm3d")
+    rows = {}
+    for mode in ("graph", "plain"):
+        s = tg.Solver(sw, precision=64, mode=mode)
+        s.solve(0.0, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.solve(0.0, 20)
+        torch.cuda.synchronize()
+        rows[mode] = 1e3 * (time.perf_counter() - t0) / 20
+        s.close()
+    out["swarm3d_512_agents"] = {"ms_per_iteration_graph": rows["graph"], "ms_per_iteration_plain": rows["plain"],
+                                 "pair_steps_per_iteration": 130816 * 40, "precision": 64}
+    return out
 
 
 def solver_launches(solver) -> int:

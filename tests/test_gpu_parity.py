@@ -311,3 +311,37 @@ def test_double_float_mixed_batch_sampled(tg):
     for k in range(48):
         if gd[k]["iters"] == gn[k]["iters"]:
             assert rel(gd[k]["X"], gn[k]["X"]) <= 1e-9, k
+
+
+def test_fp32_converged_solutions_against_fp64_oracle(tg):
+    """Float32 runs that reach tol 1e-4: converged positions and inputs within
+    1e-4 relative of the float64 oracle after the same number of iterations."""
+    b = make_workload("mixed", n_scen=512)
+    g, _ = gpu_run(tg, b, 1e-4, 200, precision=32)
+    done = [k for k in range(b.n_scen) if g[k]["status"] == tg.CONVERGED and g[k]["iters"] > 1]
+    done = sorted(done, key=lambda k: int(b.N[k]) * g[k]["iters"])[:4]
+    assert len(done) >= 2
+    for k in done:
+        o = oracle.admm(b, k, tol=0.0, max_iter=g[k]["iters"])
+        assert rel(g[k]["X"][:, :, :2], o["X"][:, :, :2]) <= 1e-4, k
+        assert rel(g[k]["U"], o["U"]) <= 1e-3, k
+
+
+def test_largest_mixed_batch_scenarios_fp64(tg):
+    """The largest scenarios of the mixed batch (N = 32, T = 40: 496 pairs) in one
+    batch with small ones: iterates match the oracle (maximum-size case)."""
+    big = make_workload("mixed", n_scen=2, N_override=32, T_override=40)
+    small = make_workload("mixed", n_scen=3, first=10)
+    parts = []
+    for bb in (big, small):
+        for k in range(bb.n_scen):
+            s = bb.scenario(k)
+            parts.append(dict(N=int(s.N[0]), T=int(s.T[0]), x_init=s.x_init, x_ref=s.x_ref, a=s.a, w0=s.w0,
+                              d=float(s.d_min[0]), rho=float(s.rho[0]), umax=1.0, c=None))
+    b = make_batch(parts, dp=2, dt=0.1, umax=1.0)
+    g, _ = gpu_run(tg, b, 0.0, 3)
+    for k in range(b.n_scen):
+        o = oracle.admm(b, k, tol=0.0, max_iter=3, nthreads=8)
+        assert rel(g[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(g[k]["theta"], o["theta"]) <= 1e-9, k
+        assert rel(g[k]["U"], o["U"]) <= 1e-9, k
