@@ -285,7 +285,11 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
     for (int t = T - 1; t >= 0; --t) {
       const uint16_t mask = Wm[(size_t)t * N + i];
       F Pt[NX][NX], K[NU][NX], L[NU][NU];
-      bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, rbar, t >= 1 ? qbar : nullptr, Pt, K, L);
+      auto put = [&](int r, int c, F v) {
+        Pt[r][c] = v;
+        Pt[c][r] = v;
+      };
+      bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, rbar, t >= 1 ? qbar : nullptr, 1, put, K, L);
 #pragma unroll
       for (int r = 0; r < NU; ++r) {
 #pragma unroll

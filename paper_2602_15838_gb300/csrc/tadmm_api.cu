@@ -116,7 +116,7 @@ static void free_all(tadmm_handle* h) {
   if (!h) return;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->wexec) cudaGraphExecDestroy(h->wexec);
-  void* gptrs[] = {h->gs_iter, h->gs_active, h->gs_need, h->gs_fail, h->gs_rb, h->gs_sb};
+  void* gptrs[] = {h->gs_iter, h->gs_active, h->gs_need, h->gs_fail, h->gs_rb, h->gs_sb, h->gs_blk};
   for (void* p : gptrs)
     if (p) cudaFree(p);
   void* ptrs0[] = {h->goff, h->gmem, h->gorder};
@@ -294,7 +294,8 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
         pairs += h->meta_h[sc].P;
         gp += h->meta_h[sc].P;
       }
-      h->max_group_pairs = std::max(h->max_group_pairs, gp);
+      // groups that run the group path: several scenarios, or one of <= 32 agents
+      if (groups[g].size() > 1 || h->N[groups[g][0]] <= 32) h->max_group_pairs = std::max(h->max_group_pairs, gp);
       gw[g] = double(h->T[groups[g][0]]) * (600.0 + 30.0 * pairs / 32.0);
     }
     std::vector<int32_t> gord(groups.size());

@@ -83,6 +83,7 @@ struct Dev {
   int32_t start_mode;
   int32_t as_max;            // 0: 10*T*NU + 10
   double eps_rel;
+  int32_t single_as_group;   // 1: a lone scenario of at most 32 agents also runs the group path
 };
 
 template <int NX, int NU>
@@ -174,6 +175,18 @@ struct EqpScan {
   int out;        // some free input of the EQP solution left the box
 };
 
+// Per-agent constants of the local QP used at every stage, kept in shared
+// memory (one column per thread, stride = threads of the CTA) rather than in
+// registers.  The terminal-stage terms and x_0 are read from global memory.
+template <int NX, int NU>
+struct AgentConst {
+  static constexpr int QB = 0;             // Hessian diagonal of x_t, t < T
+  static constexpr int QL = NX;            // -2 Q x_ref
+  static constexpr int RB = 2 * NX;        // Hessian diagonal of u_t
+  static constexpr int RHO = 2 * NX + NU;  // penalty parameter
+  static constexpr int KC = 2 * NX + NU + 1;
+};
+
 template <typename F, int NX, int NU, int DP>
 struct AgentCtx {
   const Model<F, NX, NU>* M;
@@ -185,11 +198,13 @@ struct AgentCtx {
   F* Us;
   F* Xo;             // output level, scenario base
   const F* h;        // scenario base
-  F qbar[NX], qbarT[NX];   // Hessian diagonals of x_t (t < T) and x_T
-  F qlin[NX], qlinT[NX];   // -2 Q x_ref and -2 Qf x_ref
-  F rbar[NU];
-  F x0[NX];
-  F rho;
+  const F* kc;       // this thread's constants (AgentConst layout), stride ks
+  int ks;
+  const F* qf;       // the agent's rows of Qf, x_ref and x_init
+  const F* xr;
+  const F* xi;
+
+  __device__ __forceinline__ F k(int e) const { return kc[e * ks]; }
 
   __device__ __forceinline__ F& C(int t, int e) const {
     return cache[((size_t)t * CacheLayout<NX, NU>::E + e) * N + i];
@@ -199,10 +214,15 @@ struct AgentCtx {
   __device__ __forceinline__ F& u(int t, int c) const { return U[((size_t)t * NU + c) * N + i]; }
   __device__ __forceinline__ F& us(int t, int c) const { return Us[((size_t)t * NU + c) * N + i]; }
   __device__ __forceinline__ F& x(int t, int r) const { return Xo[((size_t)t * NX + r) * N + i]; }
+  // Hessian diagonal of x_T
+  __device__ __forceinline__ F qbarT(int r) const {
+    return F(2) * qf[r] + (r < DP ? k(AgentConst<NX, NU>::RHO) * F(N - 1) : F(0));
+  }
   // linear term of x_t (t = 1..T): -2 Q_t x_ref - rho C' h_t
   __device__ __forceinline__ F q(int t, int r) const {
-    F v = (t < T) ? qlin[r] : qlinT[r];
-    if (r < DP) v -= rho * h[((size_t)(t - 1) * DP + r) * N + i];
+    using AC = AgentConst<NX, NU>;
+    F v = (t < T) ? k(AC::QL + r) : (F(-2) * qf[r]) * xr[r];
+    if (r < DP) v -= k(AC::RHO) * h[((size_t)(t - 1) * DP + r) * N + i];
     return v;
   }
 };
@@ -214,10 +234,11 @@ struct AgentCtx {
 // DI: A = [[I, dt I], [0, I]], B = [[b1 I], [b2 I]] (double integrator, checked
 // exactly on the host); the products skip the structural zeros and ones but
 // accumulate the remaining terms in the order of the dense loops.
-template <typename F, int NX, int NU, bool DI>
+// P_t entry (r, c), r <= c, is handed to put(r, c, value) as soon as it is formed.
+template <typename F, int NX, int NU, bool DI, class PutP>
 __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F (&Pn)[NX][NX],
-                                            uint16_t mask, const F (&rbar)[NU], const F* qdiag,
-                                            F (&Pt)[NX][NX], F (&K)[NU][NX], F (&L)[NU][NU]) {
+                                            uint16_t mask, const F* rbar, const F* qdiag, int ks,
+                                            PutP&& put, F (&K)[NU][NX], F (&L)[NU][NU]) {
   constexpr int H = NX / 2;
   F PA[NX][NX], PB[NX][NU];
 #pragma unroll
@@ -254,7 +275,7 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
 #pragma unroll
     for (int b = 0; b < NU; ++b) {
       const bool fb = (mask >> b) & 0x101;
-      F acc = (a == b) ? rbar[a] : F(0);
+      F acc = (a == b) ? rbar[a * ks] : F(0);
       if constexpr (DI) {
         acc = fma(Mo.B[0][0], PB[a][b], acc);
         acc = fma(Mo.B[H][0], PB[H + a][b], acc);
@@ -322,7 +343,7 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
     for (int r = 0; r < NX; ++r) {
 #pragma unroll
       for (int c = r; c < NX; ++c) {
-        F acc = (r == c) ? qdiag[r] : F(0);
+        F acc = (r == c) ? qdiag[r * ks] : F(0);
         if constexpr (DI) {
           if (r < H) {
             acc = acc + PA[r][c];
@@ -336,8 +357,7 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
         }
 #pragma unroll
         for (int k = 0; k < NU; ++k) acc = fma(Mm[k][r], K[k][c], acc);
-        Pt[r][c] = acc;
-        Pt[c][r] = acc;
+        put(r, c, acc);
       }
     }
   }
@@ -367,7 +387,7 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
-      for (int c = 0; c < NX; ++c) A.C(T, CL::P + r * NX + c) = (r == c) ? A.qbarT[r] : F(0);
+      for (int c = 0; c < NX; ++c) A.C(T, CL::P + r * NX + c) = (r == c) ? A.qbarT(r) : F(0);
   }
 #pragma unroll
   for (int r = 0; r < NX; ++r) A.C(T, CL::p + r) = pn[r];
@@ -377,12 +397,17 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
     F K[NU][NX], L[NU][NU];
     const bool refac = t <= dirty;
     if (refac) {
-      F Pn[NX][NX], Pt[NX][NX];
+      F Pn[NX][NX];
 #pragma unroll
       for (int r = 0; r < NX; ++r)
 #pragma unroll
         for (int c = 0; c < NX; ++c) Pn[r][c] = A.C(t + 1, CL::P + r * NX + c);
-      o.bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, A.rbar, t >= 1 ? A.qbar : nullptr, Pt, K, L);
+      auto put = [&](int r, int c, F v) {
+        A.C(t, CL::P + r * NX + c) = v;
+        if (c != r) A.C(t, CL::P + c * NX + r) = v;
+      };
+      o.bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, A.kc + AgentConst<NX, NU>::RB * A.ks,
+                                           t >= 1 ? A.kc + AgentConst<NX, NU>::QB * A.ks : nullptr, A.ks, put, K, L);
       ++nfact;
 #pragma unroll
       for (int a = 0; a < NU; ++a) {
@@ -390,12 +415,6 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
         for (int c = 0; c < NX; ++c) A.C(t, CL::K + a * NX + c) = K[a][c];
 #pragma unroll
         for (int b = 0; b <= a; ++b) A.C(t, CL::L + a * NU + b) = L[a][b];
-      }
-      if (t >= 1) {
-#pragma unroll
-        for (int r = 0; r < NX; ++r)
-#pragma unroll
-          for (int c = 0; c < NX; ++c) A.C(t, CL::P + r * NX + c) = Pt[r][c];
       }
       A.CM(t) = mask;
     } else {
@@ -505,7 +524,7 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
   F xv[NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
-    xv[r] = A.x0[r];
+    xv[r] = A.xi[r];
     A.x(0, r) = xv[r];
   }
   for (int t = 0; t < T; ++t) {
@@ -554,7 +573,7 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
       for (int a = 0; a < NU; ++a) {
         if (!(mask & (0x101u << a))) continue;
-        F g = A.rbar[a] * uv[a];
+        F g = A.k(AgentConst<NX, NU>::RB + a) * uv[a];
         if constexpr (DI) {
           g = fma(Mo.B[0][0], lam[a], g);
           g = fma(Mo.B[H][0], lam[H + a], g);
@@ -656,45 +675,57 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, i
     if (!clipped) return ST_CONVERGED;  // the LQR solution is the QP solution
   }
 
-  bool need_solve = true;
-  EqpScan<F> o;
+  // The lanes of the warp that reach this point step through their
+  // active-set iterations in rounds: in each round every lane that needs an
+  // EQP solve takes it in the same pass, since a pass costs the warp the same
+  // whatever number of lanes it serves.  Each lane's own sequence of working
+  // sets, steps and multiplier tests is unchanged.
+  const unsigned part = __activemask();
+  int status = -1;  // running
   for (;;) {
-    if (need_solve) {
-      if (as_max <= 0) return ST_QP_FAIL;
+    bool go = false;
+    if (status < 0) {
+      if (as_max <= 0) status = ST_QP_FAIL;
+      else go = true;
+    }
+    if (!__any_sync(part, go)) break;
+    if (go) {
       --as_max;
       ++neqp;
-      o = eqp_solve<F, NX, NU, DP, DI>(A, dirty, nfact);
-      if (o.bad) return ST_NUMERIC;
-      dirty = -1;
-      if (o.out) ratio_test<F, NX, NU, DP>(A, o);
-      if (o.blk >= 0) {
-        const F alpha = o.anum / o.aden;
-        for (int t = 0; t < T; ++t)
+      EqpScan<F> o = eqp_solve<F, NX, NU, DP, DI>(A, dirty, nfact);
+      if (o.bad) {
+        status = ST_NUMERIC;
+      } else {
+        dirty = -1;
+        if (o.out) ratio_test<F, NX, NU, DP>(A, o);
+        if (o.blk >= 0) {
+          const F alpha = o.anum / o.aden;
+          for (int t = 0; t < T; ++t)
 #pragma unroll
-          for (int a = 0; a < NU; ++a) {
-            const F cu = A.u(t, a);
-            A.u(t, a) = fma(alpha, A.us(t, a) - cu, cu);
+            for (int a = 0; a < NU; ++a) {
+              const F cu = A.u(t, a);
+              A.u(t, a) = fma(alpha, A.us(t, a) - cu, cu);
+            }
+          const int bt = o.blk / NU, ba = o.blk - bt * NU;
+          A.u(bt, ba) = (o.bside == 1) ? Mo.umin[ba] : Mo.umax[ba];
+          A.W(bt) = (uint16_t)(A.W(bt) | (o.bside == 1 ? (1u << ba) : (0x100u << ba)));
+          dirty = bt;
+        } else {
+          for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int a = 0; a < NU; ++a) A.u(t, a) = A.us(t, a);
+          if (o.widx >= 0 && o.worst < -eps_rel * o.scale) {
+            const int bt = o.widx / NU, ba = o.widx - bt * NU;
+            A.W(bt) = (uint16_t)(A.W(bt) & ~(0x101u << ba));
+            dirty = bt;
+          } else {
+            status = ST_CONVERGED;
           }
-        const int bt = o.blk / NU, ba = o.blk - bt * NU;
-        A.u(bt, ba) = (o.bside == 1) ? Mo.umin[ba] : Mo.umax[ba];
-        A.W(bt) = (uint16_t)(A.W(bt) | (o.bside == 1 ? (1u << ba) : (0x100u << ba)));
-        dirty = bt;
-        continue;
+        }
       }
-      for (int t = 0; t < T; ++t)
-#pragma unroll
-        for (int a = 0; a < NU; ++a) A.u(t, a) = A.us(t, a);
-      need_solve = false;
     }
-    if (o.widx >= 0 && o.worst < -eps_rel * o.scale) {
-      const int bt = o.widx / NU, ba = o.widx - bt * NU;
-      A.W(bt) = (uint16_t)(A.W(bt) & ~(0x101u << ba));
-      dirty = bt;
-      need_solve = true;
-      continue;
-    }
-    return ST_CONVERGED;
   }
+  return status;
 }
 
 // ---------------------------------------------------------------------------
@@ -734,9 +765,13 @@ __device__ void init_phase(const Dev<F>& D, const ScenMeta& s, int64_t t0, int64
   }
 }
 
+// Agent context of agent i; its constants are written to the thread's column
+// kc (stride ks) of a shared-memory table.
 template <typename F, int NX, int NU, int DP>
 __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, const Model<F, NX, NU>& M,
-                                                              const ScenMeta& s, int i, int lvl_out) {
+                                                              const ScenMeta& s, int i, int lvl_out, F* kc,
+                                                              int ks) {
+  using AC = AgentConst<NX, NU>;
   AgentCtx<F, NX, NU, DP> A;
   A.M = &M;
   A.N = s.N;
@@ -749,20 +784,22 @@ __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, c
   A.Us = D.Us + s.as_off * NU;
   A.Xo = D.X + (size_t)lvl_out * D.tot_xs * NX + s.xs_off * NX;
   A.h = D.h + s.as_off * DP;
-  A.rho = F(s.rho);
+  A.kc = kc;
+  A.ks = ks;
   const int64_t ag = s.agent_off + i;
+  A.qf = D.Qfd + ag * NX;
+  A.xr = D.x_ref + ag * NX;
+  A.xi = D.x_init + ag * NX;
   const F rnc = F(s.rho) * F(s.N - 1);
+  kc[AC::RHO * ks] = F(s.rho);
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
-    const F q = D.Qd[ag * NX + r], qf = D.Qfd[ag * NX + r], xr = D.x_ref[ag * NX + r];
-    A.qbar[r] = F(2) * q + (r < DP ? rnc : F(0));
-    A.qbarT[r] = F(2) * qf + (r < DP ? rnc : F(0));
-    A.qlin[r] = (F(-2) * q) * xr;
-    A.qlinT[r] = (F(-2) * qf) * xr;
-    A.x0[r] = D.x_init[ag * NX + r];
+    const F q = D.Qd[ag * NX + r], xr = D.x_ref[ag * NX + r];
+    kc[(AC::QB + r) * ks] = F(2) * q + (r < DP ? rnc : F(0));
+    kc[(AC::QL + r) * ks] = (F(-2) * q) * xr;
   }
 #pragma unroll
-  for (int c = 0; c < NU; ++c) A.rbar[c] = F(2) * D.Rd[ag * NU + c];
+  for (int c = 0; c < NU; ++c) kc[(AC::RB + c) * ks] = F(2) * D.Rd[ag * NU + c];
   return A;
 }
 
@@ -776,13 +813,13 @@ __device__ __forceinline__ int start_kind_of(const Dev<F>& D, int k) {
 template <typename F, int NX, int NU, int DP, bool DI>
 __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, int k,
                              int lvl_out, int i0, int stride, unsigned long long& neqp,
-                             unsigned long long& nfact) {
+                             unsigned long long& nfact, F* kcs) {
   const int kind = start_kind_of(D, k);
   const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
   const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
   int st = ST_CONVERGED;
   for (int i = i0; i < s.N; i += stride) {
-    AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, i, lvl_out);
+    AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, i, lvl_out, kcs + threadIdx.x, blockDim.x);
     const int r = xupdate_agent<F, NX, NU, DP, DI>(A, kind, as_max, eps, neqp, nfact);
     if (r > st) st = r;
   }
@@ -894,6 +931,81 @@ __device__ void gather_phase(const Dev<F>& D, const ScenMeta& s, int xl_new, int
   }
 }
 
+// Shared-memory tile of the tiled gather: for 32 own agents (rows) x 32
+// partners (columns), the signed weight sigma (2 theta^{k+1} - theta^k) and the
+// DP components of the pair normal.  Rows padded to 33 against bank conflicts.
+template <typename F, int DP>
+struct GatherTile {
+  F e[32][33];
+  F a[DP][32][33];
+};
+
+// The aggregate h of gather_phase for the agents i0..i0+31 of one scenario at
+// step tm1, computed by one warp.  Partners are swept in blocks of 32 in
+// increasing order; each block's weights and normals are staged through
+// coalesced row loads (pairs (i, j), i < j, are contiguous in j; pairs (j, i),
+// j < i, contiguous in i and staged transposed).  Each agent then adds its
+// partners' terms in increasing j: the same values, operations and order as
+// gather_phase, so the result is bitwise the same.
+template <typename F, int NX, int NU, int DP>
+__device__ void gather_tile(const Dev<F>& D, const ScenMeta& s, int xl_new, int tkp1, int tk, int i0, int tm1,
+                            GatherTile<F, DP>& ts) {
+  const int N = s.N, P = s.P, lane = threadIdx.x & 31;
+  const F* Xn = D.X + (size_t)xl_new * D.tot_xs * NX + s.xs_off * NX;
+  const F* thn = D.theta + (size_t)tkp1 * D.tot_ps + s.ps_off + (size_t)tm1 * P;
+  const F* tho = D.theta + (size_t)tk * D.tot_ps + s.ps_off + (size_t)tm1 * P;
+  const F* a = D.a + s.ps_off * DP + (size_t)tm1 * DP * P;
+  const int i = i0 + lane;
+  const bool own = i < N;
+  const int rows = min(32, N - i0);
+  F acc[DP];
+#pragma unroll
+  for (int c = 0; c < DP; ++c) acc[c] = own ? F(N - 1) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i] : F(0);
+  for (int j0 = 0; j0 < N; j0 += 32) {
+    const int cols = min(32, N - j0);
+    __syncwarp();
+    if (i0 < j0 + cols - 1) {
+      // pairs (i, j) with i < j: row r = own agent, lane = partner
+      const int j = j0 + lane;
+      for (int r = 0; r < rows; ++r) {
+        const int ii = i0 + r;
+        if (lane < cols && ii < j) {
+          const int pair = pair_index(N, ii, j);
+          ts.e[r][lane] = fma(F(2), thn[pair], -tho[pair]);
+#pragma unroll
+          for (int c = 0; c < DP; ++c) ts.a[c][r][lane] = a[(size_t)c * P + pair];
+        }
+      }
+    }
+    if (j0 < i0 + rows - 1) {
+      // pairs (j, i) with j < i: row r = partner, lane = own agent (transposed)
+      for (int r = 0; r < cols; ++r) {
+        const int jj = j0 + r;
+        if (own && jj < i) {
+          const int pair = pair_index(N, jj, i);
+          ts.e[lane][r] = -fma(F(2), thn[pair], -tho[pair]);
+#pragma unroll
+          for (int c = 0; c < DP; ++c) ts.a[c][lane][r] = a[(size_t)c * P + pair];
+        }
+      }
+    }
+    __syncwarp();
+    if (own) {
+      for (int cidx = 0; cidx < cols; ++cidx) {
+        if (j0 + cidx == i) continue;
+        const F e = ts.e[lane][cidx];
+#pragma unroll
+        for (int c = 0; c < DP; ++c) acc[c] = fma(e, ts.a[c][lane][cidx], acc[c]);
+      }
+    }
+  }
+  if (own) {
+    F* h = D.h + s.as_off * DP;
+#pragma unroll
+    for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+  }
+}
+
 // Pair phase and gather fused per time step for a CTA-resident scenario: the
 // projection steps of step t are computed for all pairs (coalesced), the
 // coupling weights e = 2 theta^{k+1} - theta^k and the normals of step t are
@@ -989,7 +1101,7 @@ struct CtaScratch {
 // iterations, residuals, work counters and the levels of the final iterate.
 template <typename F, int NX, int NU, int DP, bool DI>
 __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, int sc,
-                             CtaScratch& cs, F* sm, int sm_pairs) {
+                             CtaScratch& cs, F* sm, int sm_pairs, F* kcs) {
   const bool fused = sm != nullptr && s.P <= sm_pairs;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
@@ -1004,7 +1116,7 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
   unsigned long long neqp = 0, nfact = 0;
   for (int k = 0; k < D.max_iter; ++k) {
     const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
-    const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, xl ^ 1, tid, nt, neqp, nfact);
+    const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, xl ^ 1, tid, nt, neqp, nfact, kcs);
     if (st) atomicMax(&cs.flag, st);
     __syncthreads();
     iters = k + 1;
@@ -1053,6 +1165,7 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
 // decision (residuals, convergence, outputs) stays per scenario.
 // ---------------------------------------------------------------------------
 constexpr int kGroupMax = 32;
+constexpr int kPairBatch = 4;  // pairs whose operands a thread loads before computing
 
 constexpr int kGroupPairs = kGroupMax * (kGroupMax - 1) / 2;
 
@@ -1086,7 +1199,7 @@ __device__ __forceinline__ int member_of(const int* off, int G, int u) {
 
 template <typename F, int NX, int NU, int DP, bool DI>
 __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int* members, int G, GroupSm& gs,
-                          GroupStage<F, DP>& st, F* sm) {
+                          GroupStage<F, DP>& st, F* sm, F* kcs) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid < G) {
     const int sc = members[tid];
@@ -1139,7 +1252,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     // x-update
     if (my_m >= 0 && gs.active[my_m]) {
       const ScenMeta& s = gs.meta[my_m];
-      AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1);
+      AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1, kcs + tid, nt);
       const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
       const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
       const int st = xupdate_agent<F, NX, NU, DP, DI>(A, start_kind_of(D, k), as_max, eps, neqp, nfact);
@@ -1155,44 +1268,80 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     }
     __syncthreads();
     // fused consensus projection / dual update and gather, step by step; the
-    // step's positions and the pair table are read from shared memory
+    // step's positions and the pair table are read from shared memory.  The
+    // next step's positions, and the operands of each batch of kPairBatch
+    // pairs, are loaded ahead of their use so that the load latency overlaps
+    // the arithmetic.
+    const bool mine = my_m >= 0 && gs.active[my_m];
+    const F* Xmine = nullptr;
+    int Nmine = 1;
+    F pnext[DP];
+    if (mine) {
+      const ScenMeta& s = gs.meta[my_m];
+      Xmine = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+      Nmine = s.N;
+#pragma unroll
+      for (int c = 0; c < DP; ++c) pnext[c] = Xmine[((size_t)NX + c) * Nmine + my_i];
+    }
     for (int tm1 = 0; tm1 < T; ++tm1) {
-      if (my_m >= 0 && gs.active[my_m]) {
-        const ScenMeta& s = gs.meta[my_m];
-        const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+      if (mine) {
 #pragma unroll
-        for (int c = 0; c < DP; ++c) st.pos[c][tid] = Xn[((size_t)(tm1 + 1) * NX + c) * s.N + my_i];
+        for (int c = 0; c < DP; ++c) st.pos[c][tid] = pnext[c];
       }
       __syncthreads();
-      for (int u = tid; u < nP; u += nt) {
-        const int m = st.mem[u];
-        if (!gs.active[m]) continue;
-        const ScenMeta& s = gs.meta[m];
-        const int P = s.P, pair = u - gs.poff[m];
-        const F* a = D.a + s.ps_off * DP;
-        const size_t q = (size_t)tm1 * P + pair;
-        const uint32_t fij = st.pair[u];
-        const int fi = fij & 0xFF, fj = fij >> 8;
-        F sdot = 0;
-        unsigned long long amax = 0;
+      for (int ub = tid; ub < nP; ub += kPairBatch * nt) {
+        F av[kPairBatch][DP], thv[kPairBatch];
+        int mk[kPairBatch];
 #pragma unroll
-        for (int c = 0; c < DP; ++c) {
-          const F av = a[((size_t)tm1 * DP + c) * P + pair];
-          smA[c * nP + u] = av;
-          sdot = fma(av, st.pos[c][fi] - st.pos[c][fj], sdot);
-          const unsigned long long ab = abs_bits(av);
-          amax = ab > amax ? ab : amax;
+        for (int b = 0; b < kPairBatch; ++b) {
+          const int u = ub + b * nt;
+          mk[b] = -1;
+          if (u < nP) {
+            const int m = st.mem[u];
+            if (gs.active[m]) {
+              mk[b] = m;
+              const ScenMeta& s = gs.meta[m];
+              const int P = s.P, pair = u - gs.poff[m];
+              const F* a = D.a + s.ps_off * DP;
+#pragma unroll
+              for (int c = 0; c < DP; ++c) av[b][c] = a[((size_t)tm1 * DP + c) * P + pair];
+              thv[b] = D.theta[(size_t)tk * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair];
+            }
+          }
         }
-        const F th = D.theta[(size_t)tk * D.tot_ps + s.ps_off + q];
-        F tn = fma(F(s.d) - sdot, F(0.5), th);
-        if (sign_set(tn)) tn = F(0);
-        D.theta[(size_t)tkp1 * D.tot_ps + s.ps_off + q] = tn;
-        smE[u] = fma(F(2), tn, -th);
-        const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
-        if (v > gs.rb[m]) atomicMax(&gs.rb[m], v);
+#pragma unroll
+        for (int b = 0; b < kPairBatch; ++b) {
+          if (mk[b] < 0) continue;
+          const int u = ub + b * nt, m = mk[b];
+          const ScenMeta& s = gs.meta[m];
+          const int P = s.P, pair = u - gs.poff[m];
+          const uint32_t fij = st.pair[u];
+          const int fi = fij & 0xFF, fj = fij >> 8;
+          F sdot = 0;
+          unsigned long long amax = 0;
+#pragma unroll
+          for (int c = 0; c < DP; ++c) {
+            const F avc = av[b][c];
+            smA[c * nP + u] = avc;
+            sdot = fma(avc, st.pos[c][fi] - st.pos[c][fj], sdot);
+            const unsigned long long ab = abs_bits(avc);
+            amax = ab > amax ? ab : amax;
+          }
+          const F th = thv[b];
+          F tn = fma(F(s.d) - sdot, F(0.5), th);
+          if (sign_set(tn)) tn = F(0);
+          D.theta[(size_t)tkp1 * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair] = tn;
+          smE[u] = fma(F(2), tn, -th);
+          const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
+          if (v > gs.rb[m]) atomicMax(&gs.rb[m], v);
+        }
       }
       __syncthreads();
-      if (my_m >= 0 && gs.active[my_m]) {
+      if (mine && tm1 + 1 < T) {
+#pragma unroll
+        for (int c = 0; c < DP; ++c) pnext[c] = Xmine[((size_t)(tm1 + 2) * NX + c) * Nmine + my_i];
+      }
+      if (mine) {
         const ScenMeta& s = gs.meta[my_m];
         const int N = s.N, i = my_i, base = gs.poff[my_m];
         F acc[DP];

@@ -91,6 +91,8 @@ struct tadmm_handle {
   // graph mode (conditional WHILE node over the per-iteration phase kernels)
   void *gs_iter = nullptr, *gs_active = nullptr, *gs_need = nullptr, *gs_fail = nullptr, *gs_rb = nullptr,
        *gs_sb = nullptr;
+  void* gs_blk = nullptr;   // int2 (scenario, first agent) per 32-agent gather block
+  int n_gblk = 0;
   cudaGraphExec_t wexec = nullptr;
   double w_tol = -1.0;
   int w_iter = -1;

@@ -30,7 +30,9 @@ __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batche
   __shared__ GroupStage<F, DP> gst;
   __shared__ int s_q;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  F* sm = D.sm_pairs > 0 ? (F*)dyn_smem : nullptr;
+  // dynamic shared memory: agent constants [KC][threads], then the pair staging
+  F* kcs = (F*)dyn_smem;
+  F* sm = D.sm_pairs > 0 ? kcs + AgentConst<NX, NU>::KC * blockDim.x : nullptr;
   load_model<F, NX, NU>(M, D.model);
   for (;;) {
     __syncthreads();
@@ -40,12 +42,12 @@ __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batche
     if (qi >= D.n_groups) return;
     const int g = D.order[qi];
     const int b0 = D.goff[g], G = D.goff[g + 1] - b0;
-    if (G == 1) {
+    if (G == 1 && !(D.single_as_group && D.meta[D.gmem[b0]].N <= kGroupMax)) {
       const int sc = D.gmem[b0];
       const ScenMeta s = D.meta[sc];
-      run_scenario<F, NX, NU, DP, DI>(D, M, s, sc, cs, sm, D.sm_pairs);
+      run_scenario<F, NX, NU, DP, DI>(D, M, s, sc, cs, sm, D.sm_pairs, kcs);
     } else {
-      run_group<F, NX, NU, DP, DI>(D, M, D.gmem + b0, G, gs, gst, sm);
+      run_group<F, NX, NU, DP, DI>(D, M, D.gmem + b0, G, gs, gst, sm, kcs);
     }
   }
 }
@@ -65,15 +67,16 @@ __global__ void k_init(Dev<F> D, int sc) {
 }
 
 template <typename F, int NX, int NU, int DP, bool DI>
-__global__ void __launch_bounds__(128) k_xupdate(Dev<F> D, int sc, int k, int lvl_out, int32_t* flag) {
+__global__ void __launch_bounds__(32) k_xupdate(Dev<F> D, int sc, int k, int lvl_out, int32_t* flag) {
   __shared__ Model<F, NX, NU> M;
+  __shared__ F kcs[AgentConst<NX, NU>::KC * 32];
   load_model<F, NX, NU>(M, D.model);
   __syncthreads();
   const ScenMeta s = D.meta[sc];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.N) return;
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, lvl_out, i, s.N, neqp, nfact);
+  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, lvl_out, i, s.N, neqp, nfact, kcs);
   if (st) atomicMax(flag, st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
@@ -102,11 +105,12 @@ __global__ void __launch_bounds__(256) k_dual(Dev<F> D, int sc, int xl, int tkm1
   if (threadIdx.x == 0 && sb) atomicMax(red1, sb);
 }
 
+// One warp per (block of 32 agents, step): grid (ceil(N / 32), T), 32 threads.
 template <typename F, int NX, int NU, int DP>
-__global__ void k_gather(Dev<F> D, int sc, int xl_new, int tkp1, int tk) {
+__global__ void __launch_bounds__(32) k_gather(Dev<F> D, int sc, int xl_new, int tkp1, int tk) {
+  __shared__ GatherTile<F, DP> ts;
   const ScenMeta s = D.meta[sc];
-  gather_phase<F, NX, NU, DP>(D, s, xl_new, tkp1, tk, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                              (int64_t)gridDim.x * blockDim.x);
+  gather_tile<F, NX, NU, DP>(D, s, xl_new, tkp1, tk, blockIdx.x * 32, blockIdx.y, ts);
 }
 
 template <typename F>
@@ -168,9 +172,10 @@ __global__ void k_g_init(Dev<F> D, GState G) {
 }
 
 template <typename F, int NX, int NU, int DP, bool DI>
-__global__ void __launch_bounds__(128) k_g_xupdate(Dev<F> D, GState G, const int32_t* __restrict__ agent_scen,
+__global__ void __launch_bounds__(32) k_g_xupdate(Dev<F> D, GState G, const int32_t* __restrict__ agent_scen,
                                                    int64_t tot_agents) {
   __shared__ Model<F, NX, NU> M;
+  __shared__ F kcs[AgentConst<NX, NU>::KC * 32];
   load_model<F, NX, NU>(M, D.model);
   __syncthreads();
   const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(128) k_g_xupdate(Dev<F> D, GState G, const int
   const ScenMeta s = D.meta[sc];
   const int i = (int)(ga - s.agent_off), k = G.iter[sc];
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, (k + 1) & 1, i, s.N, neqp, nfact);
+  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, (k + 1) & 1, i, s.N, neqp, nfact, kcs);
   if (st) atomicMax(&G.fail[sc], st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
@@ -285,19 +290,18 @@ __global__ void k_g_check2(Dev<F> D, GState G, cudaGraphConditionalHandle cond) 
   if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
+// One warp per (scenario, block of 32 agents, step): blk[b] = (scenario, first agent).
 template <typename F, int NX, int NU, int DP>
-__global__ void __launch_bounds__(128) k_g_gather(Dev<F> D, GState G, const int32_t* __restrict__ agent_scen,
-                                                  int64_t tot_agents) {
-  const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int tm1 = blockIdx.y;
-  if (ga >= tot_agents) return;
-  const int sc = agent_scen[ga];
+__global__ void __launch_bounds__(32) k_g_gather(Dev<F> D, GState G, const int2* __restrict__ blk) {
+  __shared__ GatherTile<F, DP> ts;
+  const int2 b = blk[blockIdx.x];
+  const int sc = b.x;
   if (!G.active[sc]) return;
   const ScenMeta s = D.meta[sc];
+  const int tm1 = blockIdx.y;
   if (tm1 >= s.T) return;
   const int k1 = G.iter[sc];  // already advanced: levels of iterate k1 = k + 1
-  const int64_t idx = (int64_t)tm1 * s.N + (ga - s.agent_off);
-  gather_phase<F, NX, NU, DP>(D, s, k1 & 1, k1 % 3, (k1 + 2) % 3, idx, (int64_t)s.N * s.T);
+  gather_tile<F, NX, NU, DP>(D, s, k1 & 1, k1 % 3, (k1 + 2) % 3, b.y, tm1, ts);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,6 +423,7 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.order = h->gorder;
   D.as_max = h->opt.as_max;
   D.eps_rel = h->opt.eps_rel;
+  D.single_as_group = (h->opt.flags & (TADMM_FLAG_NO_GROUPING | TADMM_FLAG_NO_FUSED_PAIR_GATHER)) ? 0 : 1;
   return D;
 }
 
@@ -497,13 +502,16 @@ static int variant_maxt(int v) {
 }
 
 // Dynamic shared memory of the fused pair/gather staging: (DP + 1) values per
-// pair of the largest scenario, if that fits the per-CTA budget.
+// pair of the largest scenario, if that fits the per-CTA budget; otherwise per
+// pair of the largest group that runs the group path (at most 32 agents), the
+// larger scenarios then taking the unfused sweeps.
 template <typename F, int DP>
 static size_t fused_smem_bytes(const tadmm_handle* h, int* pairs_out) {
   int pmax = h->max_group_pairs;
   for (const ScenMeta& m : h->meta_h) pmax = std::max(pmax, m.P);
-  const size_t bytes = (size_t)(DP + 1) * pmax * sizeof(F);
   const size_t budget = 96 * 1024;
+  if ((size_t)(DP + 1) * pmax * sizeof(F) > budget) pmax = h->max_group_pairs;
+  const size_t bytes = (size_t)(DP + 1) * pmax * sizeof(F);
   if ((h->opt.flags & TADMM_FLAG_NO_FUSED_PAIR_GATHER) || pmax == 0 || bytes > budget) {
     if (pairs_out) *pairs_out = 0;
     return 0;
@@ -512,11 +520,17 @@ static size_t fused_smem_bytes(const tadmm_handle* h, int* pairs_out) {
   return bytes;
 }
 
+// Dynamic shared memory of the per-thread agent constants.
+template <typename F, int NX, int NU>
+static size_t agent_const_bytes(int tpc) {
+  return (size_t)AgentConst<NX, NU>::KC * tpc * sizeof(F);
+}
+
 template <typename F, int NX, int NU, int DP>
 int Impl<F, NX, NU, DP>::max_ctas_per_sm(int tpc, int variant, const tadmm_handle* h) {
   int n = 0;
   if (tpc > variant_maxt(variant)) return 0;
-  const size_t smem = h ? fused_smem_bytes<F, DP>(h, nullptr) : 0;
+  const size_t smem = (h ? fused_smem_bytes<F, DP>(h, nullptr) : 0) + agent_const_bytes<F, NX, NU>(tpc);
   const void* kfn = batched_kernel<F, NX, NU, DP>(variant, h ? h->di != 0 : false);
   if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kfn, tpc, smem) != cudaSuccess) {
@@ -544,7 +558,7 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
     D.tol = tol;
     D.max_iter = max_iter;
     int smp = 0;
-    const size_t smem = fused_smem_bytes<F, DP>(h, &smp);
+    const size_t smem = fused_smem_bytes<F, DP>(h, &smp) + agent_const_bytes<F, NX, NU>(tpc);
     D.sm_pairs = smp;
     cudaGraph_t g = nullptr;
     int rc = cuda_check(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -591,9 +605,9 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
       cudaMemsetAsync(h->flag, 0, sizeof(int32_t), st);
       cudaMemsetAsync(h->red2, 0, 2 * sizeof(unsigned long long), st);
       if (h->di)
-        k_xupdate<F, NX, NU, DP, true><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
+        k_xupdate<F, NX, NU, DP, true><<<grid_for(s.N, 32), 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
       else
-        k_xupdate<F, NX, NU, DP, false><<<grid_for(s.N, 128), 128, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
+        k_xupdate<F, NX, NU, DP, false><<<grid_for(s.N, 32), 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
       k_pair<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, xl, tk, tkp1, h->red2);
       launches += 2;
       cudaMemcpyAsync(hb, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
@@ -621,7 +635,7 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
         if (r_ok && s_ok) { status = ST_CONVERGED; xl ^= 1; break; }
         if (last) { xl ^= 1; break; }
       }
-      k_gather<F, NX, NU, DP><<<grid_for(NT, 128, h->sm_count * 8), 128, 0, st>>>(D, sc, xl ^ 1, tkp1, tk);
+      k_gather<F, NX, NU, DP><<<dim3((s.N + 31) / 32, s.T), 32, 0, st>>>(D, sc, xl ^ 1, tkp1, tk);
       ++launches;
       xl ^= 1;
     }
@@ -644,6 +658,23 @@ int Impl<F, NX, NU, DP>::solve_graph(tadmm_handle* h, double tol, int max_iter, 
       cudaGetLastError();
       return set_error(TADMM_ENOMEM, "graph-mode state allocation failed");
     }
+  }
+  if (!h->gs_blk) {
+    // gather blocks: (scenario, first agent) for every 32 agents of every scenario
+    std::vector<int32_t> blk;
+    for (int sc = 0; sc < h->n_scen; ++sc)
+      for (int i0 = 0; i0 < h->meta_h[sc].N; i0 += 32) {
+        blk.push_back(sc);
+        blk.push_back(i0);
+      }
+    h->n_gblk = (int)(blk.size() / 2);
+    if (cudaMalloc(&h->gs_blk, 4 * std::max<size_t>(blk.size(), 2)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(TADMM_ENOMEM, "graph-mode state allocation failed");
+    }
+    if ((rc = cuda_check(cudaMemcpy(h->gs_blk, blk.data(), 4 * blk.size(), cudaMemcpyHostToDevice),
+                         "graph-mode gather table")))
+      return rc;
   }
   GState G{(int32_t*)h->gs_iter, (int32_t*)h->gs_active, (int32_t*)h->gs_need, (int32_t*)h->gs_fail,
            (unsigned long long*)h->gs_rb, (unsigned long long*)h->gs_sb};
@@ -680,18 +711,18 @@ int Impl<F, NX, NU, DP>::solve_graph(tadmm_handle* h, double tol, int max_iter, 
       cudaGraphDestroy(g);
       return rc;
     }
-    const dim3 gx(grid_for(h->tot_agents, 128, 1 << 30));
+    const dim3 gx(grid_for(h->tot_agents, 32, 1 << 30));
     const dim3 gp(grid_for(h->tot_pairs, 128, 1 << 30), tmax);
-    const dim3 gg(grid_for(h->tot_agents, 128, 1 << 30), tmax);
+    const dim3 gg(h->n_gblk, tmax);
     if (h->di)
-      k_g_xupdate<F, NX, NU, DP, true><<<gx, 128, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+      k_g_xupdate<F, NX, NU, DP, true><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
     else
-      k_g_xupdate<F, NX, NU, DP, false><<<gx, 128, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+      k_g_xupdate<F, NX, NU, DP, false><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
     if (h->tot_pairs > 0) k_g_pair<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);
     k_g_check1<F><<<grid_for(h->n_scen, 128), 128, 0, h->cap_stream>>>(D, G);
     if (h->tot_pairs > 0) k_g_dual<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);
     k_g_check2<F><<<1, 1024, 0, h->cap_stream>>>(D, G, cond);
-    k_g_gather<F, NX, NU, DP><<<gg, 128, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+    k_g_gather<F, NX, NU, DP><<<gg, 32, 0, h->cap_stream>>>(D, G, (const int2*)h->gs_blk);
     cudaError_t le = cudaGetLastError();
     cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &body);
     if (le != cudaSuccess || ee != cudaSuccess) {

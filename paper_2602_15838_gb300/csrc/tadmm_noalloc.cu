@@ -93,13 +93,14 @@ __global__ void k_noalloc_setup(ScenMeta* meta, int32_t* order, int32_t* pairs, 
 // The single scenario's ADMM run: the same phases as the batched persistent
 // kernel, in one CTA.
 template <typename F, int NX, int NU, int DP>
-__global__ void __launch_bounds__(256) k_noalloc_solve(Dev<F> D) {
+__global__ void __launch_bounds__(64) k_noalloc_solve(Dev<F> D) {
   __shared__ Model<F, NX, NU> M;
   __shared__ CtaScratch cs;
+  __shared__ F kcs[AgentConst<NX, NU>::KC * 64];
   load_model<F, NX, NU>(M, D.model);
   __syncthreads();
   const ScenMeta s = D.meta[0];
-  run_scenario<F, NX, NU, DP, false>(D, M, s, 0, cs, nullptr, 0);
+  run_scenario<F, NX, NU, DP, false>(D, M, s, 0, cs, nullptr, 0, kcs);
 }
 
 __global__ void k_noalloc_results(const int32_t* status, const int32_t* iters, const double* res,
