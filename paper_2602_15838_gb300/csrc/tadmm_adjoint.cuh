@@ -123,25 +123,9 @@ __device__ void lq_solve(const Model<F, NX, NU>& Mo, const F* cache, const uint1
       for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], Pcp[r], acc);
       sv[a] = (mask & (0x101u << a)) ? F(0) : acc;
 #pragma unroll
-      for (int b = 0; b < NU; ++b) L[a][b] = (b <= a) ? C(t, CL::L + a * NU + b) : F(0);
+      for (int b = 0; b < NU; ++b) L[a][b] = C(t, CL::L + (b <= a ? a * NU + b : b * NU + a));
     }
-    {
-      F y[NU];
-#pragma unroll
-      for (int r = 0; r < NU; ++r) {
-        F v = -sv[r];
-#pragma unroll
-        for (int k = 0; k < r; ++k) v = fma(-L[r][k], y[k], v);
-        y[r] = v * L[r][r];
-      }
-#pragma unroll
-      for (int r = NU - 1; r >= 0; --r) {
-        F v = y[r];
-#pragma unroll
-        for (int k = r + 1; k < NU; ++k) v = fma(-L[k][r], kv[k], v);
-        kv[r] = v * L[r][r];
-      }
-    }
+    neg_sinv<F, NU>(L, sv, kv);
 #pragma unroll
     for (int a = 0; a < NU; ++a) kk[t * NU + a] = kv[a];
     if (t >= 1) {

@@ -90,7 +90,7 @@ template <int NX, int NU>
 struct CacheLayout {
   static constexpr int P = 0;
   static constexpr int K = NX * NX;
-  static constexpr int L = K + NU * NX;
+  static constexpr int L = K + NU * NX;   // S^{-1}, lower triangle (row-major NU x NU slots)
   static constexpr int k = L + NU * NU;
   static constexpr int p = k + NU;
   static constexpr int E = p + NX;
@@ -218,6 +218,15 @@ struct AgentCtx {
   __device__ __forceinline__ F qbarT(int r) const {
     return F(2) * qf[r] + (r < DP ? k(AgentConst<NX, NU>::RHO) * F(N - 1) : F(0));
   }
+  // h_t component r (r < DP) of stage t = 1..T
+  __device__ __forceinline__ F hv(int t, int r) const { return h[((size_t)(t - 1) * DP + r) * N + i]; }
+  // linear term of x_t, t < T, from a loaded h_t component
+  __device__ __forceinline__ F q_h(int r, F hr) const {
+    using AC = AgentConst<NX, NU>;
+    F v = k(AC::QL + r);
+    if (r < DP) v -= k(AC::RHO) * hr;
+    return v;
+  }
   // linear term of x_t (t = 1..T): -2 Q_t x_ref - rho C' h_t
   __device__ __forceinline__ F q(int t, int r) const {
     using AC = AgentConst<NX, NU>;
@@ -230,10 +239,56 @@ struct AgentCtx {
 // Factorization of one stage with inputs in `mask` fixed (Riccati backward
 // recursion of Sec. IV.B restricted to the free inputs):
 //   S = Rbar + B'P B, M = B'P A (fixed rows/cols replaced by identity / zero),
-//   S = L L', K = -S^{-1} M, P_t = Qbar_t + A'P A + M'K.
+//   K = -S^{-1} M, P_t = Qbar_t + A'P A + M'K; L receives S^{-1}.
 // DI: A = [[I, dt I], [0, I]], B = [[b1 I], [b2 I]] (double integrator, checked
 // exactly on the host); the products skip the structural zeros and ones but
 // accumulate the remaining terms in the order of the dense loops.
+// Inverse of the symmetric NU x NU matrix S (NU = 2 or 3) by its adjugate;
+// returns 1 unless S is positive definite (Sylvester's criterion: positive
+// leading principal minors).  Si receives the full symmetric inverse.
+template <typename F, int NU>
+__device__ __forceinline__ int sym_inverse(const F (&S)[NU][NU], F (&Si)[NU][NU]) {
+  static_assert(NU == 2 || NU == 3, "input dimension 2 or 3");
+  if constexpr (NU == 2) {
+    const F det = fma(S[0][0], S[1][1], -(S[0][1] * S[0][1]));
+    const int bad = !(S[0][0] > F(0)) || !(det > F(0));
+    const F id = F(1) / det;
+    Si[0][0] = S[1][1] * id;
+    Si[1][1] = S[0][0] * id;
+    Si[0][1] = Si[1][0] = -(S[0][1] * id);
+    return bad;
+  } else {
+    const F c00 = fma(S[1][1], S[2][2], -(S[1][2] * S[1][2]));
+    const F c01 = fma(S[0][2], S[1][2], -(S[0][1] * S[2][2]));
+    const F c02 = fma(S[0][1], S[1][2], -(S[0][2] * S[1][1]));
+    const F c11 = fma(S[0][0], S[2][2], -(S[0][2] * S[0][2]));
+    const F c12 = fma(S[0][1], S[0][2], -(S[0][0] * S[1][2]));
+    const F c22 = fma(S[0][0], S[1][1], -(S[0][1] * S[0][1]));
+    const F det = fma(S[0][2], c02, fma(S[0][1], c01, S[0][0] * c00));
+    const int bad = !(S[0][0] > F(0)) || !(c22 > F(0)) || !(det > F(0));
+    const F id = F(1) / det;
+    Si[0][0] = c00 * id;
+    Si[1][1] = c11 * id;
+    Si[2][2] = c22 * id;
+    Si[0][1] = Si[1][0] = c01 * id;
+    Si[0][2] = Si[2][0] = c02 * id;
+    Si[1][2] = Si[2][1] = c12 * id;
+    return bad;
+  }
+}
+
+// out = -S^{-1} v with the symmetric inverse Si.
+template <typename F, int NU>
+__device__ __forceinline__ void neg_sinv(const F (&Si)[NU][NU], const F (&v)[NU], F (&out)[NU]) {
+#pragma unroll
+  for (int a = 0; a < NU; ++a) {
+    F acc = Si[a][0] * v[0];
+#pragma unroll
+    for (int b = 1; b < NU; ++b) acc = fma(Si[a][b], v[b], acc);
+    out[a] = -acc;
+  }
+}
+
 // P_t entry (r, c), r <= c, is handed to put(r, c, value) as soon as it is formed.
 template <typename F, int NX, int NU, bool DI, class PutP>
 __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F (&Pn)[NX][NX],
@@ -298,44 +353,16 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
       Mm[a][c] = fa ? F(0) : acc;
     }
   }
-  // Cholesky S = L L', diagonal stored inverted
-  int bad = 0;
-#pragma unroll
-  for (int j = 0; j < NU; ++j) {
-    F dj = S[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) dj = fma(-L[j][k], L[j][k], dj);
-    if (!(dj > F(0))) bad = 1;
-    const F inv = F(1) / sqrt_(dj);
-    L[j][j] = inv;
-#pragma unroll
-    for (int r = j + 1; r < NU; ++r) {
-      F v = S[r][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) v = fma(-L[r][k], L[j][k], v);
-      L[r][j] = v * inv;
-    }
-#pragma unroll
-    for (int r = 0; r < j; ++r) L[r][j] = 0;
-  }
-  // K = -S^{-1} M, column by column
+  // S^{-1} and K = -S^{-1} M, column by column
+  const int bad = sym_inverse<F, NU>(S, L);
 #pragma unroll
   for (int c = 0; c < NX; ++c) {
-    F y[NU];
+    F mc[NU], kc[NU];
 #pragma unroll
-    for (int r = 0; r < NU; ++r) {
-      F v = -Mm[r][c];
+    for (int r = 0; r < NU; ++r) mc[r] = Mm[r][c];
+    neg_sinv<F, NU>(L, mc, kc);
 #pragma unroll
-      for (int k = 0; k < r; ++k) v = fma(-L[r][k], y[k], v);
-      y[r] = v * L[r][r];
-    }
-#pragma unroll
-    for (int r = NU - 1; r >= 0; --r) {
-      F v = y[r];
-#pragma unroll
-      for (int k = r + 1; k < NU; ++k) v = fma(-L[k][r], K[k][c], v);
-      K[r][c] = v * L[r][r];
-    }
+    for (int r = 0; r < NU; ++r) K[r][c] = kc[r];
   }
   if (qdiag != nullptr) {
     // P_t = Qbar_t + A'(P A) + M'K, upper triangle mirrored
@@ -392,9 +419,25 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
   for (int r = 0; r < NX; ++r) A.C(T, CL::p + r) = pn[r];
 
+  // the mask, cached gains and h of the next stage are loaded one stage ahead
+  uint16_t mask_n = A.W(T - 1);
+  F Kn[NU][NX], Ln[NU][NU], hn[DP];
+  if (T - 1 > dirty) {
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+#pragma unroll
+      for (int c = 0; c < NX; ++c) Kn[a][c] = A.C(T - 1, CL::K + a * NX + c);
+#pragma unroll
+      for (int b = 0; b < NU; ++b) Ln[a][b] = A.C(T - 1, CL::L + (b <= a ? a * NU + b : b * NU + a));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < DP; ++r) hn[r] = (T - 1 >= 1) ? A.hv(T - 1, r) : F(0);
   for (int t = T - 1; t >= 0; --t) {
-    const uint16_t mask = A.W(t);
-    F K[NU][NX], L[NU][NU];
+    const uint16_t mask = mask_n;
+    F K[NU][NX], L[NU][NU], ht[DP];
+#pragma unroll
+    for (int r = 0; r < DP; ++r) ht[r] = hn[r];
     const bool refac = t <= dirty;
     if (refac) {
       F Pn[NX][NX];
@@ -421,10 +464,24 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
 #pragma unroll
       for (int a = 0; a < NU; ++a) {
 #pragma unroll
-        for (int c = 0; c < NX; ++c) K[a][c] = A.C(t, CL::K + a * NX + c);
+        for (int c = 0; c < NX; ++c) K[a][c] = Kn[a][c];
 #pragma unroll
-        for (int b = 0; b < NU; ++b) L[a][b] = (b <= a) ? A.C(t, CL::L + a * NU + b) : F(0);
+        for (int b = 0; b < NU; ++b) L[a][b] = Ln[a][b];
       }
+    }
+    if (t >= 1) {
+      mask_n = A.W(t - 1);
+      if (t - 1 > dirty) {
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+#pragma unroll
+          for (int c = 0; c < NX; ++c) Kn[a][c] = A.C(t - 1, CL::K + a * NX + c);
+#pragma unroll
+          for (int b = 0; b < NU; ++b) Ln[a][b] = A.C(t - 1, CL::L + (b <= a ? a * NU + b : b * NU + a));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < DP; ++r) hn[r] = (t - 1 >= 1) ? A.hv(t - 1, r) : F(0);
     }
     // affine pass: P_{t+1} c + p_{t+1} with c = B_fixed u_fixed
     F Pcp[NX];
@@ -472,29 +529,13 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
       }
       sv[a] = (mask & (0x101u << a)) ? F(0) : acc;
     }
-    {
-      F y[NU];
-#pragma unroll
-      for (int r = 0; r < NU; ++r) {
-        F v = -sv[r];
-#pragma unroll
-        for (int k = 0; k < r; ++k) v = fma(-L[r][k], y[k], v);
-        y[r] = v * L[r][r];
-      }
-#pragma unroll
-      for (int r = NU - 1; r >= 0; --r) {
-        F v = y[r];
-#pragma unroll
-        for (int k = r + 1; k < NU; ++k) v = fma(-L[k][r], kk[k], v);
-        kk[r] = v * L[r][r];
-      }
-    }
+    neg_sinv<F, NU>(L, sv, kk);
 #pragma unroll
     for (int a = 0; a < NU; ++a) A.C(t, CL::k + a) = kk[a];
     if (t >= 1) {
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
-        F acc = A.q(t, r);
+        F acc = A.q_h(r, r < DP ? ht[r] : F(0));
         if constexpr (DI) {
           if (r < H) {
             acc = acc + Pcp[r];
@@ -527,17 +568,42 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
     xv[r] = A.xi[r];
     A.x(0, r) = xv[r];
   }
+  // the mask and feedback of the next stage are loaded one stage ahead
+  uint16_t fmask_n = A.W(0);
+  F kf_n[NU], Kf_n[NU][NX];
+#pragma unroll
+  for (int a = 0; a < NU; ++a) {
+    kf_n[a] = A.C(0, CL::k + a);
+#pragma unroll
+    for (int c = 0; c < NX; ++c) Kf_n[a][c] = A.C(0, CL::K + a * NX + c);
+  }
   for (int t = 0; t < T; ++t) {
-    const uint16_t mask = A.W(t);
+    const uint16_t mask = fmask_n;
+    F kf[NU], Kf[NU][NX];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      kf[a] = kf_n[a];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) Kf[a][c] = Kf_n[a][c];
+    }
+    if (t + 1 < T) {
+      fmask_n = A.W(t + 1);
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        kf_n[a] = A.C(t + 1, CL::k + a);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) Kf_n[a][c] = A.C(t + 1, CL::K + a * NX + c);
+      }
+    }
     F uv[NU];
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
       if (mask & (1u << a)) uv[a] = Mo.umin[a];
       else if (mask & (0x100u << a)) uv[a] = Mo.umax[a];
       else {
-        F acc = A.C(t, CL::k + a);
+        F acc = kf[a];
 #pragma unroll
-        for (int c = 0; c < NX; ++c) acc = fma(A.C(t, CL::K + a * NX + c), xv[c], acc);
+        for (int c = 0; c < NX; ++c) acc = fma(Kf[a][c], xv[c], acc);
         uv[a] = acc;
         const unsigned long long ku = mono_key(acc);
         o.out |= (ku < kmin[a]) | (ku > kmax[a]);
