@@ -28,6 +28,8 @@
 
 #include "tadmm_df64.cuh"
 
+#include <type_traits>
+
 namespace tadmm {
 
 enum { ST_CONVERGED = 0, ST_NOT_CONVERGED = 1, ST_QP_FAIL = 2, ST_NUMERIC = 3 };
@@ -84,6 +86,7 @@ struct Dev {
   int32_t as_max;            // 0: 10*T*NU + 10
   double eps_rel;
   int32_t single_as_group;   // 1: a lone scenario of at most 32 agents also runs the group path
+  int32_t coop;              // 1: refactorizations may be spread over lane groups
 };
 
 template <int NX, int NU>
@@ -203,6 +206,7 @@ struct AgentCtx {
   const F* qf;       // the agent's rows of Qf, x_ref and x_init
   const F* xr;
   const F* xi;
+  int coop;          // cooperative refactorization allowed (uniform over the warp)
 
   __device__ __forceinline__ F k(int e) const { return kc[e * ks]; }
 
@@ -391,15 +395,245 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
   return bad;
 }
 
-// One EQP solve: backward pass (refactor stages t <= dirty, affine pass at
-// every stage), then forward pass (Sec. IV.B forward rollout) writing Us and X.
+// ---------------------------------------------------------------------------
+// Stage factorizations of a warp's agents (the refactorization part of the
+// Riccati backward recursion, Sec. IV.B), taken before an EQP pass.  Every
+// lane of the warp calls this together; `own` marks the lanes whose agent
+// needs stages dirty..0 refactored.  When few agents need it, the work of each
+// agent's stage is spread over a group of lanes (one lane per row of P): the
+// FP64 pipe costs the warp the same per instruction whatever the number of
+// active lanes, so a refactorization that serves a handful of agents is
+// otherwise paid at full price.  Each value is formed by the same operations,
+// in the same order, as in factor_stage, so both forms give identical bits.
+// ---------------------------------------------------------------------------
+template <int NX>
+struct CoopShape {
+  static constexpr int GS = NX <= 4 ? 4 : 8;      // lanes per agent group
+  static constexpr int NG = 32 / GS;               // groups per warp
+  static constexpr int MAXOWN = NX <= 4 ? 16 : 16; // largest owner count taken cooperatively
+};
+
+template <typename F>
+__device__ __forceinline__ F shfl_f(F v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// v[idx] for a lane-dependent idx without local-memory indexing.
+template <typename F, int N>
+__device__ __forceinline__ F pick(const F (&v)[N], int idx) {
+  F r = v[0];
+#pragma unroll
+  for (int c = 1; c < N; ++c)
+    if (idx == c) r = v[c];
+  return r;
+}
+
+template <typename F, int NX, int NU, int DP, bool DI>
+__device__ void refactor_sweep(const AgentCtx<F, NX, NU, DP>& A, bool own, int dirty, unsigned long long& nfact,
+                               int& bad_out) {
+  using CL = CacheLayout<NX, NU>;
+  using AC = AgentConst<NX, NU>;
+  constexpr unsigned FULL = 0xffffffffu;
+  const unsigned owners = __ballot_sync(FULL, own && dirty >= 0);
+  if (!owners) return;
+  const int lane = threadIdx.x & 31;
+  const bool mine = own && dirty >= 0;
+  if (mine && dirty >= A.T - 1) {
+    // P_T = Qbar_T
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int c = 0; c < NX; ++c) A.C(A.T, CL::P + r * NX + c) = (r == c) ? A.qbarT(r) : F(0);
+  }
+  if (mine) nfact += (unsigned long long)(dirty + 1);
+  __syncwarp();
+  const int n = __popc(owners);
+  constexpr bool coop_type = std::is_same<F, double>::value || std::is_same<F, float>::value;
+  if (!(DI && coop_type) || n > CoopShape<NX>::MAXOWN || !A.coop) {
+    // one lane per agent
+    const int maxd = __reduce_max_sync(FULL, mine ? dirty : -1);
+    __syncwarp();
+    for (int t = maxd; t >= 0; --t) {
+      if (mine && t <= dirty) {
+        const uint16_t mask = A.W(t);
+        F Pn[NX][NX], K[NU][NX], L[NU][NU];
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int c = 0; c < NX; ++c) Pn[r][c] = A.C(t + 1, CL::P + r * NX + c);
+        auto put = [&](int r, int c, F v) {
+          A.C(t, CL::P + r * NX + c) = v;
+          if (c != r) A.C(t, CL::P + c * NX + r) = v;
+        };
+        bad_out |= factor_stage<F, NX, NU, DI>(*A.M, Pn, mask, A.kc + AC::RB * A.ks,
+                                               t >= 1 ? A.kc + AC::QB * A.ks : nullptr, A.ks, put, K, L);
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+#pragma unroll
+          for (int c = 0; c < NX; ++c) A.C(t, CL::K + a * NX + c) = K[a][c];
+#pragma unroll
+          for (int b = 0; b <= a; ++b) A.C(t, CL::L + a * NU + b) = L[a][b];
+        }
+        A.CM(t) = mask;
+      }
+    }
+    __syncwarp();
+    return;
+  }
+  if constexpr (DI && coop_type) {
+    constexpr int GS = CoopShape<NX>::GS, NG = CoopShape<NX>::NG, H = NX / 2;
+    static_assert(NU == H, "double integrator: one input per position axis");
+    const Model<F, NX, NU>& Mo = *A.M;
+    const F dt = Mo.A[0][H], b1 = Mo.B[0][0], b2 = Mo.B[H][0];
+    const int g = lane / GS, r = lane % GS, gbase = g * GS;
+    const int rr = r < NX ? r : NX - 1;  // row of this lane (lanes past NX mirror the last row, never store)
+    int gbad = 0;
+    unsigned rem = owners;
+    while (rem) {
+      // the next NG owners, in lane order; group g takes the g-th of them
+      unsigned chunk = 0, m = rem;
+      for (int k = 0; k < NG && m; ++k) {
+        chunk |= m & (0u - m);
+        m &= m - 1;
+      }
+      rem &= ~chunk;
+      int olane = -1;
+      {
+        unsigned c2 = chunk;
+        for (int k = 0; k < g && c2; ++k) c2 &= c2 - 1;
+        if (c2) olane = __ffs(c2) - 1;
+      }
+      const int src = olane >= 0 ? olane : lane;
+      F* const ocache = (F*)__shfl_sync(FULL, (unsigned long long)A.cache, src);
+      uint16_t* const oW = (uint16_t*)__shfl_sync(FULL, (unsigned long long)A.Wm, src);
+      uint16_t* const oC = (uint16_t*)__shfl_sync(FULL, (unsigned long long)A.Cm, src);
+      const F* const okc = (const F*)__shfl_sync(FULL, (unsigned long long)A.kc, src);
+      const int oks = __shfl_sync(FULL, A.ks, src);
+      const int oN = __shfl_sync(FULL, A.N, src);
+      const int oi = __shfl_sync(FULL, A.i, src);
+      const int od = __shfl_sync(FULL, mine ? dirty : -1, src);
+      const bool gact = olane >= 0;
+      const int maxd = __reduce_max_sync(FULL, gact ? od : -1);
+      auto OC = [&](int t, int e) -> F& { return ocache[((size_t)t * CL::E + e) * oN + oi]; };
+      for (int t = maxd; t >= 0; --t) {
+        const bool act = gact && t <= od;
+        const bool row = act && r < NX;
+        const uint16_t mask = act ? oW[(size_t)t * oN + oi] : (uint16_t)0;
+        F Pr[NX];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) Pr[c] = act ? OC(t + 1, CL::P + rr * NX + c) : F(0);
+        F PAr[NX], PBr[NU];
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+          PAr[c] = Pr[c];
+          PAr[H + c] = fma(Pr[H + c], F(1), Pr[c] * dt);
+          PBr[c] = fma(Pr[H + c], b2, Pr[c] * b1);
+        }
+        // rows H + a of PA and PB for the lanes a < NU
+        const int shi = gbase + (r < NU ? r + H : rr);
+        F PAh[NX], PBh[NU];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) PAh[c] = shfl_f(PAr[c], shi);
+#pragma unroll
+        for (int c = 0; c < NU; ++c) PBh[c] = shfl_f(PBr[c], shi);
+        // row ra = min(r, NU - 1) of S and of M = B'P A (fixed rows/cols replaced)
+        const int ra = r < NU ? r : NU - 1;
+        const bool fa = (mask >> ra) & 0x101;
+        F Srow[NU], Mrow[NX];
+#pragma unroll
+        for (int b = 0; b < NU; ++b) {
+          const bool fb = (mask >> b) & 0x101;
+          F acc = (ra == b) ? (act ? okc[(AC::RB + ra) * oks] : F(1)) : F(0);
+          acc = fma(b1, PBr[b], acc);
+          acc = fma(b2, PBh[b], acc);
+          Srow[b] = (fa || fb) ? F(ra == b ? 1 : 0) : acc;
+        }
+#pragma unroll
+        for (int c = 0; c < NX; ++c) {
+          F acc = 0;
+          acc = fma(b1, PAr[c], acc);
+          acc = fma(b2, PAh[c], acc);
+          Mrow[c] = fa ? F(0) : acc;
+        }
+        // S, M on every lane of the group; S^{-1}; column rr of K
+        F S[NU][NU], Mm[NU][NX], Si[NU][NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+#pragma unroll
+          for (int b = 0; b < NU; ++b) S[a][b] = shfl_f(Srow[b], gbase + a);
+#pragma unroll
+          for (int c = 0; c < NX; ++c) Mm[a][c] = shfl_f(Mrow[c], gbase + a);
+        }
+        const int sbad = sym_inverse<F, NU>(S, Si);
+        if (act && r == 0) gbad |= sbad;
+        F kcol[NU];
+        {
+          F mc[NU];
+#pragma unroll
+          for (int b = 0; b < NU; ++b) mc[b] = pick<F, NX>(Mm[b], rr);
+          neg_sinv<F, NU>(Si, mc, kcol);
+        }
+        if (row) {
+#pragma unroll
+          for (int a = 0; a < NU; ++a) OC(t, CL::K + a * NX + rr) = kcol[a];
+        }
+        if (act && r == 0) {
+#pragma unroll
+          for (int a = 0; a < NU; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) OC(t, CL::L + a * NU + b) = Si[a][b];
+          oC[(size_t)t * oN + oi] = mask;
+        }
+        if (t >= 1) {
+          // P_t row rr: Qbar_t + A'(P A) + M'K, entries c >= rr
+          F K[NU][NX], PAl[NX];
+#pragma unroll
+          for (int c = 0; c < NX; ++c)
+#pragma unroll
+            for (int a = 0; a < NU; ++a) K[a][c] = shfl_f(kcol[a], gbase + c);
+          const int slo = gbase + (rr >= H ? rr - H : rr);
+#pragma unroll
+          for (int c = 0; c < NX; ++c) PAl[c] = shfl_f(PAr[c], slo);
+          const F qd = act ? okc[(AC::QB + rr) * oks] : F(0);
+          F mr[NU];
+#pragma unroll
+          for (int k = 0; k < NU; ++k) mr[k] = pick<F, NX>(Mm[k], rr);
+#pragma unroll
+          for (int c = 0; c < NX; ++c) {
+            if (c < rr) continue;
+            F acc = (rr == c) ? qd : F(0);
+            if (rr < H) {
+              acc = acc + PAr[c];
+            } else {
+              acc = fma(dt, PAl[c], acc);
+              acc = acc + PAr[c];
+            }
+#pragma unroll
+            for (int k = 0; k < NU; ++k) acc = fma(mr[k], K[k][c], acc);
+            if (row) {
+              OC(t, CL::P + rr * NX + c) = acc;
+              if (c != rr) OC(t, CL::P + c * NX + rr) = acc;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      // each owner of the chunk takes its group's status
+      const int gi = __popc(chunk & ((1u << lane) - 1u));
+      const int b = __shfl_sync(FULL, gbad, (mine && ((chunk >> lane) & 1u) ? gi : 0) * GS);
+      if (mine && ((chunk >> lane) & 1u)) bad_out |= b;
+      gbad = 0;
+    }
+  }
+}
+
+// One EQP solve with the cached stage factors (refactor_sweep brings them up to
+// date first): backward affine pass, then forward pass (Sec. IV.B forward rollout) writing Us and X.
 // The forward pass also scans the working-set multipliers
 // mu = +-(Rbar u + B' lambda_{t+1}) with the costate lambda_{t+1} =
 // P_{t+1} x_{t+1} + p_{t+1} (Sec. IV.B dual recovery), evaluated only at stages
 // that hold fixed inputs, and flags free inputs that left the box (integer
 // keys); the exact ratio test runs only when such an input exists.
 template <typename F, int NX, int NU, int DP, bool DI>
-__device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, unsigned long long& nfact) {
+__device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
   constexpr int H = NX / 2;
   using CL = CacheLayout<NX, NU>;
   const Model<F, NX, NU>& Mo = *A.M;
@@ -410,26 +644,18 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
   F pn[NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r) pn[r] = A.q(T, r);
-  if (dirty >= T - 1) {
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int c = 0; c < NX; ++c) A.C(T, CL::P + r * NX + c) = (r == c) ? A.qbarT(r) : F(0);
-  }
 #pragma unroll
   for (int r = 0; r < NX; ++r) A.C(T, CL::p + r) = pn[r];
 
   // the mask, cached gains and h of the next stage are loaded one stage ahead
   uint16_t mask_n = A.W(T - 1);
   F Kn[NU][NX], Ln[NU][NU], hn[DP];
-  if (T - 1 > dirty) {
 #pragma unroll
-    for (int a = 0; a < NU; ++a) {
+  for (int a = 0; a < NU; ++a) {
 #pragma unroll
-      for (int c = 0; c < NX; ++c) Kn[a][c] = A.C(T - 1, CL::K + a * NX + c);
+    for (int c = 0; c < NX; ++c) Kn[a][c] = A.C(T - 1, CL::K + a * NX + c);
 #pragma unroll
-      for (int b = 0; b < NU; ++b) Ln[a][b] = A.C(T - 1, CL::L + (b <= a ? a * NU + b : b * NU + a));
-    }
+    for (int b = 0; b < NU; ++b) Ln[a][b] = A.C(T - 1, CL::L + (b <= a ? a * NU + b : b * NU + a));
   }
 #pragma unroll
   for (int r = 0; r < DP; ++r) hn[r] = (T - 1 >= 1) ? A.hv(T - 1, r) : F(0);
@@ -438,47 +664,21 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A, int dirty, uns
     F K[NU][NX], L[NU][NU], ht[DP];
 #pragma unroll
     for (int r = 0; r < DP; ++r) ht[r] = hn[r];
-    const bool refac = t <= dirty;
-    if (refac) {
-      F Pn[NX][NX];
 #pragma unroll
-      for (int r = 0; r < NX; ++r)
+    for (int a = 0; a < NU; ++a) {
 #pragma unroll
-        for (int c = 0; c < NX; ++c) Pn[r][c] = A.C(t + 1, CL::P + r * NX + c);
-      auto put = [&](int r, int c, F v) {
-        A.C(t, CL::P + r * NX + c) = v;
-        if (c != r) A.C(t, CL::P + c * NX + r) = v;
-      };
-      o.bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, A.kc + AgentConst<NX, NU>::RB * A.ks,
-                                           t >= 1 ? A.kc + AgentConst<NX, NU>::QB * A.ks : nullptr, A.ks, put, K, L);
-      ++nfact;
+      for (int c = 0; c < NX; ++c) K[a][c] = Kn[a][c];
 #pragma unroll
-      for (int a = 0; a < NU; ++a) {
-#pragma unroll
-        for (int c = 0; c < NX; ++c) A.C(t, CL::K + a * NX + c) = K[a][c];
-#pragma unroll
-        for (int b = 0; b <= a; ++b) A.C(t, CL::L + a * NU + b) = L[a][b];
-      }
-      A.CM(t) = mask;
-    } else {
-#pragma unroll
-      for (int a = 0; a < NU; ++a) {
-#pragma unroll
-        for (int c = 0; c < NX; ++c) K[a][c] = Kn[a][c];
-#pragma unroll
-        for (int b = 0; b < NU; ++b) L[a][b] = Ln[a][b];
-      }
+      for (int b = 0; b < NU; ++b) L[a][b] = Ln[a][b];
     }
     if (t >= 1) {
       mask_n = A.W(t - 1);
-      if (t - 1 > dirty) {
 #pragma unroll
-        for (int a = 0; a < NU; ++a) {
+      for (int a = 0; a < NU; ++a) {
 #pragma unroll
-          for (int c = 0; c < NX; ++c) Kn[a][c] = A.C(t - 1, CL::K + a * NX + c);
+        for (int c = 0; c < NX; ++c) Kn[a][c] = A.C(t - 1, CL::K + a * NX + c);
 #pragma unroll
-          for (int b = 0; b < NU; ++b) Ln[a][b] = A.C(t - 1, CL::L + (b <= a ? a * NU + b : b * NU + a));
-        }
+        for (int b = 0; b < NU; ++b) Ln[a][b] = A.C(t - 1, CL::L + (b <= a ? a * NU + b : b * NU + a));
       }
 #pragma unroll
       for (int r = 0; r < DP; ++r) hn[r] = (t - 1 >= 1) ? A.hv(t - 1, r) : F(0);
@@ -697,69 +897,82 @@ __device__ void ratio_test(const AgentCtx<F, NX, NU, DP>& A, EqpScan<F>& o) {
 // method (Nocedal & Wright Alg. 16.3) over Riccati EQP solves.
 // start_kind: QP_COLD (u = clip(0), W empty), QP_LQR (clipped affine-LQR warm
 // start, Sec. IV.B-C) or QP_GIVEN (hot start from the stored u, W and factors).
+// All 32 lanes of the warp call this together; a lane with has = false owns no
+// agent and only helps the others' refactorizations.  The lanes step through
+// their active-set iterations in rounds: in each round every lane that needs
+// an EQP solve takes it in the same pass, since a pass costs the warp the same
+// whatever number of lanes it serves.  Each lane's own sequence of working
+// sets, steps and multiplier tests is unchanged.
 // Returns ST_CONVERGED, ST_QP_FAIL or ST_NUMERIC.
 template <typename F, int NX, int NU, int DP, bool DI>
-__device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, int start_kind, int as_max, F eps_rel,
+__device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, bool has, int start_kind, int as_max, F eps_rel,
                              unsigned long long& neqp, unsigned long long& nfact) {
-  const int T = A.T;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int T = has ? A.T : 0;
   const Model<F, NX, NU>& Mo = *A.M;
-  if (start_kind == QP_COLD) {
-    for (int t = 0; t < T; ++t) {
-      A.W(t) = 0;
-#pragma unroll
-      for (int a = 0; a < NU; ++a) {
-        F z = 0;
-        if (z < Mo.umin[a]) z = Mo.umin[a];
-        if (z > Mo.umax[a]) z = Mo.umax[a];
-        A.u(t, a) = z;
-      }
-    }
-  } else if (start_kind == QP_LQR) {
-    for (int t = 0; t < T; ++t) A.W(t) = 0;
-  }
-  // stages whose cached factors do not match the working set
+  int status = has ? -1 : ST_CONVERGED;  // -1: running
   int dirty = -1;
-  for (int t = 0; t < T; ++t)
-    if (A.CM(t) != A.W(t)) dirty = t;
-
-  if (start_kind == QP_LQR) {
-    EqpScan<F> o = eqp_solve<F, NX, NU, DP, DI>(A, dirty, nfact);
-    if (o.bad) return ST_NUMERIC;
-    dirty = -1;
-    bool clipped = false;
-    for (int t = 0; t < T; ++t) {
-      uint16_t m = 0;
+  if (has) {
+    if (start_kind == QP_COLD) {
+      for (int t = 0; t < T; ++t) {
+        A.W(t) = 0;
 #pragma unroll
-      for (int a = 0; a < NU; ++a) {
-        F v = A.us(t, a);
-        if (v < Mo.umin[a]) { v = Mo.umin[a]; m |= (uint16_t)(1u << a); }
-        else if (v > Mo.umax[a]) { v = Mo.umax[a]; m |= (uint16_t)(0x100u << a); }
-        A.u(t, a) = v;
+        for (int a = 0; a < NU; ++a) {
+          F z = 0;
+          if (z < Mo.umin[a]) z = Mo.umin[a];
+          if (z > Mo.umax[a]) z = Mo.umax[a];
+          A.u(t, a) = z;
+        }
       }
-      if (m) { A.W(t) = m; clipped = true; dirty = t; }
+    } else if (start_kind == QP_LQR) {
+      for (int t = 0; t < T; ++t) A.W(t) = 0;
     }
-    if (!clipped) return ST_CONVERGED;  // the LQR solution is the QP solution
+    // stages whose cached factors do not match the working set
+    for (int t = 0; t < T; ++t)
+      if (A.CM(t) != A.W(t)) dirty = t;
   }
 
-  // The lanes of the warp that reach this point step through their
-  // active-set iterations in rounds: in each round every lane that needs an
-  // EQP solve takes it in the same pass, since a pass costs the warp the same
-  // whatever number of lanes it serves.  Each lane's own sequence of working
-  // sets, steps and multiplier tests is unchanged.
-  const unsigned part = __activemask();
-  int status = -1;  // running
+  const bool lqr = has && start_kind == QP_LQR;
+  if (__any_sync(FULL, lqr)) {
+    int bad = 0;
+    refactor_sweep<F, NX, NU, DP, DI>(A, lqr, dirty, nfact, bad);
+    if (lqr) {
+      const EqpScan<F> o = eqp_solve<F, NX, NU, DP, DI>(A);
+      if (bad || o.bad) {
+        status = ST_NUMERIC;
+      } else {
+        dirty = -1;
+        bool clipped = false;
+        for (int t = 0; t < T; ++t) {
+          uint16_t m = 0;
+#pragma unroll
+          for (int a = 0; a < NU; ++a) {
+            F v = A.us(t, a);
+            if (v < Mo.umin[a]) { v = Mo.umin[a]; m |= (uint16_t)(1u << a); }
+            else if (v > Mo.umax[a]) { v = Mo.umax[a]; m |= (uint16_t)(0x100u << a); }
+            A.u(t, a) = v;
+          }
+          if (m) { A.W(t) = m; clipped = true; dirty = t; }
+        }
+        if (!clipped) status = ST_CONVERGED;  // the LQR solution is the QP solution
+      }
+    }
+  }
+
   for (;;) {
     bool go = false;
     if (status < 0) {
       if (as_max <= 0) status = ST_QP_FAIL;
       else go = true;
     }
-    if (!__any_sync(part, go)) break;
+    if (!__any_sync(FULL, go)) break;
+    int bad = 0;
+    refactor_sweep<F, NX, NU, DP, DI>(A, go, dirty, nfact, bad);
     if (go) {
       --as_max;
       ++neqp;
-      EqpScan<F> o = eqp_solve<F, NX, NU, DP, DI>(A, dirty, nfact);
-      if (o.bad) {
+      EqpScan<F> o = eqp_solve<F, NX, NU, DP, DI>(A);
+      if (bad || o.bad) {
         status = ST_NUMERIC;
       } else {
         dirty = -1;
@@ -852,6 +1065,7 @@ __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, c
   A.h = D.h + s.as_off * DP;
   A.kc = kc;
   A.ks = ks;
+  A.coop = D.coop;
   const int64_t ag = s.agent_off + i;
   A.qf = D.Qfd + ag * NX;
   A.xr = D.x_ref + ag * NX;
@@ -869,6 +1083,30 @@ __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, c
   return A;
 }
 
+// Context of a lane that owns no agent in this x-update (it only helps).
+template <typename F, int NX, int NU, int DP>
+__device__ __forceinline__ AgentCtx<F, NX, NU, DP> idle_agent(const Model<F, NX, NU>& M, F* kc, int ks, int coop) {
+  AgentCtx<F, NX, NU, DP> A;
+  A.M = &M;
+  A.N = 1;
+  A.T = 0;
+  A.i = 0;
+  A.cache = nullptr;
+  A.Wm = nullptr;
+  A.Cm = nullptr;
+  A.U = nullptr;
+  A.Us = nullptr;
+  A.Xo = nullptr;
+  A.h = nullptr;
+  A.kc = kc;
+  A.ks = ks;
+  A.qf = nullptr;
+  A.xr = nullptr;
+  A.xi = nullptr;
+  A.coop = coop;
+  return A;
+}
+
 template <typename F>
 __device__ __forceinline__ int start_kind_of(const Dev<F>& D, int k) {
   if (D.start_mode == START_COLD) return QP_COLD;
@@ -876,18 +1114,26 @@ __device__ __forceinline__ int start_kind_of(const Dev<F>& D, int k) {
   return QP_GIVEN;
 }
 
+// x-update of agents i0, i0 + stride, ... of scenario s (none when in_scen is
+// false).  Every lane of the warp calls this; all lanes take the same number
+// of rounds, so that xupdate_agent always runs warp-wide.
 template <typename F, int NX, int NU, int DP, bool DI>
-__device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, int k,
+__device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, bool in_scen, int k,
                              int lvl_out, int i0, int stride, unsigned long long& neqp,
                              unsigned long long& nfact, F* kcs) {
   const int kind = start_kind_of(D, k);
   const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
   const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
+  const int mine = (in_scen && i0 < s.N) ? (s.N - i0 + stride - 1) / stride : 0;
+  const int rounds = __reduce_max_sync(0xffffffffu, mine);
   int st = ST_CONVERGED;
-  for (int i = i0; i < s.N; i += stride) {
-    AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, i, lvl_out, kcs + threadIdx.x, blockDim.x);
-    const int r = xupdate_agent<F, NX, NU, DP, DI>(A, kind, as_max, eps, neqp, nfact);
-    if (r > st) st = r;
+  for (int r = 0; r < rounds; ++r) {
+    const bool has = r < mine;
+    const AgentCtx<F, NX, NU, DP> A =
+        has ? make_agent<F, NX, NU, DP>(D, M, s, i0 + r * stride, lvl_out, kcs + threadIdx.x, blockDim.x)
+            : idle_agent<F, NX, NU, DP>(M, kcs + threadIdx.x, blockDim.x, D.coop);
+    const int res = xupdate_agent<F, NX, NU, DP, DI>(A, has, kind, as_max, eps, neqp, nfact);
+    if (has && res > st) st = res;
   }
   return st;
 }
@@ -1182,7 +1428,7 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
   unsigned long long neqp = 0, nfact = 0;
   for (int k = 0; k < D.max_iter; ++k) {
     const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
-    const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, xl ^ 1, tid, nt, neqp, nfact, kcs);
+    const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, true, k, xl ^ 1, tid, nt, neqp, nfact, kcs);
     if (st) atomicMax(&cs.flag, st);
     __syncthreads();
     iters = k + 1;
@@ -1315,14 +1561,16 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
   for (int k = 0; k < D.max_iter; ++k) {
     const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
     const bool last = (k + 1 == D.max_iter);
-    // x-update
-    if (my_m >= 0 && gs.active[my_m]) {
-      const ScenMeta& s = gs.meta[my_m];
-      AgentCtx<F, NX, NU, DP> A = make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1, kcs + tid, nt);
+    // x-update (every lane of the warp takes part; lanes without an active agent help)
+    {
+      const bool has = my_m >= 0 && gs.active[my_m] != 0;
+      const ScenMeta& s = gs.meta[has ? my_m : 0];
+      const AgentCtx<F, NX, NU, DP> A = has ? make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1, kcs + tid, nt)
+                                            : idle_agent<F, NX, NU, DP>(M, kcs + tid, nt, D.coop);
       const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
       const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
-      const int st = xupdate_agent<F, NX, NU, DP, DI>(A, start_kind_of(D, k), as_max, eps, neqp, nfact);
-      if (st) atomicMax(&gs.flag[my_m], st);
+      const int st = xupdate_agent<F, NX, NU, DP, DI>(A, has, start_kind_of(D, k), as_max, eps, neqp, nfact);
+      if (has && st) atomicMax(&gs.flag[my_m], st);
     }
     __syncthreads();
     if (tid < G && gs.active[tid] && gs.flag[tid]) {

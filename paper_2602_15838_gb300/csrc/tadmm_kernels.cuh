@@ -74,10 +74,9 @@ __global__ void __launch_bounds__(32) k_xupdate(Dev<F> D, int sc, int k, int lvl
   __syncthreads();
   const ScenMeta s = D.meta[sc];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.N) return;
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, lvl_out, i, s.N, neqp, nfact, kcs);
-  if (st) atomicMax(flag, st);
+  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, true, k, lvl_out, i, s.N, neqp, nfact, kcs);
+  if (st && i < s.N) atomicMax(flag, st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
 }
@@ -179,13 +178,15 @@ __global__ void __launch_bounds__(32) k_g_xupdate(Dev<F> D, GState G, const int3
   load_model<F, NX, NU>(M, D.model);
   __syncthreads();
   const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ga >= tot_agents) return;
-  const int sc = agent_scen[ga];
-  if (!G.active[sc]) return;
+  // every lane of the warp takes part in the x-update; lanes past the last
+  // agent or of a stopped scenario only help
+  const int sc = ga < tot_agents ? agent_scen[ga] : 0;
+  const bool in_scen = ga < tot_agents && G.active[sc];
   const ScenMeta s = D.meta[sc];
   const int i = (int)(ga - s.agent_off), k = G.iter[sc];
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, k, (k + 1) & 1, i, s.N, neqp, nfact, kcs);
+  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, in_scen, k, (k + 1) & 1, i, s.N, neqp, nfact, kcs);
+  if (!in_scen) return;
   if (st) atomicMax(&G.fail[sc], st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
@@ -424,6 +425,7 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.as_max = h->opt.as_max;
   D.eps_rel = h->opt.eps_rel;
   D.single_as_group = (h->opt.flags & (TADMM_FLAG_NO_GROUPING | TADMM_FLAG_NO_FUSED_PAIR_GATHER)) ? 0 : 1;
+  D.coop = (h->opt.flags & TADMM_FLAG_NO_COOP_REFACTOR) ? 0 : 1;
   return D;
 }
 
