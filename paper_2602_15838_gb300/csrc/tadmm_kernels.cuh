@@ -67,16 +67,19 @@ __global__ void k_init(Dev<F> D, int sc) {
 }
 
 template <typename F, int NX, int NU, int DP, bool DI>
-__global__ void __launch_bounds__(32) k_xupdate(Dev<F> D, int sc, int k, int lvl_out, int32_t* flag) {
+// One warp per CTA; lanes 0..apw-1 own agents blockIdx.x * apw + lane, the
+// other lanes help with their refactorizations.
+__global__ void __launch_bounds__(32) k_xupdate(Dev<F> D, int sc, int k, int lvl_out, int32_t* flag, int apw) {
   __shared__ Model<F, NX, NU> M;
   __shared__ F kcs[AgentConst<NX, NU>::KC * 32];
   load_model<F, NX, NU>(M, D.model);
   __syncthreads();
   const ScenMeta s = D.meta[sc];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool owns = (int)threadIdx.x < apw;
+  const int i = blockIdx.x * apw + threadIdx.x;
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, true, k, lvl_out, i, s.N, neqp, nfact, kcs);
-  if (st && i < s.N) atomicMax(flag, st);
+  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, owns, k, lvl_out, i, s.N, neqp, nfact, kcs);
+  if (st && owns && i < s.N) atomicMax(flag, st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
 }
@@ -172,16 +175,17 @@ __global__ void k_g_init(Dev<F> D, GState G) {
 
 template <typename F, int NX, int NU, int DP, bool DI>
 __global__ void __launch_bounds__(32) k_g_xupdate(Dev<F> D, GState G, const int32_t* __restrict__ agent_scen,
-                                                   int64_t tot_agents) {
+                                                   int64_t tot_agents, int apw) {
   __shared__ Model<F, NX, NU> M;
   __shared__ F kcs[AgentConst<NX, NU>::KC * 32];
   load_model<F, NX, NU>(M, D.model);
   __syncthreads();
-  const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // every lane of the warp takes part in the x-update; lanes past the last
-  // agent or of a stopped scenario only help
-  const int sc = ga < tot_agents ? agent_scen[ga] : 0;
-  const bool in_scen = ga < tot_agents && G.active[sc];
+  const int64_t ga = (int64_t)blockIdx.x * apw + threadIdx.x;
+  // every lane of the warp takes part in the x-update; lanes past apw, past
+  // the last agent or of a stopped scenario only help
+  const bool owns = (int)threadIdx.x < apw && ga < tot_agents;
+  const int sc = owns ? agent_scen[ga] : 0;
+  const bool in_scen = owns && G.active[sc];
   const ScenMeta s = D.meta[sc];
   const int i = (int)(ga - s.agent_off), k = G.iter[sc];
   unsigned long long neqp = 0, nfact = 0;
@@ -585,6 +589,17 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
   return cuda_check(cudaGraphLaunch(h->gexec, st), "graph launch");
 }
 
+// Agents per warp of the per-phase x-update kernels: 32 (one per lane) when
+// there are enough agents to give every SM a few warps; otherwise fewer, down
+// to one per lane group of the cooperative refactorization, so that a small
+// agent count is spread over more SMs and every owner can have a lane group.
+template <int NX>
+static int agents_per_warp(int64_t agents, int sm_count) {
+  int apw = 32;
+  while (apw > CoopShape<NX>::NG && (int64_t)apw * sm_count * 2 > agents) apw /= 2;
+  return apw;
+}
+
 template <typename F, int NX, int NU, int DP>
 int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, cudaStream_t st) {
   Dev<F> D = make_dev<F>(h);
@@ -595,6 +610,7 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
   for (int sc = 0; sc < h->n_scen; ++sc) {
     const ScenMeta& s = h->meta_h[sc];
     const int64_t PT = (int64_t)s.P * s.T, NT = (int64_t)s.N * s.T;
+    const int apw = agents_per_warp<NX>(s.N, h->sm_count);
     k_init<F, NX, NU, DP><<<grid_for(std::max(PT, NT), 256, 4096), 256, 0, st>>>(D, sc);
     ++launches;
     int xl = 0, status = ST_NOT_CONVERGED, iters = 0, tfin = 0;
@@ -607,9 +623,9 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
       cudaMemsetAsync(h->flag, 0, sizeof(int32_t), st);
       cudaMemsetAsync(h->red2, 0, 2 * sizeof(unsigned long long), st);
       if (h->di)
-        k_xupdate<F, NX, NU, DP, true><<<grid_for(s.N, 32), 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
+        k_xupdate<F, NX, NU, DP, true><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
       else
-        k_xupdate<F, NX, NU, DP, false><<<grid_for(s.N, 32), 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag);
+        k_xupdate<F, NX, NU, DP, false><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
       k_pair<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, xl, tk, tkp1, h->red2);
       launches += 2;
       cudaMemcpyAsync(hb, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
@@ -713,13 +729,14 @@ int Impl<F, NX, NU, DP>::solve_graph(tadmm_handle* h, double tol, int max_iter, 
       cudaGraphDestroy(g);
       return rc;
     }
-    const dim3 gx(grid_for(h->tot_agents, 32, 1 << 30));
+    const int gapw = agents_per_warp<NX>(h->tot_agents, h->sm_count);
+    const dim3 gx((unsigned)((h->tot_agents + gapw - 1) / gapw));
     const dim3 gp(grid_for(h->tot_pairs, 128, 1 << 30), tmax);
     const dim3 gg(h->n_gblk, tmax);
     if (h->di)
-      k_g_xupdate<F, NX, NU, DP, true><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+      k_g_xupdate<F, NX, NU, DP, true><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
     else
-      k_g_xupdate<F, NX, NU, DP, false><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents);
+      k_g_xupdate<F, NX, NU, DP, false><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
     if (h->tot_pairs > 0) k_g_pair<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);
     k_g_check1<F><<<grid_for(h->n_scen, 128), 128, 0, h->cap_stream>>>(D, G);
     if (h->tot_pairs > 0) k_g_dual<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);
