@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
         Pt[r][c] = v;
         Pt[c][r] = v;
       };
-      bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, rbar, t >= 1 ? qbar : nullptr, 1, put, K, L);
+      auto putB = [](int, int, F) {};
+      bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, rbar, t >= 1 ? qbar : nullptr, 1, put, putB, K, L);
 #pragma unroll
       for (int r = 0; r < NU; ++r) {
 #pragma unroll

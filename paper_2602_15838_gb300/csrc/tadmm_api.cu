@@ -41,7 +41,13 @@ using tadmm::set_error;
     return set_error(TADMM_EINVAL, "unsupported precision / dimensions");            \
   } while (0)
 
-static int cache_words(int nx, int nu) { return nx * nx + nu * nx + nu * nu + nu + nx; }
+// Words of the per-stage factor cache: the layout of the kernels (CacheLayout)
+// for the dispatched model sizes.
+static int cache_words(int nx, int nu) {
+  if (nx == 4 && nu == 2) return tadmm::CacheLayout<4, 2>::E;
+  if (nx == 6 && nu == 3) return tadmm::CacheLayout<6, 3>::E;
+  return nx * nx + nu * nx + nu * nu + nu + nx * nu + nu;
+}
 
 static bool finite_all(const double* p, int64_t n) {
   for (int64_t k = 0; k < n; ++k)

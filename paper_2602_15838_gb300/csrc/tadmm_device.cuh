@@ -89,14 +89,20 @@ struct Dev {
   int32_t coop;              // 1: refactorizations may be spread over lane groups
 };
 
+// Per-stage factor cache of one agent (stage t):
+//   P   P_t (NX x NX)             K   feedback K_t (NU x NX)
+//   L   S_t^{-1}, lower triangle  k   feedforward k_t (NU)
+//   PB  P_{t+1} B (NX x NU)       bp  B' p_{t+1} (NU), written by the backward
+//                                     pass where the stage holds fixed inputs
 template <int NX, int NU>
 struct CacheLayout {
   static constexpr int P = 0;
   static constexpr int K = NX * NX;
   static constexpr int L = K + NU * NX;   // S^{-1}, lower triangle (row-major NU x NU slots)
   static constexpr int k = L + NU * NU;
-  static constexpr int p = k + NU;
-  static constexpr int E = p + NX;
+  static constexpr int PB = k + NU;
+  static constexpr int bp = PB + NX * NU;
+  static constexpr int E = bp + NU;
 };
 
 template <typename F, int NX, int NU>
@@ -293,11 +299,12 @@ __device__ __forceinline__ void neg_sinv(const F (&Si)[NU][NU], const F (&v)[NU]
   }
 }
 
-// P_t entry (r, c), r <= c, is handed to put(r, c, value) as soon as it is formed.
-template <typename F, int NX, int NU, bool DI, class PutP>
+// P_t entry (r, c), r <= c, is handed to put(r, c, value) as soon as it is
+// formed, and entry (r, a) of P_{t+1} B to putB(r, a, value).
+template <typename F, int NX, int NU, bool DI, class PutP, class PutB>
 __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F (&Pn)[NX][NX],
                                             uint16_t mask, const F* rbar, const F* qdiag, int ks,
-                                            PutP&& put, F (&K)[NU][NX], F (&L)[NU][NU]) {
+                                            PutP&& put, PutB&& putB, F (&K)[NU][NX], F (&L)[NU][NU]) {
   constexpr int H = NX / 2;
   F PA[NX][NX], PB[NX][NU];
 #pragma unroll
@@ -327,6 +334,10 @@ __device__ __forceinline__ int factor_stage(const Model<F, NX, NU>& Mo, const F 
       }
     }
   }
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int c = 0; c < NU; ++c) putB(r, c, PB[r][c]);
   F S[NU][NU], Mm[NU][NX];
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
@@ -463,8 +474,9 @@ __device__ void refactor_sweep(const AgentCtx<F, NX, NU, DP>& A, bool own, int d
           A.C(t, CL::P + r * NX + c) = v;
           if (c != r) A.C(t, CL::P + c * NX + r) = v;
         };
+        auto putB = [&](int r, int a, F v) { A.C(t, CL::PB + r * NU + a) = v; };
         bad_out |= factor_stage<F, NX, NU, DI>(*A.M, Pn, mask, A.kc + AC::RB * A.ks,
-                                               t >= 1 ? A.kc + AC::QB * A.ks : nullptr, A.ks, put, K, L);
+                                               t >= 1 ? A.kc + AC::QB * A.ks : nullptr, A.ks, put, putB, K, L);
 #pragma unroll
         for (int a = 0; a < NU; ++a) {
 #pragma unroll
@@ -574,6 +586,8 @@ __device__ void refactor_sweep(const AgentCtx<F, NX, NU, DP>& A, bool own, int d
         if (row) {
 #pragma unroll
           for (int a = 0; a < NU; ++a) OC(t, CL::K + a * NX + rr) = kcol[a];
+#pragma unroll
+          for (int a = 0; a < NU; ++a) OC(t, CL::PB + rr * NU + a) = PBr[a];
         }
         if (act && r == 0) {
 #pragma unroll
@@ -644,8 +658,6 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
   F pn[NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r) pn[r] = A.q(T, r);
-#pragma unroll
-  for (int r = 0; r < NX; ++r) A.C(T, CL::p + r) = pn[r];
 
   // the mask, cached gains and h of the next stage are loaded one stage ahead
   uint16_t mask_n = A.W(T - 1);
@@ -683,37 +695,31 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
 #pragma unroll
       for (int r = 0; r < DP; ++r) hn[r] = (t - 1 >= 1) ? A.hv(t - 1, r) : F(0);
     }
-    // affine pass: P_{t+1} c + p_{t+1} with c = B_fixed u_fixed
+    // affine pass: P_{t+1} c + p_{t+1} with c = B_fixed u_fixed, i.e.
+    // p_{t+1} + sum over the fixed inputs a of (P_{t+1} B)[:, a] u_a
     F Pcp[NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r) Pcp[r] = pn[r];
     if (mask) {
-      F cv[NX];
-      if constexpr (DI) {
 #pragma unroll
-        for (int c = 0; c < H; ++c) {
-          const F ub = (mask & (1u << c)) ? Mo.umin[c] : ((mask & (0x100u << c)) ? Mo.umax[c] : F(0));
-          cv[c] = Mo.B[0][0] * ub;
-          cv[H + c] = Mo.B[H][0] * ub;
-        }
-      } else {
+      for (int a = 0; a < NU; ++a) {
+        if (!(mask & (0x101u << a))) continue;
+        const F ub = (mask & (1u << a)) ? Mo.umin[a] : Mo.umax[a];
 #pragma unroll
-        for (int r = 0; r < NX; ++r) {
-          F acc = 0;
-#pragma unroll
-          for (int c = 0; c < NU; ++c) {
-            if (mask & (1u << c)) acc = fma(Mo.B[r][c], Mo.umin[c], acc);
-            else if (mask & (0x100u << c)) acc = fma(Mo.B[r][c], Mo.umax[c], acc);
-          }
-          cv[r] = acc;
-        }
+        for (int r = 0; r < NX; ++r) Pcp[r] = fma(A.C(t, CL::PB + r * NU + a), ub, Pcp[r]);
       }
+      // B' p_{t+1} for the multipliers of the forward pass
 #pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        F acc = Pcp[r];
+      for (int a = 0; a < NU; ++a) {
+        F acc = 0;
+        if constexpr (DI) {
+          acc = fma(Mo.B[0][0], pn[a], acc);
+          acc = fma(Mo.B[H][0], pn[H + a], acc);
+        } else {
 #pragma unroll
-        for (int c = 0; c < NX; ++c) acc = fma(A.C(t + 1, CL::P + r * NX + c), cv[c], acc);
-        Pcp[r] = acc;
+          for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], pn[r], acc);
+        }
+        A.C(t, CL::bp + a) = acc;
       }
     }
     F sv[NU], kk[NU];
@@ -749,7 +755,6 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
         }
 #pragma unroll
         for (int k = 0; k < NU; ++k) acc = fma(K[k][r], sv[k], acc);
-        A.C(t, CL::p + r) = acc;
         pn[r] = acc;
       }
     }
@@ -828,25 +833,14 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
       }
     }
     if (mask) {
-      F lam[NX];
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        F acc = A.C(t + 1, CL::p + r);
-#pragma unroll
-        for (int c = 0; c < NX; ++c) acc = fma(A.C(t + 1, CL::P + r * NX + c), xn[c], acc);
-        lam[r] = acc;
-      }
 #pragma unroll
       for (int a = 0; a < NU; ++a) {
         if (!(mask & (0x101u << a))) continue;
-        F g = A.k(AgentConst<NX, NU>::RB + a) * uv[a];
-        if constexpr (DI) {
-          g = fma(Mo.B[0][0], lam[a], g);
-          g = fma(Mo.B[H][0], lam[H + a], g);
-        } else {
+        // Rbar u + B' lambda_{t+1} with B' lambda_{t+1} = (P_{t+1} B)' x_{t+1} + B' p_{t+1}
+        F g = A.C(t, CL::bp + a);
 #pragma unroll
-          for (int r = 0; r < NX; ++r) g = fma(Mo.B[r][a], lam[r], g);
-        }
+        for (int c = 0; c < NX; ++c) g = fma(A.C(t, CL::PB + c * NU + a), xn[c], g);
+        g = fma(A.k(AgentConst<NX, NU>::RB + a), uv[a], g);
         const F mu = (mask & (1u << a)) ? g : -g;
         const F am = fabs_(mu);
         if (am > o.scale) o.scale = am;
