@@ -105,6 +105,8 @@ struct CacheLayout {
   static constexpr int E = bp + NU;
 };
 
+constexpr int kStageBatch = 4;  // stages whose operands the active-set bookkeeping loads ahead
+
 template <typename F, int NX, int NU>
 struct Model {
   F A[NX][NX];
@@ -868,13 +870,28 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
 template <typename F, int NX, int NU, int DP>
 __device__ void ratio_test(const AgentCtx<F, NX, NU, DP>& A, EqpScan<F>& o) {
   const Model<F, NX, NU>& Mo = *A.M;
-  for (int t = 0; t < A.T; ++t) {
-    const uint16_t mask = A.W(t);
+  for (int t0 = 0; t0 < A.T; t0 += kStageBatch) {
+    // the operands of kStageBatch stages are loaded before they are used
+    uint16_t mk[kStageBatch];
+    F cuv[kStageBatch][NU], suv[kStageBatch][NU];
+#pragma unroll
+    for (int j = 0; j < kStageBatch; ++j) {
+      const int t = t0 + j;
+      mk[j] = t < A.T ? A.W(t) : (uint16_t)0xFFFF;
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        cuv[j][a] = t < A.T ? A.u(t, a) : F(0);
+        suv[j][a] = t < A.T ? A.us(t, a) : F(0);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kStageBatch; ++j)
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
-      if (mask & (0x101u << a)) continue;
-      const F cu = A.u(t, a);
-      const F p = A.us(t, a) - cu;
+      const int t = t0 + j;
+      if (mk[j] & (0x101u << a)) continue;
+      const F cu = cuv[j][a];
+      const F p = suv[j][a] - cu;
       F num = 0, den = 0;
       int side = 0;
       if (p < F(0)) { num = cu - Mo.umin[a]; den = -p; side = 1; }
@@ -884,6 +901,30 @@ __device__ void ratio_test(const AgentCtx<F, NX, NU, DP>& A, EqpScan<F>& o) {
         if (num * o.aden < o.anum * den) { o.anum = num; o.aden = den; o.blk = t * NU + a; o.bside = side; }
       }
     }
+  }
+}
+
+// u <- u + alpha (us - u) (alpha < 1) or u <- us (alpha = 1 passed as full),
+// kStageBatch stages at a time with the loads ahead of the stores.
+template <typename F, int NX, int NU, int DP>
+__device__ __forceinline__ void step_inputs(const AgentCtx<F, NX, NU, DP>& A, int T, bool full, F alpha) {
+  for (int t0 = 0; t0 < T; t0 += kStageBatch) {
+    F cuv[kStageBatch][NU], suv[kStageBatch][NU];
+#pragma unroll
+    for (int j = 0; j < kStageBatch; ++j)
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        const int t = t0 + j;
+        cuv[j][a] = (t < T && !full) ? A.u(t, a) : F(0);
+        suv[j][a] = t < T ? A.us(t, a) : F(0);
+      }
+#pragma unroll
+    for (int j = 0; j < kStageBatch; ++j)
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        const int t = t0 + j;
+        if (t < T) A.u(t, a) = full ? suv[j][a] : fma(alpha, suv[j][a] - cuv[j][a], cuv[j][a]);
+      }
   }
 }
 
@@ -922,8 +963,17 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, bool has, int sta
       for (int t = 0; t < T; ++t) A.W(t) = 0;
     }
     // stages whose cached factors do not match the working set
-    for (int t = 0; t < T; ++t)
-      if (A.CM(t) != A.W(t)) dirty = t;
+    for (int t0 = 0; t0 < T; t0 += kStageBatch) {
+      uint16_t cm[kStageBatch], w[kStageBatch];
+#pragma unroll
+      for (int j = 0; j < kStageBatch; ++j) {
+        cm[j] = t0 + j < T ? A.CM(t0 + j) : (uint16_t)0;
+        w[j] = t0 + j < T ? A.W(t0 + j) : (uint16_t)0;
+      }
+#pragma unroll
+      for (int j = 0; j < kStageBatch; ++j)
+        if (cm[j] != w[j]) dirty = t0 + j;
+    }
   }
 
   const bool lqr = has && start_kind == QP_LQR;
@@ -973,20 +1023,13 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, bool has, int sta
         if (o.out) ratio_test<F, NX, NU, DP>(A, o);
         if (o.blk >= 0) {
           const F alpha = o.anum / o.aden;
-          for (int t = 0; t < T; ++t)
-#pragma unroll
-            for (int a = 0; a < NU; ++a) {
-              const F cu = A.u(t, a);
-              A.u(t, a) = fma(alpha, A.us(t, a) - cu, cu);
-            }
+          step_inputs<F, NX, NU, DP>(A, T, false, alpha);
           const int bt = o.blk / NU, ba = o.blk - bt * NU;
           A.u(bt, ba) = (o.bside == 1) ? Mo.umin[ba] : Mo.umax[ba];
           A.W(bt) = (uint16_t)(A.W(bt) | (o.bside == 1 ? (1u << ba) : (0x100u << ba)));
           dirty = bt;
         } else {
-          for (int t = 0; t < T; ++t)
-#pragma unroll
-            for (int a = 0; a < NU; ++a) A.u(t, a) = A.us(t, a);
+          step_inputs<F, NX, NU, DP>(A, T, true, F(1));
           if (o.widx >= 0 && o.worst < -eps_rel * o.scale) {
             const int bt = o.widx / NU, ba = o.widx - bt * NU;
             A.W(bt) = (uint16_t)(A.W(bt) & ~(0x101u << ba));
@@ -1152,18 +1195,18 @@ __device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tk, i
     const int pair = (int)(q - (int64_t)tm1 * P);
     const int pk = pr[pair];
     const int i = pk & 0xFFFF, j = pk >> 16;
-    F sdot = 0;
+    F g = d;  // d - a'(p_i - p_j)
     unsigned long long amax = 0;
 #pragma unroll
     for (int c = 0; c < DP; ++c) {
       const F av = a[((size_t)tm1 * DP + c) * P + pair];
       const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
-      sdot = fma(av, Xn[ro + i] - Xn[ro + j], sdot);
+      g = fma(-av, Xn[ro + i] - Xn[ro + j], g);
       const unsigned long long ab = abs_bits(av);
       amax = ab > amax ? ab : amax;
     }
     const F th = thk[q];
-    F tn = fma(d - sdot, F(0.5), th);
+    F tn = fma(g, F(0.5), th);
     if (sign_set(tn)) tn = F(0);
     thn[q] = tn;
     const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
@@ -1336,19 +1379,19 @@ __device__ void pair_gather_fused(const Dev<F>& D, const ScenMeta& s, int xl, in
     for (int pair = tid; pair < P; pair += nt) {
       const int pk = pr[pair];
       const int i = pk & 0xFFFF, j = pk >> 16;
-      F sdot = 0;
+      F g = d;  // d - a'(p_i - p_j)
       unsigned long long amax = 0;
 #pragma unroll
       for (int c = 0; c < DP; ++c) {
         const F av = a[((size_t)tm1 * DP + c) * P + pair];
         smA[c * P + pair] = av;
         const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
-        sdot = fma(av, Xn[ro + i] - Xn[ro + j], sdot);
+        g = fma(-av, Xn[ro + i] - Xn[ro + j], g);
         const unsigned long long ab = abs_bits(av);
         amax = ab > amax ? ab : amax;
       }
       const F th = thk[qb + pair];
-      F tn = fma(d - sdot, F(0.5), th);
+      F tn = fma(g, F(0.5), th);
       if (sign_set(tn)) tn = F(0);
       thn[qb + pair] = tn;
       smE[pair] = fma(F(2), tn, -th);
@@ -1625,18 +1668,18 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           const int P = s.P, pair = u - gs.poff[m];
           const uint32_t fij = st.pair[u];
           const int fi = fij & 0xFF, fj = fij >> 8;
-          F sdot = 0;
+          F g = F(s.d);  // d - a'(p_i - p_j)
           unsigned long long amax = 0;
 #pragma unroll
           for (int c = 0; c < DP; ++c) {
             const F avc = av[b][c];
             smA[c * nP + u] = avc;
-            sdot = fma(avc, st.pos[c][fi] - st.pos[c][fj], sdot);
+            g = fma(-avc, st.pos[c][fi] - st.pos[c][fj], g);
             const unsigned long long ab = abs_bits(avc);
             amax = ab > amax ? ab : amax;
           }
           const F th = thv[b];
-          F tn = fma(F(s.d) - sdot, F(0.5), th);
+          F tn = fma(g, F(0.5), th);
           if (sign_set(tn)) tn = F(0);
           D.theta[(size_t)tkp1 * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair] = tn;
           smE[u] = fma(F(2), tn, -th);
