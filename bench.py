@@ -237,7 +237,7 @@ def run_ours(args, rank, world):
     batch = workload_batch(args.n_scen, rank)
     solver = tg.Solver(batch, precision=args.precision, start="turbo", mode="batched",
                        threads_per_cta=args.tpc, kernel_variant=args.variant)
-    tpc, cps, var = (args.tpc, 0, args.variant) if args.no_autotune else solver.autotune(probe_iter=10)
+    tpc, cps, var = (args.tpc, 0, args.variant) if args.no_autotune else solver.autotune(probe_iter=100)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -375,7 +375,7 @@ def timed_solves(tg, torch, batch, args, reps=2, **kw):
     """Device time and solves of one solve of `batch` (after one untimed solve)."""
     do_tune = kw.pop("autotune", True)
     s = tg.Solver(batch, start="turbo", mode=kw.pop("mode", "batched"), **kw)
-    tuned = s.autotune(probe_iter=10) if do_tune else None
+    tuned = s.autotune(probe_iter=60) if do_tune else None
     s.solve(args.tol, args.max_iter)
     torch.cuda.synchronize()
     ms = []
