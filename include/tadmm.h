@@ -106,8 +106,9 @@ typedef struct {
                                              double-float (pairs of floats, 48-bit significand) on the
                                              FP32 pipe instead of the FP64 pipe; results agree with
                                              float64 to about 1e-13 relative */
-#define TADMM_FLAG_NO_COOP_REFACTOR 16    /* stage refactorizations one lane per agent, never spread over a
-                                             group of lanes (bitwise the same results) */
+#define TADMM_FLAG_NO_LANE_GROUPS 16      /* stage refactorizations and EQP passes one lane per agent, never
+                                             spread over a group of lanes (bitwise the same results) */
+#define TADMM_FLAG_NO_COOP_REFACTOR TADMM_FLAG_NO_LANE_GROUPS
 
 typedef struct tadmm_handle tadmm_handle;
 

@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4
 CONVERGED, NOT_CONVERGED, QP_FAIL, NUMERIC = 0, 1, 2, 3
 START = {"cold": 0, "hot": 1, "turbo": 2}
 FLAG_NO_FUSED_PAIR_GATHER, FLAG_NO_STRUCTURE, FLAG_NO_GROUPING, FLAG_DOUBLE_FLOAT = 1, 2, 4, 8
-FLAG_NO_COOP_REFACTOR = 16
+FLAG_NO_LANE_GROUPS = FLAG_NO_COOP_REFACTOR = 16
 MODE = {"batched": 0, "plain": 1, "graph": 2}
 
 _dp = C.POINTER(C.c_double)

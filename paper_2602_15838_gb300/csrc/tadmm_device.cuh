@@ -198,6 +198,13 @@ struct AgentConst {
   static constexpr int KC = 2 * NX + NU + 1;
 };
 
+// Pieces of the linear term q_t = -2 Q_t x_ref - rho C' h_t, shared by every
+// code path that forms it so that all form it with the same operations.
+template <typename F>
+__device__ __forceinline__ F lin_term(F base, F rho, F hr) { return fma(-rho, hr, base); }
+template <typename F>
+__device__ __forceinline__ F terminal_lin(F qf, F xr) { return (F(-2) * qf) * xr; }
+
 template <typename F, int NX, int NU, int DP>
 struct AgentCtx {
   const Model<F, NX, NU>* M;
@@ -236,14 +243,14 @@ struct AgentCtx {
   __device__ __forceinline__ F q_h(int r, F hr) const {
     using AC = AgentConst<NX, NU>;
     F v = k(AC::QL + r);
-    if (r < DP) v -= k(AC::RHO) * hr;
+    if (r < DP) v = lin_term(v, k(AC::RHO), hr);
     return v;
   }
   // linear term of x_t (t = 1..T): -2 Q_t x_ref - rho C' h_t
   __device__ __forceinline__ F q(int t, int r) const {
     using AC = AgentConst<NX, NU>;
-    F v = (t < T) ? k(AC::QL + r) : (F(-2) * qf[r]) * xr[r];
-    if (r < DP) v -= k(AC::RHO) * h[((size_t)(t - 1) * DP + r) * N + i];
+    F v = (t < T) ? k(AC::QL + r) : terminal_lin(qf[r], xr[r]);
+    if (r < DP) v = lin_term(v, k(AC::RHO), h[((size_t)(t - 1) * DP + r) * N + i]);
     return v;
   }
 };
@@ -864,6 +871,201 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
   return o;
 }
 
+// EQP solve of the agents of up to CoopShape<NX>::NG lanes of the warp, each
+// agent on a group of lanes with one lane per state row: the backward affine
+// pass and the forward rollout exchange rows by warp shuffles, so that an
+// agent's stage recurrence is a few operations long instead of a few dozen.
+// Every value is formed by the same operations, in the same order, as in
+// eqp_solve, so both give identical bits.  Every lane of the warp calls this;
+// `go` marks the lanes whose agent takes the pass (at most NG of them, the
+// caller checks).  The owner lane receives its agent's scan.  Used by the
+// per-phase x-update kernels, where few agents share a warp and each agent's
+// recurrence latency sets the time; in the persistent kernel the FP64 pipe is
+// shared by eight warps per SM and a lane-group pass saves nothing.
+template <typename F, int NX, int NU, int DP>
+__device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int GS = CoopShape<NX>::GS, H = NX / 2;
+  using CL = CacheLayout<NX, NU>;
+  using AC = AgentConst<NX, NU>;
+  const Model<F, NX, NU>& Mo = *A.M;
+  const F dt = Mo.A[0][H], b1 = Mo.B[0][0], b2 = Mo.B[H][0];
+  const int lane = threadIdx.x & 31, g = lane / GS, r = lane % GS, gbase = g * GS;
+  const int rr = r < NX ? r : NX - 1;  // state row of this lane
+  const int ra = r < NU ? r : NU - 1;  // input of this lane
+  const unsigned owners = __ballot_sync(FULL, go);
+  int olane = -1;
+  {
+    unsigned m = owners;
+    for (int k = 0; k < g && m; ++k) m &= m - 1;
+    if (m) olane = __ffs(m) - 1;
+  }
+  const int src = olane >= 0 ? olane : lane;
+  auto sp = [&](auto p) { return (decltype(p))__shfl_sync(FULL, (unsigned long long)p, src); };
+  F* const cache = sp(A.cache);
+  uint16_t* const Wm = sp(A.Wm);
+  F* const Us = sp(A.Us);
+  F* const Xo = sp(A.Xo);
+  const F* const hp = sp(A.h);
+  const F* const kc = sp(A.kc);
+  const F* const qf = sp(A.qf);
+  const F* const xr = sp(A.xr);
+  const F* const xi = sp(A.xi);
+  const int ks = __shfl_sync(FULL, A.ks, src), N = __shfl_sync(FULL, A.N, src);
+  const int ai = __shfl_sync(FULL, A.i, src), T = __shfl_sync(FULL, A.T, src);
+  const bool gact = olane >= 0;
+  const bool row = gact && r < NX;
+  const int Tm = __reduce_max_sync(FULL, gact ? T : 0);
+  auto C = [&](int t, int e) -> F& { return cache[((size_t)t * CL::E + e) * N + ai]; };
+  const F rho = gact ? kc[AC::RHO * ks] : F(0);
+
+  // backward affine pass; this lane carries p_{t+1}[rr]
+  F pn = F(0);
+  if (gact) {
+    pn = terminal_lin(qf[rr], xr[rr]);
+    if (rr < DP) pn = lin_term(pn, rho, hp[((size_t)(T - 1) * DP + rr) * N + ai]);
+  }
+  for (int t = Tm - 1; t >= 0; --t) {
+    const bool act = gact && t < T;
+    const uint16_t mask = act ? Wm[(size_t)t * N + ai] : (uint16_t)0;
+    F Pcp = pn;
+    if (mask) {
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        if (!(mask & (0x101u << a))) continue;
+        const F ub = (mask & (1u << a)) ? Mo.umin[a] : Mo.umax[a];
+        Pcp = fma(C(t, CL::PB + rr * NU + a), ub, Pcp);
+      }
+    }
+    // rows H + ra of p_{t+1} and of P_{t+1} c + p_{t+1}
+    const int shi = gbase + H + ra;
+    const F pnh = shfl_f(pn, shi), Pcph = shfl_f(Pcp, shi);
+    if (mask && r < NU) {
+      F acc = 0;
+      acc = fma(b1, pn, acc);
+      acc = fma(b2, pnh, acc);
+      C(t, CL::bp + ra) = acc;
+    }
+    F svl = 0;
+    {
+      F acc = 0;
+      acc = fma(b1, Pcp, acc);
+      acc = fma(b2, Pcph, acc);
+      svl = (mask & (0x101u << ra)) ? F(0) : acc;
+    }
+    F sv[NU];
+#pragma unroll
+    for (int b = 0; b < NU; ++b) sv[b] = shfl_f(svl, gbase + b);
+    if (act && r < NU) {
+      // k_t row ra = -(S^{-1} s)[ra]
+      F si[NU];
+#pragma unroll
+      for (int b = 0; b < NU; ++b) si[b] = C(t, CL::L + (b <= ra ? ra * NU + b : b * NU + ra));
+      F acc = si[0] * sv[0];
+#pragma unroll
+      for (int b = 1; b < NU; ++b) acc = fma(si[b], sv[b], acc);
+      C(t, CL::k + ra) = -acc;
+    }
+    if (t >= 1) {
+      const F Pcpl = shfl_f(Pcp, gbase + (rr >= H ? rr - H : rr));
+      if (act) {
+        F acc = kc[(AC::QL + rr) * ks];
+        if (rr < DP) acc = lin_term(acc, rho, hp[((size_t)(t - 1) * DP + rr) * N + ai]);
+        if (rr < H) {
+          acc = acc + Pcp;
+        } else {
+          acc = fma(dt, Pcpl, acc);
+          acc = acc + Pcp;
+        }
+#pragma unroll
+        for (int k = 0; k < NU; ++k) acc = fma(C(t, CL::K + k * NX + rr), sv[k], acc);
+        pn = acc;
+      }
+    }
+  }
+  __syncwarp();
+
+  // forward rollout; this lane carries x_t[rr]
+  EqpScan<F> o;
+  o.anum = 1; o.aden = 1; o.blk = -1; o.bside = 0; o.worst = 0; o.widx = -1; o.scale = 1; o.bad = 0; o.out = 0;
+  const unsigned long long kmin = mono_key(Mo.umin[ra]), kmax = mono_key(Mo.umax[ra]);
+  F xl = gact ? xi[rr] : F(0);
+  if (row) Xo[(size_t)rr * N + ai] = xl;
+  for (int t = 0; t < Tm; ++t) {
+    const bool act = gact && t < T;
+    const uint16_t mask = act ? Wm[(size_t)t * N + ai] : (uint16_t)0;
+    F xv[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) xv[c] = shfl_f(xl, gbase + c);
+    F ul;
+    if (mask & (1u << ra)) ul = Mo.umin[ra];
+    else if (mask & (0x100u << ra)) ul = Mo.umax[ra];
+    else {
+      F acc = act ? C(t, CL::k + ra) : F(0);
+#pragma unroll
+      for (int c = 0; c < NX; ++c) acc = fma(act ? C(t, CL::K + ra * NX + c) : F(0), xv[c], acc);
+      ul = acc;
+      const unsigned long long ku = mono_key(acc);
+      if (act && r < NU) o.out |= (ku < kmin) | (ku > kmax);
+    }
+    F uv[NU];
+#pragma unroll
+    for (int b = 0; b < NU; ++b) uv[b] = shfl_f(ul, gbase + b);
+    F xn;
+    if (rr < H) xn = fma(b1, pick<F, NU>(uv, rr), fma(dt, pick<F, NX>(xv, H + rr), xl));
+    else xn = fma(b2, pick<F, NU>(uv, rr - H), xl);
+    // every lane takes part in the shuffles (the masks differ between groups)
+    F xnv[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) xnv[c] = shfl_f(xn, gbase + c);
+    if (mask) {
+      if (act && r < NU && (mask & (0x101u << ra))) {
+        F gg = C(t, CL::bp + ra);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) gg = fma(C(t, CL::PB + c * NU + ra), xnv[c], gg);
+        gg = fma(kc[(AC::RB + ra) * ks], ul, gg);
+        const F mu = (mask & (1u << ra)) ? gg : -gg;
+        const F am = fabs_(mu);
+        if (am > o.scale) o.scale = am;
+        if (mu < o.worst) { o.worst = mu; o.widx = t * NU + ra; }
+        if (!(am == am)) o.bad = 1;
+      }
+    }
+    if (act && r < NU) Us[((size_t)t * NU + ra) * N + ai] = ul;
+    if (act && r < NX) Xo[((size_t)(t + 1) * NX + rr) * N + ai] = xn;
+    xl = xn;
+  }
+  if (row && (!(xl == xl) || fabs_(xl) > F(1e30))) o.bad = 1;
+  // combine the group's lanes: first (lowest index) most negative multiplier,
+  // largest |mu|, any flag
+#pragma unroll
+  for (int off = GS / 2; off > 0; off >>= 1) {
+    const F w2 = shfl_f(o.worst, lane ^ off);
+    const int i2 = __shfl_sync(FULL, o.widx, lane ^ off);
+    const F s2 = shfl_f(o.scale, lane ^ off);
+    const int b2i = __shfl_sync(FULL, o.bad, lane ^ off), o2 = __shfl_sync(FULL, o.out, lane ^ off);
+    if (i2 >= 0 && (o.widx < 0 || w2 < o.worst || (!(o.worst < w2) && i2 < o.widx))) {
+      o.worst = w2;
+      o.widx = i2;
+    }
+    if (s2 > o.scale) o.scale = s2;
+    o.bad |= b2i;
+    o.out |= o2;
+  }
+  // the owner takes its group's result
+  const int gi = __popc(owners & ((1u << lane) - 1u));
+  const int from = (go ? gi : g) * GS;
+  EqpScan<F> res;
+  res.anum = 1; res.aden = 1; res.blk = -1; res.bside = 0;
+  res.worst = shfl_f(o.worst, from);
+  res.widx = __shfl_sync(FULL, o.widx, from);
+  res.scale = shfl_f(o.scale, from);
+  res.bad = __shfl_sync(FULL, o.bad, from);
+  res.out = __shfl_sync(FULL, o.out, from);
+  __syncwarp();
+  return res;
+}
+
 // Ratio test of the primal active set (Nocedal & Wright Alg. 16.3) for the step
 // p = us - u over the free inputs: smallest blocking ratio (clamped at 0), ties
 // to the lowest (t, c) index, ratios compared as num*aden < anum*den.
@@ -939,7 +1141,7 @@ __device__ __forceinline__ void step_inputs(const AgentCtx<F, NX, NU, DP>& A, in
 // whatever number of lanes it serves.  Each lane's own sequence of working
 // sets, steps and multiplier tests is unchanged.
 // Returns ST_CONVERGED, ST_QP_FAIL or ST_NUMERIC.
-template <typename F, int NX, int NU, int DP, bool DI>
+template <typename F, int NX, int NU, int DP, bool DI, bool COOP_EQP>
 __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, bool has, int start_kind, int as_max, F eps_rel,
                              unsigned long long& neqp, unsigned long long& nfact) {
   constexpr unsigned FULL = 0xffffffffu;
@@ -1012,10 +1214,19 @@ __device__ int xupdate_agent(const AgentCtx<F, NX, NU, DP>& A, bool has, int sta
     if (!__any_sync(FULL, go)) break;
     int bad = 0;
     refactor_sweep<F, NX, NU, DP, DI>(A, go, dirty, nfact, bad);
+    // few agents in this round: each takes its pass on a group of lanes
+    EqpScan<F> o;
+    bool coop_pass = false;
+    if constexpr (COOP_EQP && DI && (std::is_same<F, double>::value || std::is_same<F, float>::value)) {
+      if (A.coop && __popc(__ballot_sync(FULL, go)) <= CoopShape<NX>::NG) {
+        o = eqp_coop<F, NX, NU, DP>(A, go);
+        coop_pass = true;
+      }
+    }
     if (go) {
       --as_max;
       ++neqp;
-      EqpScan<F> o = eqp_solve<F, NX, NU, DP, DI>(A);
+      if (!coop_pass) o = eqp_solve<F, NX, NU, DP, DI>(A);
       if (bad || o.bad) {
         status = ST_NUMERIC;
       } else {
@@ -1154,7 +1365,7 @@ __device__ __forceinline__ int start_kind_of(const Dev<F>& D, int k) {
 // x-update of agents i0, i0 + stride, ... of scenario s (none when in_scen is
 // false).  Every lane of the warp calls this; all lanes take the same number
 // of rounds, so that xupdate_agent always runs warp-wide.
-template <typename F, int NX, int NU, int DP, bool DI>
+template <typename F, int NX, int NU, int DP, bool DI, bool COOP_EQP = false>
 __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, bool in_scen, int k,
                              int lvl_out, int i0, int stride, unsigned long long& neqp,
                              unsigned long long& nfact, F* kcs) {
@@ -1169,7 +1380,7 @@ __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const S
     const AgentCtx<F, NX, NU, DP> A =
         has ? make_agent<F, NX, NU, DP>(D, M, s, i0 + r * stride, lvl_out, kcs + threadIdx.x, blockDim.x)
             : idle_agent<F, NX, NU, DP>(M, kcs + threadIdx.x, blockDim.x, D.coop);
-    const int res = xupdate_agent<F, NX, NU, DP, DI>(A, has, kind, as_max, eps, neqp, nfact);
+    const int res = xupdate_agent<F, NX, NU, DP, DI, COOP_EQP>(A, has, kind, as_max, eps, neqp, nfact);
     if (has && res > st) st = res;
   }
   return st;
@@ -1606,7 +1817,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
                                             : idle_agent<F, NX, NU, DP>(M, kcs + tid, nt, D.coop);
       const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
       const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
-      const int st = xupdate_agent<F, NX, NU, DP, DI>(A, has, start_kind_of(D, k), as_max, eps, neqp, nfact);
+      const int st = xupdate_agent<F, NX, NU, DP, DI, false>(A, has, start_kind_of(D, k), as_max, eps, neqp, nfact);
       if (has && st) atomicMax(&gs.flag[my_m], st);
     }
     __syncthreads();

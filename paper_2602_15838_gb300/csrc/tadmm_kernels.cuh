@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(32) k_xupdate(Dev<F> D, int sc, int k, int lvl
   const bool owns = (int)threadIdx.x < apw;
   const int i = blockIdx.x * apw + threadIdx.x;
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, owns, k, lvl_out, i, s.N, neqp, nfact, kcs);
+  const int st = xupdate_phase<F, NX, NU, DP, DI, true>(D, M, s, owns, k, lvl_out, i, s.N, neqp, nfact, kcs);
   if (st && owns && i < s.N) atomicMax(flag, st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(32) k_g_xupdate(Dev<F> D, GState G, const int3
   const ScenMeta s = D.meta[sc];
   const int i = (int)(ga - s.agent_off), k = G.iter[sc];
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI>(D, M, s, in_scen, k, (k + 1) & 1, i, s.N, neqp, nfact, kcs);
+  const int st = xupdate_phase<F, NX, NU, DP, DI, true>(D, M, s, in_scen, k, (k + 1) & 1, i, s.N, neqp, nfact, kcs);
   if (!in_scen) return;
   if (st) atomicMax(&G.fail[sc], st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
@@ -429,7 +429,7 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.as_max = h->opt.as_max;
   D.eps_rel = h->opt.eps_rel;
   D.single_as_group = (h->opt.flags & (TADMM_FLAG_NO_GROUPING | TADMM_FLAG_NO_FUSED_PAIR_GATHER)) ? 0 : 1;
-  D.coop = (h->opt.flags & TADMM_FLAG_NO_COOP_REFACTOR) ? 0 : 1;
+  D.coop = (h->opt.flags & TADMM_FLAG_NO_LANE_GROUPS) ? 0 : 1;
   return D;
 }
 

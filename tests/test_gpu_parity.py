@@ -348,13 +348,14 @@ def test_largest_mixed_batch_scenarios_fp64(tg):
 
 
 def test_cooperative_refactorization_bitwise_equal(tg):
-    """Stage refactorizations spread over lane groups give bitwise the same
-    iterates, working sets and counters as one lane per agent: the mixed batch
-    through the persistent kernel (2D, groups of 4 lanes) and the 512-agent 3D
-    swarm through the graph-mode kernels (groups of 8 lanes)."""
+    """Stage refactorizations and EQP passes spread over lane groups give
+    bitwise the same iterates, working sets and counters as one lane per
+    agent: the mixed batch through the persistent kernel and the graph-mode
+    kernels (2D, groups of 4 lanes) and the 512-agent 3D swarm through the
+    graph-mode kernels (groups of 8 lanes)."""
     b = make_workload("mixed", n_scen=48)
     for tol, it in ((0.0, 12), (1e-4, 300)):
-        ref, cr = gpu_run(tg, b, tol, it, flags=tg.FLAG_NO_COOP_REFACTOR)
+        ref, cr = gpu_run(tg, b, tol, it, flags=tg.FLAG_NO_LANE_GROUPS)
         g, cg = gpu_run(tg, b, tol, it)
         for k in range(b.n_scen):
             assert g[k]["status"] == ref[k]["status"] and g[k]["iters"] == ref[k]["iters"], k
@@ -362,8 +363,16 @@ def test_cooperative_refactorization_bitwise_equal(tg):
             assert np.array_equal(g[k]["theta"], ref[k]["theta"]), k
             assert np.array_equal(g[k]["W"], ref[k]["W"]), k
         assert np.array_equal(cg["eqp"], cr["eqp"]) and np.array_equal(cg["fact"], cr["fact"])
+    for tol, it in ((0.0, 6), (1e-4, 200)):
+        ref, cr = gpu_run(tg, b, tol, it, mode="graph", flags=tg.FLAG_NO_LANE_GROUPS)
+        g, cg = gpu_run(tg, b, tol, it, mode="graph")
+        for k in range(b.n_scen):
+            assert g[k]["status"] == ref[k]["status"] and g[k]["iters"] == ref[k]["iters"], k
+            assert np.array_equal(g[k]["X"], ref[k]["X"]), k
+            assert np.array_equal(g[k]["theta"], ref[k]["theta"]), k
+        assert np.array_equal(cg["eqp"], cr["eqp"]) and np.array_equal(cg["fact"], cr["fact"])
     sw = make_workload("swarm3d")
-    ref, cr = gpu_run(tg, sw, 0.0, 2, mode="graph", flags=tg.FLAG_NO_COOP_REFACTOR)
+    ref, cr = gpu_run(tg, sw, 0.0, 2, mode="graph", flags=tg.FLAG_NO_LANE_GROUPS)
     g, cg = gpu_run(tg, sw, 0.0, 2, mode="graph")
     assert np.array_equal(g[0]["X"], ref[0]["X"])
     assert np.array_equal(g[0]["theta"], ref[0]["theta"])
