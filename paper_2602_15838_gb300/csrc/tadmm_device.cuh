@@ -163,6 +163,9 @@ __device__ __forceinline__ unsigned long long mono_key(float v) {
 }
 __device__ __forceinline__ bool sign_set(double v) { return __double_as_longlong(v) < 0; }
 __device__ __forceinline__ bool sign_set(float v) { return __float_as_int(v) < 0; }
+// NaN test on an abs_bits key.
+__device__ __forceinline__ bool nan_key(unsigned long long ab, double) { return ab > 0x7FF0000000000000ull; }
+__device__ __forceinline__ bool nan_key(unsigned long long ab, float) { return ab > 0x7F800000ull; }
 
 __device__ __forceinline__ int pair_index(int N, int i, int j) {  // i < j
   return i * N - (i * (i + 1)) / 2 + (j - i - 1);
@@ -851,10 +854,11 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
         for (int c = 0; c < NX; ++c) g = fma(A.C(t, CL::PB + c * NU + a), xn[c], g);
         g = fma(A.k(AgentConst<NX, NU>::RB + a), uv[a], g);
         const F mu = (mask & (1u << a)) ? g : -g;
-        const F am = fabs_(mu);
-        if (am > o.scale) o.scale = am;
-        if (mu < o.worst) { o.worst = mu; o.widx = t * NU + a; }
-        if (!(am == am)) o.bad = 1;
+        // comparisons on integer keys (the FP64 pipe is kept for arithmetic)
+        const unsigned long long ab = abs_bits(mu);
+        if (ab > abs_bits(o.scale)) o.scale = from_bits(ab, F(0));
+        if (mono_key(mu) < mono_key(o.worst)) { o.worst = mu; o.widx = t * NU + a; }
+        if (nan_key(ab, F(0))) o.bad = 1;
       }
     }
 #pragma unroll
@@ -1025,10 +1029,10 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
         for (int c = 0; c < NX; ++c) gg = fma(C(t, CL::PB + c * NU + ra), xnv[c], gg);
         gg = fma(kc[(AC::RB + ra) * ks], ul, gg);
         const F mu = (mask & (1u << ra)) ? gg : -gg;
-        const F am = fabs_(mu);
-        if (am > o.scale) o.scale = am;
-        if (mu < o.worst) { o.worst = mu; o.widx = t * NU + ra; }
-        if (!(am == am)) o.bad = 1;
+        const unsigned long long ab = abs_bits(mu);
+        if (ab > abs_bits(o.scale)) o.scale = from_bits(ab, F(0));
+        if (mono_key(mu) < mono_key(o.worst)) { o.worst = mu; o.widx = t * NU + ra; }
+        if (nan_key(ab, F(0))) o.bad = 1;
       }
     }
     if (act && r < NU) Us[((size_t)t * NU + ra) * N + ai] = ul;
@@ -1044,11 +1048,12 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
     const int i2 = __shfl_sync(FULL, o.widx, lane ^ off);
     const F s2 = shfl_f(o.scale, lane ^ off);
     const int b2i = __shfl_sync(FULL, o.bad, lane ^ off), o2 = __shfl_sync(FULL, o.out, lane ^ off);
-    if (i2 >= 0 && (o.widx < 0 || w2 < o.worst || (!(o.worst < w2) && i2 < o.widx))) {
+    const unsigned long long k1 = mono_key(o.worst), k2 = mono_key(w2);
+    if (i2 >= 0 && (o.widx < 0 || k2 < k1 || (k2 == k1 && i2 < o.widx))) {
       o.worst = w2;
       o.widx = i2;
     }
-    if (s2 > o.scale) o.scale = s2;
+    if (abs_bits(s2) > abs_bits(o.scale)) o.scale = s2;
     o.bad |= b2i;
     o.out |= o2;
   }
@@ -1094,13 +1099,21 @@ __device__ void ratio_test(const AgentCtx<F, NX, NU, DP>& A, EqpScan<F>& o) {
       if (mk[j] & (0x101u << a)) continue;
       const F cu = cuv[j][a];
       const F p = suv[j][a] - cu;
-      F num = 0, den = 0;
-      int side = 0;
-      if (p < F(0)) { num = cu - Mo.umin[a]; den = -p; side = 1; }
-      else if (p > F(0)) { num = Mo.umax[a] - cu; den = p; side = 2; }
-      if (side) {
-        if (num < F(0)) num = 0;
-        if (num * o.aden < o.anum * den) { o.anum = num; o.aden = den; o.blk = t * NU + a; o.bside = side; }
+      // signs and the ratio comparison on integer keys: p < 0 (side 1) or
+      // p > 0 (side 2); num = distance to the bound, clamped at +0; den = |p|;
+      // blocking when num / den < anum / aden, compared as num*aden < anum*den
+      const unsigned long long pb = abs_bits(p);
+      if (pb == 0) continue;
+      const bool lower = sign_set(p);
+      const F hi = lower ? cu : Mo.umax[a], lo = lower ? Mo.umin[a] : cu;
+      F num = hi - lo;
+      if (sign_set(num)) num = F(0);
+      const F den = from_bits(pb, F(0));
+      if (mono_key(num * o.aden) < mono_key(o.anum * den)) {
+        o.anum = num;
+        o.aden = den;
+        o.blk = t * NU + a;
+        o.bside = lower ? 1 : 2;
       }
     }
   }

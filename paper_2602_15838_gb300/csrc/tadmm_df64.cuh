@@ -110,6 +110,8 @@ __device__ __forceinline__ unsigned long long abs_bits(df64 v) {
   return ((unsigned long long)(uint32_t)__float_as_int(a.hi) << 32) | f32_key(a.lo);
 }
 __device__ __forceinline__ unsigned long long ord_bits(df64 v) { return abs_bits(v); }
+// NaN test on an abs_bits key (the high word carries |hi|).
+__device__ __forceinline__ bool nan_key(unsigned long long ab, df64) { return (ab >> 32) > 0x7F800000ull; }
 __device__ __forceinline__ df64 from_bits(unsigned long long b, df64) {
   return df64(__int_as_float((int)(uint32_t)(b >> 32)), f32_unkey((uint32_t)b));
 }
