@@ -96,6 +96,15 @@ typedef struct {
   int32_t kernel_variant;  /* batched mode: register-budget variant 0..2 of the persistent kernel
                               (0: no cap; 1: 32 threads x 12 CTAs/SM; 2: 64 threads x 8 CTAs/SM) */
   int32_t flags;           /* TADMM_FLAG_* bits; 0 = all optimizations on */
+  /* Residual balancing of the penalty (an extension: the paper keeps rho fixed;
+   * Boyd et al. 2011, Sec. 3.4.1).  Every adapt_every iterations (0 = off), after
+   * the residuals r, s of that iteration and if the scenario has not stopped:
+   * rho *= adapt_tau when r > adapt_mu * s, rho /= adapt_tau when s > adapt_mu * r,
+   * the scaled duals rescaled so that the unscaled multipliers are unchanged.
+   * Batched mode only, scenarios of at most 32 agents; EINVAL otherwise. */
+  int32_t adapt_every;
+  double adapt_mu;         /* > 1 */
+  double adapt_tau;        /* > 1 */
 } tadmm_options;
 
 /* option flags (results are the same either way; for testing and measurement) */
@@ -143,6 +152,11 @@ int tadmm_get_solution(tadmm_handle* h, double* X, double* U, double* theta, int
  * eqp [n_scen] active-set EQP solves summed over agents and iterations,
  * fact [n_scen] Riccati stage factorizations, pairsteps processed. */
 int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pairsteps);
+
+/* Penalty of each scenario at the end of the last solve and the number of
+ * times residual balancing changed it (host buffers, synchronous; either may
+ * be NULL).  Without residual balancing: the input rho and 0. */
+int tadmm_get_penalty(tadmm_handle* h, double* rho_final, int32_t* rho_changes);
 
 /* Times the candidate launch shapes of the batched persistent kernel (threads
  * per CTA, resident CTAs per SM, register-budget variant) on this batch with

@@ -38,7 +38,8 @@ class TadmmBatch(C.Structure):
 class TadmmOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("start_mode", C.c_int32), ("as_max", C.c_int32),
                 ("eps_rel", C.c_double), ("mode", C.c_int32), ("threads_per_cta", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("kernel_variant", C.c_int32), ("flags", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("kernel_variant", C.c_int32), ("flags", C.c_int32),
+                ("adapt_every", C.c_int32), ("adapt_mu", C.c_double), ("adapt_tau", C.c_double)]
 
 
 class TadmmError(RuntimeError):
@@ -61,6 +62,7 @@ def lib():
         L.tadmm_get_solution.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_get_counters.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
+        L.tadmm_get_penalty.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
         L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p, _i32p]
         L.tadmm_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -121,15 +123,17 @@ class Solver:
 
     def __init__(self, batch, precision: int = 64, start: str = "turbo", mode: str = "batched",
                  as_max: int = 0, eps_rel: float = 0.0, threads_per_cta: int = 0, ctas_per_sm: int = 0,
-                 kernel_variant: int = 0, flags: int = 0):
+                 kernel_variant: int = 0, flags: int = 0, adapt=None):
+        """adapt = (every, mu, tau) turns on residual balancing of rho (batched mode)."""
         import torch
         if not torch.cuda.is_available():
             raise TadmmError("no CUDA device: the solver has no CPU path")
         self.batch = batch
         self.precision = precision
         self._hb = _HostBatch(batch)
+        ae, am, at = (0, 10.0, 2.0) if adapt is None else adapt
         opt = TadmmOptions(precision, START[start], as_max, eps_rel, MODE[mode], threads_per_cta, ctas_per_sm,
-                           kernel_variant, flags)
+                           kernel_variant, flags, int(ae), float(am), float(at))
         h = C.c_void_p()
         _check(lib().tadmm_create(C.byref(self._hb.s), C.byref(opt), C.byref(h)), "tadmm_create")
         self.h = h
@@ -220,6 +224,14 @@ class Solver:
         _check(lib().tadmm_get_counters(self.h, eqp.ctypes.data_as(_i64p), fact.ctypes.data_as(_i64p),
                                         ps.ctypes.data_as(_i64p)), "tadmm_get_counters")
         return dict(eqp=eqp, fact=fact, pairsteps=ps)
+
+    def penalty(self):
+        """Final rho per scenario and the number of residual-balancing changes."""
+        rho = np.zeros(self.n_scen, dtype=np.float64)
+        chg = np.zeros(self.n_scen, dtype=np.int32)
+        _check(lib().tadmm_get_penalty(self.h, rho.ctypes.data_as(C.POINTER(C.c_double)),
+                                       chg.ctypes.data_as(C.POINTER(C.c_int32))), "tadmm_get_penalty")
+        return dict(rho=rho, changes=chg)
 
     def split(self, sol):
         """Splits packed host results into per-scenario arrays (X [N,T+1,nx], U, theta [P,T], W)."""

@@ -131,7 +131,7 @@ static void free_all(tadmm_handle* h) {
   void* ptrs[] = {h->meta,   h->order, h->pairs, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
                   h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->X,      h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
-                  h->res,    h->eqp,   h->fact,  h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
+                  h->res,    h->eqp,   h->fact,  h->rho_out, h->rho_chg, h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
                   h->ex_buf, h->flag,  h->red2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -207,6 +207,17 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   if (o.ctas_per_sm < 0) return set_error(TADMM_EINVAL, "ctas_per_sm must be >= 0");
   if (o.kernel_variant < 0 || o.kernel_variant > 2) return set_error(TADMM_EINVAL, "kernel_variant must be in 0..2");
 
+  if (o.adapt_every < 0) return set_error(TADMM_EINVAL, "adapt_every must be >= 0");
+  if (o.adapt_every > 0) {
+    if (!(o.adapt_mu > 1.0) || !(o.adapt_tau > 1.0) || !std::isfinite(o.adapt_mu) || !std::isfinite(o.adapt_tau))
+      return set_error(TADMM_EINVAL, "residual balancing needs finite adapt_mu > 1 and adapt_tau > 1");
+    if (o.mode != TADMM_MODE_BATCHED)
+      return set_error(TADMM_EINVAL, "residual balancing runs in the batched mode");
+    if (o.flags & (TADMM_FLAG_NO_GROUPING | TADMM_FLAG_NO_FUSED_PAIR_GATHER))
+      return set_error(TADMM_EINVAL, "residual balancing runs on the group path (no NO_GROUPING / NO_FUSED flags)");
+    for (int s2 = 0; s2 < b->n_scen; ++s2)
+      if (b->N[s2] > 32) return set_error(TADMM_EINVAL, "residual balancing supports scenarios of at most 32 agents");
+  }
   if ((o.flags & TADMM_FLAG_DOUBLE_FLOAT) && (o.precision != 64 || b->nx != 4))
     return set_error(TADMM_EINVAL, "TADMM_FLAG_DOUBLE_FLOAT needs precision 64 and (nx, nu, dp) = (4, 2, 2)");
   tadmm_handle* h = new tadmm_handle();
@@ -340,6 +351,7 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
       (rc = dmalloc(&h->status, 4 * h->n_scen)) || (rc = dmalloc(&h->iters, 4 * h->n_scen)) ||
       (rc = dmalloc(&h->cur_lvl, 4 * h->n_scen)) || (rc = dmalloc(&h->res, 16 * h->n_scen)) ||
       (rc = dmalloc(&h->eqp, 8 * h->n_scen)) || (rc = dmalloc(&h->fact, 8 * h->n_scen)) ||
+      (rc = dmalloc(&h->rho_out, 8 * h->n_scen)) || (rc = dmalloc(&h->rho_chg, 4 * h->n_scen)) ||
       (rc = dmalloc(&h->queue, 16)) ||
       (rc = dmalloc(&h->st_model, 8 * (nx * nx + nx * nu + 2 * nu))) ||
       (rc = dmalloc(&h->st_agent, 8 * na * (4 * nx + nu))) || (rc = dmalloc(&h->st_a, 8 * h->tot_ps * dp)) ||
@@ -465,6 +477,26 @@ extern "C" int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, 
     std::vector<int32_t> it(h->n_scen);
     if ((rc = cuda_check(cudaMemcpy(it.data(), h->iters, 4 * h->n_scen, cudaMemcpyDeviceToHost), "iters"))) return rc;
     for (int s = 0; s < h->n_scen; ++s) pairsteps[s] = (int64_t)it[s] * h->meta_h[s].P * h->meta_h[s].T;
+  }
+  return TADMM_OK;
+}
+
+extern "C" int tadmm_get_penalty(tadmm_handle* h, double* rho_final, int32_t* rho_changes) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!h->solved) return set_error(TADMM_ESTATE, "get_penalty before solve");
+  int rc;
+  if ((rc = cuda_check(cudaDeviceSynchronize(), "penalty sync"))) return rc;
+  if (h->opt.mode == TADMM_MODE_BATCHED) {
+    if (rho_final && (rc = cuda_check(cudaMemcpy(rho_final, h->rho_out, 8 * h->n_scen, cudaMemcpyDeviceToHost), "rho")))
+      return rc;
+    if (rho_changes &&
+        (rc = cuda_check(cudaMemcpy(rho_changes, h->rho_chg, 4 * h->n_scen, cudaMemcpyDeviceToHost), "rho changes")))
+      return rc;
+  } else {
+    for (int s = 0; s < h->n_scen; ++s) {
+      if (rho_final) rho_final[s] = h->meta_h[s].rho;
+      if (rho_changes) rho_changes[s] = 0;
+    }
   }
   return TADMM_OK;
 }

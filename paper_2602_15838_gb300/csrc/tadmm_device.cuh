@@ -87,6 +87,10 @@ struct Dev {
   double eps_rel;
   int32_t single_as_group;   // 1: a lone scenario of at most 32 agents also runs the group path
   int32_t coop;              // 1: refactorizations may be spread over lane groups
+  int32_t adapt_every;       // residual balancing of rho every adapt_every iterations (0: off)
+  double adapt_mu, adapt_tau;
+  double* rho_out;           // [n_scen] final rho (batched mode), or nullptr
+  int32_t* rho_chg;          // [n_scen] number of rho changes
 };
 
 // Per-stage factor cache of one agent (stage t):
@@ -1310,7 +1314,7 @@ __device__ void init_phase(const Dev<F>& D, const ScenMeta& s, int64_t t0, int64
 template <typename F, int NX, int NU, int DP>
 __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, const Model<F, NX, NU>& M,
                                                               const ScenMeta& s, int i, int lvl_out, F* kc,
-                                                              int ks) {
+                                                              int ks, double rho) {
   using AC = AgentConst<NX, NU>;
   AgentCtx<F, NX, NU, DP> A;
   A.M = &M;
@@ -1331,8 +1335,8 @@ __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, c
   A.qf = D.Qfd + ag * NX;
   A.xr = D.x_ref + ag * NX;
   A.xi = D.x_init + ag * NX;
-  const F rnc = F(s.rho) * F(s.N - 1);
-  kc[AC::RHO * ks] = F(s.rho);
+  const F rnc = F(rho) * F(s.N - 1);
+  kc[AC::RHO * ks] = F(rho);
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
     const F q = D.Qd[ag * NX + r], xr = D.x_ref[ag * NX + r];
@@ -1391,7 +1395,7 @@ __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const S
   for (int r = 0; r < rounds; ++r) {
     const bool has = r < mine;
     const AgentCtx<F, NX, NU, DP> A =
-        has ? make_agent<F, NX, NU, DP>(D, M, s, i0 + r * stride, lvl_out, kcs + threadIdx.x, blockDim.x)
+        has ? make_agent<F, NX, NU, DP>(D, M, s, i0 + r * stride, lvl_out, kcs + threadIdx.x, blockDim.x, s.rho)
             : idle_agent<F, NX, NU, DP>(M, kcs + threadIdx.x, blockDim.x, D.coop);
     const int res = xupdate_agent<F, NX, NU, DP, DI, COOP_EQP>(A, has, kind, as_max, eps, neqp, nfact);
     if (has && res > st) st = res;
@@ -1727,6 +1731,10 @@ __device__ void run_scenario(const Dev<F>& D, const Model<F, NX, NU>& M, const S
     D.res[2 * sc + 1] = double(sres);
     D.eqp[sc] = cs.cnt[0];
     D.fact[sc] = cs.cnt[1];
+    if (D.rho_out) {
+      D.rho_out[sc] = s.rho;
+      D.rho_chg[sc] = 0;
+    }
   }
 }
 
@@ -1760,7 +1768,11 @@ struct GroupSm {
   unsigned long long rb[kGroupMax];
   unsigned long long sb[kGroupMax];
   unsigned long long cnt[kGroupMax][2];
-  int G, nA, nP, T, any;
+  double rho[kGroupMax];    // current penalty per member (residual balancing)
+  double scale[kGroupMax];  // this iteration's penalty factor per member
+  int rhoc[kGroupMax];      // penalty changes per member
+  int adapt[kGroupMax];     // member's penalty changed this iteration
+  int G, nA, nP, T, any, anyad;
 };
 
 // Member owning flattened index u given exclusive prefix sums off[0..G].
@@ -1785,6 +1797,9 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     gs.sb[tid] = 0;
     gs.cnt[tid][0] = 0;
     gs.cnt[tid][1] = 0;
+    gs.rho[tid] = gs.meta[tid].rho;
+    gs.rhoc[tid] = 0;
+    gs.adapt[tid] = 0;
   }
   __syncthreads();
   if (tid == 0) {
@@ -1822,11 +1837,13 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
   for (int k = 0; k < D.max_iter; ++k) {
     const int tk = k % 3, tkp1 = (k + 1) % 3, tkm1 = (k + 2) % 3;
     const bool last = (k + 1 == D.max_iter);
+    const bool adapt_iter = D.adapt_every > 0 && (k + 1) % D.adapt_every == 0;
     // x-update (every lane of the warp takes part; lanes without an active agent help)
     {
       const bool has = my_m >= 0 && gs.active[my_m] != 0;
       const ScenMeta& s = gs.meta[has ? my_m : 0];
-      const AgentCtx<F, NX, NU, DP> A = has ? make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1, kcs + tid, nt)
+      const AgentCtx<F, NX, NU, DP> A = has ? make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1, kcs + tid, nt,
+                                                                        gs.rho[my_m])
                                             : idle_agent<F, NX, NU, DP>(M, kcs + tid, nt, D.coop);
       const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
       const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
@@ -1949,7 +1966,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           D.iters[sc] = k + 1;
           D.cur_lvl[sc] = (xl ^ 1) | (tkp1 << 1);
           D.res[2 * sc] = double(r);
-        } else if (r <= F(D.tol) || last) {
+        } else if (r <= F(D.tol) || last || adapt_iter) {
           gs.need[tid] = 1;
         }
       }
@@ -1980,7 +1997,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
       const F r = from_bits(gs.rb[tid], F(0));
       D.res[2 * sc] = double(r);
       if (gs.need[tid]) {
-        const F sres = F(gs.meta[tid].rho) * from_bits(gs.sb[tid], F(0));
+        const F sres = F(gs.rho[tid]) * from_bits(gs.sb[tid], F(0));
         D.res[2 * sc + 1] = double(sres);
         int stop = 0, status = ST_NOT_CONVERGED;
         if (!finite_(sres)) { stop = 1; status = ST_NUMERIC; }
@@ -1991,6 +2008,17 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           D.status[sc] = status;
           D.iters[sc] = k + 1;
           D.cur_lvl[sc] = (xl ^ 1) | (tkp1 << 1);
+        } else if (adapt_iter) {
+          // residual balancing (Boyd et al. 2011, Sec. 3.4.1)
+          double scale = 1.0;
+          if (double(r) > D.adapt_mu * double(sres)) scale = D.adapt_tau;
+          else if (double(sres) > D.adapt_mu * double(r)) scale = 1.0 / D.adapt_tau;
+          if (scale != 1.0) {
+            gs.adapt[tid] = 1;
+            gs.scale[tid] = scale;
+            gs.rho[tid] *= scale;
+            gs.rhoc[tid] += 1;
+          }
         }
       }
       gs.rb[tid] = 0;
@@ -1998,11 +2026,72 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     }
     __syncthreads();
     if (tid == 0) {
-      int any = 0;
-      for (int m = 0; m < G; ++m) any |= gs.active[m];
+      int any = 0, anyad = 0;
+      for (int m = 0; m < G; ++m) {
+        any |= gs.active[m];
+        anyad |= gs.adapt[m];
+      }
       gs.any = any;
+      gs.anyad = anyad;
     }
     __syncthreads();
+    if (gs.anyad) {
+      // rho changed by `scale` for the flagged members: the scaled duals
+      // become theta^{k+1} / scale; the previous slot is set to
+      // theta^k - theta^{k+1} + theta^{k+1} / scale so that the consensus
+      // copies w (and the next dual residual) are unchanged; then the
+      // aggregate h of the next x-update is formed again, and every stage is
+      // refactorized (the Hessian holds rho)
+      for (int tm1 = 0; tm1 < T; ++tm1) {
+        for (int u = tid; u < nP; u += nt) {
+          const int m = st.mem[u];
+          if (!gs.adapt[m]) continue;
+          const ScenMeta& s = gs.meta[m];
+          const int P = s.P, pair = u - gs.poff[m];
+          const size_t q = s.ps_off + (size_t)tm1 * P + pair;
+          F* const t1p = D.theta + (size_t)tkp1 * D.tot_ps + q;
+          F* const t0p = D.theta + (size_t)tk * D.tot_ps + q;
+          const F th1 = *t1p, th0 = *t0p;
+          const F t1 = th1 / F(gs.scale[m]);
+          const F t0 = (th0 - th1) + t1;
+          *t1p = t1;
+          *t0p = t0;
+          smE[u] = fma(F(2), t1, -t0);
+          const F* a = D.a + s.ps_off * DP;
+#pragma unroll
+          for (int c = 0; c < DP; ++c) smA[c * nP + u] = a[((size_t)tm1 * DP + c) * P + pair];
+        }
+        __syncthreads();
+        if (my_m >= 0 && gs.adapt[my_m]) {
+          const ScenMeta& s = gs.meta[my_m];
+          const int N = s.N, i = my_i, base = gs.poff[my_m];
+          const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+          F acc[DP];
+#pragma unroll
+          for (int c = 0; c < DP; ++c) acc[c] = F(N - 1) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
+          for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            const bool first = i < j;
+            const int pair = base + (first ? pair_index(N, i, j) : pair_index(N, j, i));
+            F e = smE[pair];
+            if (!first) e = -e;
+#pragma unroll
+            for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * nP + pair], acc[c]);
+          }
+          F* h = D.h + s.as_off * DP;
+#pragma unroll
+          for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+        }
+        __syncthreads();
+      }
+      if (my_m >= 0 && gs.adapt[my_m]) {
+        const ScenMeta& s = gs.meta[my_m];
+        for (int t = 0; t < s.T; ++t) D.Cm[s.as_off + (size_t)t * s.N + my_i] = 0xFFFF;
+      }
+      __syncthreads();
+      if (tid < G) gs.adapt[tid] = 0;
+      __syncthreads();
+    }
     xl ^= 1;
     if (!gs.any) break;
   }
@@ -2012,6 +2101,10 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
   }
   __syncthreads();
   if (tid < G) {
+    if (D.rho_out) {
+      D.rho_out[gs.sid[tid]] = gs.rho[tid];
+      D.rho_chg[gs.sid[tid]] = gs.rhoc[tid];
+    }
     D.eqp[gs.sid[tid]] = gs.cnt[tid][0];
     D.fact[gs.sid[tid]] = gs.cnt[tid][1];
   }

@@ -62,6 +62,8 @@ struct tadmm_handle {
   double* res = nullptr;
   unsigned long long* eqp = nullptr;
   unsigned long long* fact = nullptr;
+  double* rho_out = nullptr;     // [n_scen] penalty at the end of the last solve
+  int32_t* rho_chg = nullptr;    // [n_scen] residual-balancing changes of the last solve
   int32_t* queue = nullptr;
 
   // float64 staging in the caller's layouts (imports and exports)

@@ -391,7 +391,7 @@ __global__ void k_export_theta(Dev<F> D, const int32_t* __restrict__ pair_scen, 
 // ---------------------------------------------------------------------------
 template <typename F>
 static Dev<F> make_dev(tadmm_handle* h) {
-  Dev<F> D;
+  Dev<F> D{};
   std::memset(&D, 0, sizeof(D));
   D.meta = h->meta;
   D.pairs = h->pairs;
@@ -430,6 +430,11 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.eps_rel = h->opt.eps_rel;
   D.single_as_group = (h->opt.flags & (TADMM_FLAG_NO_GROUPING | TADMM_FLAG_NO_FUSED_PAIR_GATHER)) ? 0 : 1;
   D.coop = (h->opt.flags & TADMM_FLAG_NO_LANE_GROUPS) ? 0 : 1;
+  D.adapt_every = h->opt.adapt_every;
+  D.adapt_mu = h->opt.adapt_mu;
+  D.adapt_tau = h->opt.adapt_tau;
+  D.rho_out = h->rho_out;
+  D.rho_chg = h->rho_chg;
   return D;
 }
 

@@ -138,7 +138,7 @@ static int noalloc_run(const tadmm_scenario_dev* sc, int start_mode, double tol,
       if (rc) return rc;
     }
     cv = Carve{(char*)base};
-    Dev<F> D;
+    Dev<F> D{};  // fields not set below stay zero (no residual balancing, no penalty output)
     std::memset(&D, 0, sizeof(D));
     ScenMeta* meta = cv.take<ScenMeta>(sizeof(ScenMeta));
     int32_t* order = cv.take<int32_t>(4);

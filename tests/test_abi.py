@@ -45,13 +45,15 @@ def test_version_and_last_error(libtadmm):
 
 def _create_rc(tg, batch, **opt):
     hb = tg._HostBatch(batch)
-    o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0, 0, 0)
+    ae, am, at = opt.get("adapt", (0, 10.0, 2.0))
+    o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0, 0, 0,
+                        ae, am, at)
     h = C.c_void_p()
     rc = tg.lib().tadmm_create(C.byref(hb.s), C.byref(o), C.byref(h))
     return rc, tg.lib().tadmm_last_error().decode()
 
 
-@pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec"])
+@pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec", "adapt_mode", "adapt_mu"])
 def test_invalid_inputs_rejected_on_host(libtadmm, fault):
     tg, _ = libtadmm
     from instances import make_workload
@@ -71,6 +73,11 @@ def test_invalid_inputs_rejected_on_host(libtadmm, fault):
         b.N = np.array([0], dtype=np.int32)
     elif fault == "prec":
         opt["precision"] = 16
+    elif fault == "adapt_mode":   # residual balancing runs in the batched mode only
+        opt["mode"] = 1
+        opt["adapt"] = (5, 10.0, 2.0)
+    elif fault == "adapt_mu":
+        opt["adapt"] = (5, 1.0, 2.0)
     rc, msg = _create_rc(tg, b, **opt)
     assert rc == tg.EINVAL, msg
     assert msg

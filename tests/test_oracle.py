@@ -312,6 +312,36 @@ def test_admm_converges_to_global_qp():
     assert r["inv_dev"] <= 1e-10
 
 
+def test_residual_balancing_keeps_the_fixed_point():
+    """Residual balancing of rho (Boyd et al. 2011, Sec. 3.4.1; an extension,
+    off by default) changes the path, not the answer: started at a rho far
+    from balanced, rho is changed several times and the run still converges to
+    the global QP optimum, with the halfspace multipliers equal to
+    rho_final * theta and the scaled-dual identity y = -theta a intact."""
+    b = random_scenario(seed=3, N=3, T=8, box=1.5, rho=0.5)
+    g = oracle.global_qp(b, 0)
+    assert g["status"] == oracle.CONVERGED and g["act_h"].sum() > 0
+    r = oracle.admm(b, 0, tol=1e-10, max_iter=20000, adapt=(5, 10.0, 2.0))
+    assert r["status"] == oracle.CONVERGED
+    assert r["rho_changes"] >= 2
+    assert np.abs(r["X"] - g["X"]).max() <= 1e-7
+    assert np.abs(r["rho_final"] * r["theta"] - g["mu_h"]).max() <= 1e-5 * max(1, g["mu_h"].max())
+    assert np.array_equal(r["W"], g["W"])
+    assert r["inv_dev"] <= 1e-10
+    # rho_final is rho times tau to the net number of raises
+    k = np.log(r["rho_final"] / b.rho[0]) / np.log(2.0)
+    assert abs(k - round(k)) < 1e-12 and abs(round(k)) <= r["rho_changes"]
+
+
+def test_residual_balancing_never_due_is_plain_admm():
+    """With the first balancing point past max_iter the run is the plain one, bit for bit."""
+    b = random_scenario(seed=3, N=3, T=8, box=1.5, rho=0.5)
+    r0 = oracle.admm(b, 0, tol=0.0, max_iter=30)
+    r1 = oracle.admm(b, 0, tol=0.0, max_iter=30, adapt=(31, 10.0, 2.0))
+    assert r1["rho_changes"] == 0 and r1["rho_final"] == b.rho[0]
+    assert np.array_equal(r0["X"], r1["X"]) and np.array_equal(r0["theta"], r1["theta"])
+
+
 def test_literal_reading_is_infeasible_and_does_not_converge():
     """Zero initial velocity with c = 1 guess lines (the literal reading): the
     agents cannot swap sides in 2 s, the halfspace QP is infeasible and the
