@@ -399,6 +399,10 @@ def extras(tg, torch, batch, args):
     out["fp32"]["note"] = "float32 arithmetic, same workload; parity 1e-4 against the float64 oracle"
     out["double_float"] = timed_solves(tg, torch, batch, args, precision=64, flags=tg.FLAG_DOUBLE_FLOAT)
     out["double_float"]["note"] = "float64-grade double-float arithmetic on the FP32 pipe (parity 1e-9)"
+    out["residual_balancing"] = timed_solves(tg, torch, batch, args, precision=64, adapt=(10, 10.0, 2.0))
+    out["residual_balancing"]["note"] = ("rho balanced every 10 iterations (mu 10, tau 2; Boyd et al. 2011, "
+                                         "Sec. 3.4.1), an extension beyond the fixed rho = 1 of the workload; "
+                                         "parity against the oracle's balancing 1e-9")
     # one 512-agent 3D scenario (130816 pairs x 40 steps): graph mode vs plain mode per iteration
     from instances import make_workload
     sw = make_workload("swarm3d")
