@@ -153,6 +153,18 @@ int tadmm_get_solution(tadmm_handle* h, double* X, double* U, double* theta, int
  * fact [n_scen] Riccati stage factorizations, pairsteps processed. */
 int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pairsteps);
 
+/* Outer linearize-and-solve step (the collision constraint |p_i - p_j| >= d_min
+ * enters the QP as a halfspace linearized about a guess, Sec. III; repeating
+ * the linearization at each solution gives a sequential-QP loop; this step is
+ * an extension beyond the single linearized QP).  Replaces, on the device, every scenario's halfspace normals
+ * by a_ijt = (p_it - p_jt) / |p_it - p_jt| at the final iterate of the last
+ * solve (unchanged where the positions coincide; float64, correctly rounded
+ * operations) and the initial consensus positions w0 by that iterate's
+ * positions; the next tadmm_solve solves the re-linearized QP.  Asynchronous
+ * on `stream`; ESTATE before the first solve.  tadmm_update restores the
+ * caller's data. */
+int tadmm_relinearize(tadmm_handle* h, void* stream);
+
 /* Penalty of each scenario at the end of the last solve and the number of
  * times residual balancing changed it (host buffers, synchronous; either may
  * be NULL).  Without residual balancing: the input rho and 0. */

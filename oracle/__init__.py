@@ -270,3 +270,35 @@ def global_gradient(batch, k: int, act_h, W, targets, qf_tie=10.0):
     if rc != 0:
         raise RuntimeError(f"gradient failed ({rc})")
     return dict(X=X, U=U, loss=float(loss[0]), gQ=gQ, gR=gR, gGoal=gG)
+
+
+def relinearize(batch, X_list):
+    """One outer step of a linearize-and-solve loop over the collision
+    constraint |p_i - p_j| >= d_min (its halfspace linearization, Sec. III):
+    returns a copy of `batch` whose normals are a_ijt = (p_it - p_jt) /
+    |p_it - p_jt| at the positions of X_list[k] ([N, T+1, nx] per scenario;
+    unchanged where the positions coincide) and whose initial consensus
+    positions w0 are those positions.  Plain numpy: |d|^2 summed component by
+    component, then sqrt and division, each correctly rounded."""
+    import dataclasses
+    a = batch.a.copy()
+    w0 = batch.w0.copy()
+    po, so, dp = batch.pairstep_off, batch.agentstep_off, batch.dp
+    for k in range(batch.n_scen):
+        X = np.asarray(X_list[k], dtype=np.float64)
+        N, T = int(batch.N[k]), int(batch.T[k])
+        pos = X[:, 1:, :dp]                                  # [N, T, dp]
+        w0[so[k]:so[k + 1]] = pos.reshape(N * T, dp)
+        pk = 0
+        for i in range(N):
+            for j in range(i + 1, N):
+                d = pos[i] - pos[j]                          # [T, dp]
+                n2 = d[:, 0] * d[:, 0]
+                for c in range(1, dp):
+                    n2 = n2 + d[:, c] * d[:, c]
+                ok = n2 > 0.0
+                nr = np.sqrt(np.where(ok, n2, 1.0))
+                rows = a[po[k] + pk * T: po[k] + (pk + 1) * T]
+                rows[ok] = d[ok] / nr[ok, None]
+                pk += 1
+    return dataclasses.replace(batch, a=a, w0=w0)

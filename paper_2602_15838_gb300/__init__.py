@@ -63,6 +63,7 @@ def lib():
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_get_counters.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
         L.tadmm_get_penalty.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+        L.tadmm_relinearize.argtypes = [C.c_void_p, C.c_void_p]
         L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p, _i32p]
         L.tadmm_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -224,6 +225,12 @@ class Solver:
         _check(lib().tadmm_get_counters(self.h, eqp.ctypes.data_as(_i64p), fact.ctypes.data_as(_i64p),
                                         ps.ctypes.data_as(_i64p)), "tadmm_get_counters")
         return dict(eqp=eqp, fact=fact, pairsteps=ps)
+
+    def relinearize(self, stream=None):
+        """Re-linearizes every scenario's collision halfspaces (and the initial
+        consensus positions) at the last solution; the next solve() solves the
+        new QP (one outer step of a linearize-and-solve loop)."""
+        _check(lib().tadmm_relinearize(self.h, C.c_void_p(_stream_ptr(stream))), "tadmm_relinearize")
 
     def penalty(self):
         """Final rho per scenario and the number of residual-balancing changes."""

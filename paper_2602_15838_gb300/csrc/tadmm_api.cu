@@ -481,6 +481,13 @@ extern "C" int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, 
   return TADMM_OK;
 }
 
+extern "C" int tadmm_relinearize(tadmm_handle* h, void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!h->solved) return set_error(TADMM_ESTATE, "relinearize before solve");
+  cudaStream_t st = (cudaStream_t)stream;
+  TADMM_DISPATCH(h, relinearize(h, st));
+}
+
 extern "C" int tadmm_get_penalty(tadmm_handle* h, double* rho_final, int32_t* rho_changes) {
   if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
   if (!h->solved) return set_error(TADMM_ESTATE, "get_penalty before solve");

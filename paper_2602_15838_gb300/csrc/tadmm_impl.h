@@ -116,6 +116,7 @@ struct Impl {
   static int max_ctas_per_sm(int tpc, int variant, const tadmm_handle* h);
   static int backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev, double* xpol_dev,
                       cudaStream_t st);
+  static int relinearize(tadmm_handle* h, cudaStream_t st);
 };
 
 }  // namespace tadmm

@@ -333,6 +333,55 @@ __global__ void k_import_a(const ScenMeta* __restrict__ meta, const int32_t* __r
   }
 }
 
+// Re-linearization of the collision constraints around the final iterate of
+// the last solve (one outer step of a sequential-QP loop over the halfspace
+// linearization of Sec. III): a_ijt = (p_it - p_jt) / |p_it - p_jt| from that iterate's
+// positions, unchanged where the two positions coincide.  Formed in float64
+// with correctly rounded operations (no contraction), as in the oracle.
+template <typename F, int NX, int DP>
+__global__ void k_relin_a(Dev<F> D, F* __restrict__ a_out, const int32_t* __restrict__ pair_scen,
+                          int64_t tot_pairs) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tm1 = blockIdx.y;
+  if (gp >= tot_pairs) return;
+  const int sc = pair_scen[gp];
+  const ScenMeta s = D.meta[sc];
+  if (tm1 >= s.T) return;
+  const int lp = (int)(gp - s.pair_off);
+  const int pk = D.pairs[s.pair_off + lp];
+  const int i = pk & 0xFFFF, j = pk >> 16;
+  const F* X = D.X + (size_t)(D.cur_lvl[sc] & 1) * D.tot_xs * NX + s.xs_off * NX;
+  double dd[DP];
+#pragma unroll
+  for (int c = 0; c < DP; ++c) {
+    const size_t ro = ((size_t)(tm1 + 1) * NX + c) * s.N;
+    dd[c] = __dadd_rn(double(X[ro + i]), -double(X[ro + j]));
+  }
+  double n2 = __dmul_rn(dd[0], dd[0]);
+#pragma unroll
+  for (int c = 1; c < DP; ++c) n2 = __dadd_rn(n2, __dmul_rn(dd[c], dd[c]));
+  if (!(n2 > 0.0)) return;
+  const double nr = __dsqrt_rn(n2);
+#pragma unroll
+  for (int c = 0; c < DP; ++c) a_out[s.ps_off * DP + ((size_t)tm1 * DP + c) * s.P + lp] = F(__ddiv_rn(dd[c], nr));
+}
+
+// The next solve's initial consensus positions: the final iterate's positions.
+template <typename F, int NX, int DP>
+__global__ void k_relin_w0(Dev<F> D, F* __restrict__ w0_out, const int32_t* __restrict__ agent_scen,
+                           int64_t tot_agents) {
+  const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ga >= tot_agents) return;
+  const int sc = agent_scen[ga];
+  const ScenMeta s = D.meta[sc];
+  const int i = (int)(ga - s.agent_off);
+  const F* X = D.X + (size_t)(D.cur_lvl[sc] & 1) * D.tot_xs * NX + s.xs_off * NX;
+  for (int tm1 = 0; tm1 < s.T; ++tm1)
+#pragma unroll
+    for (int c = 0; c < DP; ++c)
+      w0_out[s.as_off * DP + ((size_t)tm1 * DP + c) * s.N + i] = X[((size_t)(tm1 + 1) * NX + c) * s.N + i];
+}
+
 // w0: caller [agent-step][dp] (agent-major, then t) -> internal [T][DP][N]
 template <typename F, int DP>
 __global__ void k_import_w0(const ScenMeta* __restrict__ meta, const int32_t* __restrict__ agent_scen,
@@ -486,6 +535,19 @@ int Impl<F, NX, NU, DP>::import_inputs(tadmm_handle* h, cudaStream_t st) {
                                                                     h->tot_pairs);
   k_import_w0<F, DP><<<grid_for(na, 128), 128, 0, st>>>(h->meta, h->agent_scen, h->st_w0, (F*)h->w0, na);
   return cuda_check(cudaGetLastError(), "import kernels");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::relinearize(tadmm_handle* h, cudaStream_t st) {
+  Dev<F> D = make_dev<F>(h);
+  int tmax = 0;
+  for (const ScenMeta& m : h->meta_h) tmax = std::max(tmax, m.T);
+  if (h->tot_pairs > 0)
+    k_relin_a<F, NX, DP><<<dim3(grid_for(h->tot_pairs, 128, 1 << 30), tmax), 128, 0, st>>>(D, (F*)h->a, h->pair_scen,
+                                                                                          h->tot_pairs);
+  k_relin_w0<F, NX, DP><<<grid_for(h->tot_agents, 128, 1 << 30), 128, 0, st>>>(D, (F*)h->w0, h->agent_scen,
+                                                                              h->tot_agents);
+  return cuda_check(cudaGetLastError(), "relinearization kernels");
 }
 
 template <typename F, int NX, int NU, int DP>

@@ -426,3 +426,42 @@ def test_residual_balancing_faster_convergence(tg):
         o = oracle.admm(b, int(k), tol=1e-4, max_iter=500, adapt=(10, 10.0, 2.0))
         assert o["status"] == oracle.CONVERGED and o["iters"] == g[k]["iters"], k
         assert rel(g[k]["X"], o["X"]) <= 1e-6, k
+
+
+def test_relinearized_solve_matches_oracle(tg):
+    """One outer linearize-and-solve step: solve, re-linearize the collision
+    halfspaces at the solution on the device (C ABI), solve again; against the
+    oracle doing the same (numpy normals from its own positions, then its
+    ADMM).  Then three outer steps on the 2-agent crossing at tol 1e-4: the
+    sequence matches the oracle's and ends with the agents at least d_min
+    apart up to the tolerance at every step."""
+    b = make_workload("mixed", n_scen=6)
+    s = tg.Solver(b)
+    s.solve(0.0, 15)
+    s.relinearize()
+    s.solve(0.0, 15)
+    g2 = s.split(s.solution())
+    s.close()
+    o1 = [oracle.admm(b, k, tol=0.0, max_iter=15) for k in range(b.n_scen)]
+    b2 = oracle.relinearize(b, [o["X"] for o in o1])
+    for k in range(b.n_scen):
+        o2 = oracle.admm(b2, k, tol=0.0, max_iter=15)
+        assert rel(g2[k]["X"], o2["X"]) <= 1e-8, k
+        assert rel(g2[k]["theta"], o2["theta"]) <= 1e-8, k
+
+    p = make_workload("pair")
+    s = tg.Solver(p)
+    bo = p
+    for outer in range(3):
+        if outer:
+            s.relinearize()
+        s.solve(1e-4, 500)
+        g = s.split(s.solution())[0]
+        o = oracle.admm(bo, 0, tol=1e-4, max_iter=500)
+        assert g["status"] == tg.CONVERGED and o["status"] == oracle.CONVERGED
+        assert g["iters"] == o["iters"], outer
+        assert rel(g["X"], o["X"]) <= 1e-6, outer
+        bo = oracle.relinearize(bo, [o["X"]])
+    s.close()
+    dist = np.linalg.norm(g["X"][0, 1:, :2] - g["X"][1, 1:, :2], axis=-1)
+    assert dist.min() >= p.d_min[0] - 1e-3

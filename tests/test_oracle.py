@@ -342,6 +342,32 @@ def test_residual_balancing_never_due_is_plain_admm():
     assert np.array_equal(r0["X"], r1["X"]) and np.array_equal(r0["theta"], r1["theta"])
 
 
+def test_relinearization_at_the_guess_reproduces_the_normals():
+    """Re-linearizing at the guess lines (the zero-input trajectories the
+    instances are built from) gives back the instance's own halfspace normals
+    and consensus guess: unit normals pointing from p_j to p_i, with
+    a . (p_i - p_j) = |p_i - p_j|."""
+    b = make_workload("mixed", n_scen=3)
+    X_list = []
+    for k in range(b.n_scen):
+        sc = b.scenario(k)
+        N, T = int(sc.N[0]), int(sc.T[0])
+        X = np.zeros((N, T + 1, b.nx))
+        X[:, 1:, :b.dp] = sc.w0.reshape(N, T, b.dp)
+        X_list.append(X)
+    r = oracle.relinearize(b, X_list)
+    assert np.abs(r.a - b.a).max() <= 1e-15
+    assert np.array_equal(r.w0, b.w0)
+    assert np.abs(np.linalg.norm(r.a, axis=1) - 1.0).max() <= 1e-15
+    k = 2
+    sc = b.scenario(k)
+    N, T = int(sc.N[0]), int(sc.T[0])
+    pos = sc.w0.reshape(N, T, b.dp)
+    a = r.scenario(k).a.reshape(-1, T, b.dp)
+    d = pos[0] - pos[1]
+    assert np.abs((a[0] * d).sum(-1) - np.linalg.norm(d, axis=-1)).max() <= 1e-14
+
+
 def test_literal_reading_is_infeasible_and_does_not_converge():
     """Zero initial velocity with c = 1 guess lines (the literal reading): the
     agents cannot swap sides in 2 s, the halfspace QP is infeasible and the
