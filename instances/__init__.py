@@ -15,4 +15,5 @@ from .generator import (  # noqa: F401
     pair_list,
     random_scenario,
     build_scenario,
+    nearest_neighbour_pairs,
 )

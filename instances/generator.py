@@ -127,6 +127,11 @@ class Batch:
     rho: np.ndarray
     targets: Optional[np.ndarray] = None
     meta: dict = dataclasses.field(default_factory=dict)
+    # coupled pairs: None = all pairs of every scenario (lexicographic); else
+    # pair_count [n_scen] and pair_ij [sum pair_count, 2] (i < j), and the
+    # pair-step rows of `a` follow this list
+    pair_count: Optional[np.ndarray] = None
+    pair_ij: Optional[np.ndarray] = None
 
     @property
     def n_scen(self) -> int:
@@ -134,7 +139,20 @@ class Batch:
 
     @property
     def P(self) -> np.ndarray:
+        if self.pair_count is not None:
+            return self.pair_count.astype(np.int64)
         return (self.N.astype(np.int64) * (self.N - 1)) // 2
+
+    @property
+    def pair_off(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.P)])
+
+    def pairs_of(self, k: int) -> np.ndarray:
+        """[P_k, 2] coupled pairs of scenario k."""
+        if self.pair_ij is None:
+            return pair_list(int(self.N[k]))
+        po = self.pair_off
+        return self.pair_ij[po[k]:po[k + 1]]
 
     @property
     def agent_off(self) -> np.ndarray:
@@ -164,6 +182,8 @@ class Batch:
             d_min=self.d_min[list(idx)].copy(), rho=self.rho[list(idx)].copy(),
             targets=None if self.targets is None else cat(self.targets, so),
             meta=dict(self.meta),
+            pair_count=None if self.pair_count is None else self.pair_count[list(idx)].copy(),
+            pair_ij=None if self.pair_ij is None else cat(self.pair_ij, self.pair_off),
         )
 
     def contiguous(self) -> "Batch":
@@ -243,6 +263,34 @@ def build_scenario(starts: np.ndarray, goals: np.ndarray, T: int, dt: float, d_m
         a = np.zeros((0, dp))
     w0 = g.reshape(-1, dp)
     return x_init, x_ref, a, w0, c
+
+
+def nearest_neighbour_pairs(batch: Batch, k: int) -> Batch:
+    """Sparse coupling: each agent keeps the pairs to its k nearest agents at
+    t = 0 (the union over both ends, i < j, lexicographic), the rest of the
+    instance unchanged (the normals of the kept pairs are the dense ones)."""
+    counts, lists, a_rows = [], [], []
+    po = batch.pairstep_off
+    for s in range(batch.n_scen):
+        N, T = int(batch.N[s]), int(batch.T[s])
+        x0 = batch.x_init[batch.agent_off[s]:batch.agent_off[s + 1], :batch.dp]
+        keep = np.zeros((N, N), dtype=bool)
+        if N > 1:
+            d = np.sqrt(((x0[:, None, :] - x0[None, :, :]) ** 2).sum(-1))
+            np.fill_diagonal(d, np.inf)
+            for i in range(N):
+                for j in np.argsort(d[i], kind="stable")[:min(k, N - 1)]:
+                    keep[min(i, int(j)), max(i, int(j))] = True
+        dense = pair_list(N)
+        sel = np.array([keep[i, j] for i, j in dense], dtype=bool) if len(dense) else np.zeros(0, dtype=bool)
+        lists.append(dense[sel])
+        counts.append(int(sel.sum()))
+        a_s = batch.a[po[s]:po[s + 1]].reshape(len(dense), T, batch.dp) if len(dense) else np.zeros((0, T, batch.dp))
+        a_rows.append(a_s[sel].reshape(-1, batch.dp))
+    return dataclasses.replace(batch, a=np.concatenate(a_rows) if a_rows else batch.a[:0],
+                               pair_count=np.asarray(counts, dtype=np.int32),
+                               pair_ij=(np.concatenate(lists).astype(np.int32) if lists else
+                                        np.zeros((0, 2), dtype=np.int32)))
 
 
 WORKLOADS = {"pair": 1, "ring14": 2, "mixed": 3, "swarm3d": 4, "diff": 5}

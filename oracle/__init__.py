@@ -36,7 +36,8 @@ class Scenario(C.Structure):
     _fields_ = [("N", C.c_int), ("T", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("dp", C.c_int),
                 ("A", _dp), ("B", _dp), ("Qd", _dp), ("Rd", _dp), ("Qfd", _dp),
                 ("x_init", _dp), ("x_ref", _dp), ("umin", _dp), ("umax", _dp),
-                ("a", _dp), ("w0", _dp), ("d_min", C.c_double), ("rho", C.c_double)]
+                ("a", _dp), ("w0", _dp), ("d_min", C.c_double), ("rho", C.c_double),
+                ("P", C.c_int), ("pairs", C.POINTER(C.c_int))]
 
 
 class Options(C.Structure):
@@ -152,18 +153,23 @@ class _ScenarioData:
         N, T = int(batch.N[k]), int(batch.T[k])
         sl = lambda arr, off: np.ascontiguousarray(arr[off[k]:off[k + 1]], dtype=np.float64)
         self.N, self.T, self.nx, self.nu, self.dp = N, T, batch.nx, batch.nu, batch.dp
-        self.P = N * (N - 1) // 2
+        self.P = int(batch.P[k])
         self.keep = dict(A=_f64(batch.A), B=_f64(batch.B), Qd=sl(batch.Qd, ao), Rd=sl(batch.Rd, ao),
                          Qfd=sl(batch.Qfd, ao), x_init=sl(batch.x_init, ao), x_ref=sl(batch.x_ref, ao),
                          umin=_f64(batch.umin), umax=_f64(batch.umax), a=sl(batch.a, po),
                          w0=sl(batch.w0, so))
         if self.keep["a"].size == 0:
             self.keep["a"] = np.zeros(1)
+        listed = getattr(batch, "pair_ij", None) is not None
+        if listed:
+            pl = np.ascontiguousarray(batch.pairs_of(k), dtype=np.int32).reshape(-1)
+            self.keep["pairs"] = pl if pl.size else np.zeros(2, dtype=np.int32)
         kp = self.keep
         self.s = Scenario(N, T, batch.nx, batch.nu, batch.dp, _d(kp["A"]), _d(kp["B"]), _d(kp["Qd"]),
                           _d(kp["Rd"]), _d(kp["Qfd"]), _d(kp["x_init"]), _d(kp["x_ref"]),
                           _d(kp["umin"]), _d(kp["umax"]), _d(kp["a"]), _d(kp["w0"]),
-                          float(batch.d_min[k]), float(batch.rho[k]))
+                          float(batch.d_min[k]), float(batch.rho[k]), self.P,
+                          kp["pairs"].ctypes.data_as(C.POINTER(C.c_int)) if listed else None)
 
 
 class _ResultData:
@@ -289,16 +295,13 @@ def relinearize(batch, X_list):
         N, T = int(batch.N[k]), int(batch.T[k])
         pos = X[:, 1:, :dp]                                  # [N, T, dp]
         w0[so[k]:so[k + 1]] = pos.reshape(N * T, dp)
-        pk = 0
-        for i in range(N):
-            for j in range(i + 1, N):
-                d = pos[i] - pos[j]                          # [T, dp]
-                n2 = d[:, 0] * d[:, 0]
-                for c in range(1, dp):
-                    n2 = n2 + d[:, c] * d[:, c]
-                ok = n2 > 0.0
-                nr = np.sqrt(np.where(ok, n2, 1.0))
-                rows = a[po[k] + pk * T: po[k] + (pk + 1) * T]
-                rows[ok] = d[ok] / nr[ok, None]
-                pk += 1
+        for pk, (i, j) in enumerate(batch.pairs_of(k)):
+            d = pos[i] - pos[j]                              # [T, dp]
+            n2 = d[:, 0] * d[:, 0]
+            for c in range(1, dp):
+                n2 = n2 + d[:, c] * d[:, c]
+            ok = n2 > 0.0
+            nr = np.sqrt(np.where(ok, n2, 1.0))
+            rows = a[po[k] + pk * T: po[k] + (pk + 1) * T]
+            rows[ok] = d[ok] / nr[ok, None]
     return dataclasses.replace(batch, a=a, w0=w0)

@@ -315,6 +315,33 @@ int orc_agent_bruteforce(const orc_agent_qp* q, double tol, double* u, int8_t* W
 /* ADMM (Sec. III.B, IV.A), literal per-side vector form                       */
 /* ------------------------------------------------------------------------- */
 
+/* Coupled pairs of a scenario as an [P][2] list (all pairs, lexicographic, when
+ * none are listed) and an N x N table of pair indices (-1: not coupled).
+ * Both malloc'd; returns P, or -1 on allocation failure. */
+static int scen_pairs(const orc_scenario* s, int** list_out, int** table_out) {
+  const int N = s->N;
+  const int P = s->pairs ? s->P : N * (N - 1) / 2;
+  int* list = (int*)malloc(sizeof(int) * (2 * (size_t)P + 2));
+  int* table = (int*)malloc(sizeof(int) * ((size_t)N * N + 1));
+  if (!list || !table) { free(list); free(table); return -1; }
+  for (size_t k = 0; k < (size_t)N * N; ++k) table[k] = -1;
+  if (s->pairs) {
+    for (int k = 0; k < P; ++k) { list[2 * k] = s->pairs[2 * k]; list[2 * k + 1] = s->pairs[2 * k + 1]; }
+  } else {
+    int k = 0;
+    for (int i = 0; i < N; ++i)
+      for (int j = i + 1; j < N; ++j, ++k) { list[2 * k] = i; list[2 * k + 1] = j; }
+  }
+  for (int k = 0; k < P; ++k) {
+    const int i = list[2 * k], j = list[2 * k + 1];
+    table[(size_t)i * N + j] = k;
+    table[(size_t)j * N + i] = k;
+  }
+  *list_out = list;
+  *table_out = table;
+  return P;
+}
+
 static inline int pair_index(int N, int i, int j) { /* i < j, lexicographic */
   return i * N - (i * (i + 1)) / 2 + (j - i - 1);
 }
@@ -346,7 +373,11 @@ int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, 
   double* Hx = (double*)malloc(sizeof(double) * (size_t)T * nx);
   double* gx = (double*)malloc(sizeof(double) * (size_t)T * nx);
   double Hu[16];
-  const int nc = N - 1;
+  int nc = N - 1;
+  if (s->pairs) {
+    nc = 0;
+    for (int k = 0; k < s->P; ++k) nc += (s->pairs[2 * k] == i) + (s->pairs[2 * k + 1] == i);
+  }
   const double* Qi = s->Qd + (size_t)i * nx;
   const double* Qfi = s->Qfd + (size_t)i * nx;
   const double* xr = s->x_ref + (size_t)i * nx;
@@ -373,7 +404,9 @@ int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, 
 
 int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   const int N = s->N, T = s->T, nx = s->nx, nu = s->nu, dp = s->dp;
-  const int P = N * (N - 1) / 2;
+  int *plist = NULL, *ptab = NULL;
+  const int P = scen_pairs(s, &plist, &ptab);
+  if (P < 0) { res->status = ORC_NUMERIC; return -1; }
   const size_t PS = (size_t)P * T * dp;
   double* wi = (double*)malloc(sizeof(double) * (PS + 1));
   double* wj = (double*)malloc(sizeof(double) * (PS + 1));
@@ -390,13 +423,12 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   res->s = INFINITY;
   res->inv_dev = 0.0;
   if (!wi || !wj || !yi || !yj || !pos) {
-    free(wi); free(wj); free(yi); free(yj); free(pos);
+    free(wi); free(wj); free(yi); free(yj); free(pos); free(plist); free(ptab);
     res->status = ORC_NUMERIC;
     return -1;
   }
-  for (int i = 0; i < N; ++i)
-    for (int j = i + 1; j < N; ++j) {
-      int pk = pair_index(N, i, j);
+  for (int pk = 0; pk < P; ++pk) {
+      const int i = plist[2 * pk], j = plist[2 * pk + 1];
       for (int t = 0; t < T; ++t)
         for (int c = 0; c < dp; ++c) {
           wi[((size_t)pk * T + t) * dp + c] = s->w0[((size_t)i * T + t) * dp + c];
@@ -417,7 +449,8 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
       double* h = (double*)calloc((size_t)T * dp, sizeof(double));
       for (int j = 0; j < N; ++j) {
         if (j == i) continue;
-        int pk = (i < j) ? pair_index(N, i, j) : pair_index(N, j, i);
+        const int pk = ptab[(size_t)i * N + j];
+        if (pk < 0) continue;
         const double* w = (i < j) ? wi : wj;
         const double* y = (i < j) ? yi : yj;
         for (int t = 0; t < T; ++t)
@@ -445,9 +478,8 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
 
     /* --- consensus projection and scaled dual update, per pair and step --- */
     double r = 0.0, sd = 0.0, dev = res->inv_dev;
-    for (int i = 0; i < N; ++i)
-      for (int j = i + 1; j < N; ++j) {
-        int pk = pair_index(N, i, j);
+    for (int pk = 0; pk < P; ++pk) {
+        const int i = plist[2 * pk], j = plist[2 * pk + 1];
         for (int t = 0; t < T; ++t) {
           size_t o2 = ((size_t)pk * T + t) * dp;
           const double* a = s->a + o2;
@@ -500,7 +532,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   }
   res->rho_final = sc.rho;
   res->as_iters = as_total;
-  free(wi); free(wj); free(yi); free(yj); free(pos);
+  free(wi); free(wj); free(yi); free(yj); free(pos); free(plist); free(ptab);
   return 0;
 }
 
@@ -554,7 +586,11 @@ static void matmul(int n, int k, int m, const double* X, const double* Y, double
 static int global_build(const orc_scenario* s, global_qp* Q) {
   const int N = s->N, T = s->T, nx = s->nx, nu = s->nu, dp = s->dp;
   Q->N = N; Q->T = T; Q->nx = nx; Q->nu = nu; Q->dp = dp;
-  Q->P = N * (N - 1) / 2; Q->m = T * nu; Q->nU = N * Q->m; Q->nC = 2 * Q->nU + Q->P * T;
+  int *plist = NULL, *ptab = NULL;
+  Q->P = scen_pairs(s, &plist, &ptab);
+  if (Q->P < 0) return -1;
+  free(ptab);
+  Q->m = T * nu; Q->nU = N * Q->m; Q->nC = 2 * Q->nU + Q->P * T;
   Q->Phi = (double*)calloc((size_t)(T + 1) * nx * nx, sizeof(double));
   Q->G = (double*)calloc((size_t)T * T * nx * nu, sizeof(double));
   Q->H = (double*)calloc((size_t)Q->nU * Q->nU, sizeof(double));
@@ -612,9 +648,8 @@ static int global_build(const orc_scenario* s, global_qp* Q) {
   }
   /* halfspace rows: a'(C x_it - C x_jt) >= d */
   int row = 2 * nU;
-  for (int i = 0; i < N; ++i)
-    for (int j = i + 1; j < N; ++j) {
-      int pk = pair_index(N, i, j);
+  for (int pk = 0; pk < Q->P; ++pk) {
+      const int i = plist[2 * pk], j = plist[2 * pk + 1];
       for (int t = 1; t <= T; ++t, ++row) {
         const double* a = s->a + ((size_t)pk * T + (t - 1)) * dp;
         double* nr = Q->Nc + (size_t)row * nU;
@@ -637,6 +672,7 @@ static int global_build(const orc_scenario* s, global_qp* Q) {
       }
     }
   free(xf);
+  free(plist);
   return 0;
 }
 

@@ -68,9 +68,13 @@ typedef struct {
   const double *Qd, *Rd, *Qfd;         /* [N][nx], [N][nu], [N][nx] */
   const double *x_init, *x_ref;        /* [N][nx] */
   const double *umin, *umax;           /* [nu] */
-  const double *a;                     /* [P][T][dp], P = N(N-1)/2, t = 1..T */
+  const double *a;                     /* [P][T][dp] in pair order, t = 1..T */
   const double *w0;                    /* [N][T][dp] initial consensus positions */
   double d_min, rho;
+  int P;                               /* number of listed pairs (ignored when pairs is NULL) */
+  const int *pairs;                    /* [P][2] coupled pairs (i < j); NULL: all N(N-1)/2 pairs in
+                                          lexicographic order.  Agent i's copy count n_c is its
+                                          number of pairs. */
 } orc_scenario;
 
 typedef struct {

@@ -9,6 +9,8 @@ Sec. V.A (Table 1).
 """
 import os
 
+import dataclasses
+
 import numpy as np
 import pytest
 from scipy.optimize import lsq_linear, minimize
@@ -366,6 +368,34 @@ def test_relinearization_at_the_guess_reproduces_the_normals():
     a = r.scenario(k).a.reshape(-1, T, b.dp)
     d = pos[0] - pos[1]
     assert np.abs((a[0] * d).sum(-1) - np.linalg.norm(d, axis=-1)).max() <= 1e-14
+
+
+def test_pair_list_of_all_pairs_is_the_dense_run():
+    """Listing every pair explicitly (lexicographic) is the dense all-pairs run, bit for bit."""
+    from instances import pair_list
+    b = make_workload("mixed", n_scen=2)
+    r0 = [oracle.admm(b, k, tol=0.0, max_iter=6) for k in range(2)]
+    bl = dataclasses.replace(b, pair_count=b.P.astype(np.int32),
+                             pair_ij=np.concatenate([pair_list(int(n)) for n in b.N]))
+    for k in range(2):
+        r1 = oracle.admm(bl, k, tol=0.0, max_iter=6)
+        assert np.array_equal(r0[k]["X"], r1["X"]) and np.array_equal(r0[k]["theta"], r1["theta"])
+
+
+def test_sparse_coupling_converges_to_its_global_qp():
+    """Coupling only each agent's nearest neighbours: the ADMM fixed point is the
+    centralized optimum of the QP with just those halfspaces, each agent's
+    copy count n_c being its number of pairs (a wrong count moves the fixed
+    point); the halfspace multipliers are rho * theta."""
+    from instances import nearest_neighbour_pairs
+    b = nearest_neighbour_pairs(random_scenario(seed=10, N=5, T=8, box=1.5, rho=20.0), 2)
+    assert 0 < int(b.P[0]) < 10
+    g = oracle.global_qp(b, 0)
+    assert g["status"] == oracle.CONVERGED and g["act_h"].sum() > 0
+    r = oracle.admm(b, 0, tol=1e-10, max_iter=40000)
+    assert r["status"] == oracle.CONVERGED
+    assert np.abs(r["X"] - g["X"]).max() <= 1e-7
+    assert np.abs(b.rho[0] * r["theta"] - g["mu_h"]).max() <= 1e-5 * max(1, g["mu_h"].max())
 
 
 def test_literal_reading_is_infeasible_and_does_not_converge():
