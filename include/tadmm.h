@@ -63,7 +63,7 @@ extern "C" {
  * only during the call that receives them.  Arrays are packed scenario after
  * scenario in this order (P_s = N_s (N_s - 1) / 2):
  *   per agent  (sum N_s rows):          Qd, Qfd, x_init, x_ref [nx]; Rd [nu]
- *   per pair-step (sum P_s T_s rows):   a [dp], pairs (i<j) lexicographic, then t = 1..T
+ *   per pair-step (sum P_s T_s rows):   a [dp], pairs in pair order, then t = 1..T
  *   per agent-step (sum N_s T_s rows):  w0 [dp], agents, then t = 1..T          */
 typedef struct {
   int32_t n_scen;
@@ -83,6 +83,13 @@ typedef struct {
   const double* w0;      /* initial consensus position per agent-step (the guess) */
   const double* d_min;   /* [n_scen] */
   const double* rho;     /* [n_scen] ADMM penalty */
+  /* Coupled pairs (an extension: the paper couples all pairs).  NULL: every
+   * pair (i < j) of each scenario in lexicographic order, P_s = N_s(N_s-1)/2.
+   * Otherwise pair_count[s] = P_s pairs listed in pair_ij [sum P_s][2] (i < j,
+   * each pair at most once), scenario after scenario, in the order of the rows
+   * of `a`; agent i's number of consensus copies n_c is its number of pairs. */
+  const int32_t* pair_count;
+  const int32_t* pair_ij;
 } tadmm_batch;
 
 typedef struct {

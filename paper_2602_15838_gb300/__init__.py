@@ -32,7 +32,7 @@ class TadmmBatch(C.Structure):
     _fields_ = [("n_scen", C.c_int32), ("nx", C.c_int32), ("nu", C.c_int32), ("dp", C.c_int32),
                 ("N", _i32p), ("T", _i32p), ("A", _dp), ("B", _dp), ("umin", _dp), ("umax", _dp),
                 ("Qd", _dp), ("Rd", _dp), ("Qfd", _dp), ("x_init", _dp), ("x_ref", _dp), ("a", _dp),
-                ("w0", _dp), ("d_min", _dp), ("rho", _dp)]
+                ("w0", _dp), ("d_min", _dp), ("rho", _dp), ("pair_count", _i32p), ("pair_ij", _i32p)]
 
 
 class TadmmOptions(C.Structure):
@@ -109,10 +109,17 @@ class _HostBatch:
             ptr = {k: v.ctypes.data_as(_dp) for k, v in self.keep.items()}
         self.N = np.ascontiguousarray(batch.N, dtype=np.int32)
         self.T = np.ascontiguousarray(batch.T, dtype=np.int32)
+        listed = getattr(batch, "pair_ij", None) is not None
+        self.pc = np.ascontiguousarray(batch.pair_count, dtype=np.int32) if listed else None
+        self.pij = (np.ascontiguousarray(batch.pair_ij, dtype=np.int32).reshape(-1) if listed else None)
+        if listed and self.pij.size == 0:
+            self.pij = np.zeros(2, dtype=np.int32)
         self.s = TadmmBatch(int(batch.n_scen), batch.nx, batch.nu, batch.dp, self.N.ctypes.data_as(_i32p),
                             self.T.ctypes.data_as(_i32p), ptr["A"], ptr["B"], ptr["umin"], ptr["umax"],
                             ptr["Qd"], ptr["Rd"], ptr["Qfd"], ptr["x_init"], ptr["x_ref"],
-                            None if not batch.a.size else ptr["a"], ptr["w0"], ptr["d_min"], ptr["rho"])
+                            None if not batch.a.size else ptr["a"], ptr["w0"], ptr["d_min"], ptr["rho"],
+                            self.pc.ctypes.data_as(_i32p) if listed else None,
+                            self.pij.ctypes.data_as(_i32p) if listed else None)
 
 
 class Solver:

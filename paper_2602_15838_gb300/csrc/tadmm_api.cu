@@ -74,8 +74,36 @@ static int validate(const tadmm_batch* b, const tadmm_handle* shape) {
     if (!std::isfinite(b->d_min[s])) return set_error(TADMM_EINVAL, "d_min must be finite");
     if (!(b->rho[s] > 0.0) || !std::isfinite(b->rho[s])) return set_error(TADMM_EINVAL, "rho must be > 0");
     na += N;
-    nps += (int64_t)N * (N - 1) / 2 * T;
     nas += (int64_t)N * T;
+  }
+  if ((b->pair_count == nullptr) != (b->pair_ij == nullptr))
+    return set_error(TADMM_EINVAL, "pair_count and pair_ij are both NULL or both set");
+  {
+    int64_t po = 0;
+    std::vector<uint8_t> seen;
+    for (int s = 0; s < b->n_scen; ++s) {
+      const int64_t N = b->N[s], T = b->T[s];
+      int64_t P = N * (N - 1) / 2;
+      if (b->pair_count) {
+        if (b->pair_count[s] < 0 || b->pair_count[s] > P)
+          return set_error(TADMM_EINVAL, "scenario " + std::to_string(s) + ": pair_count out of range");
+        P = b->pair_count[s];
+        if (shape && shape->pair_count_h.size() && shape->pair_count_h[s] != P)
+          return set_error(TADMM_EINVAL, "update: pair lists differ from the handle");
+        seen.assign((size_t)(N * N), 0);
+        for (int64_t k = 0; k < P; ++k) {
+          const int32_t i = b->pair_ij[2 * (po + k)], j = b->pair_ij[2 * (po + k) + 1];
+          if (i < 0 || j <= i || j >= N) return set_error(TADMM_EINVAL, "pair_ij entries need 0 <= i < j < N");
+          if (seen[(size_t)i * N + j]++) return set_error(TADMM_EINVAL, "pair_ij lists a pair twice");
+        }
+      }
+      po += P;
+      nps += P * T;
+    }
+    if (shape && (shape->pair_count_h.empty() != (b->pair_count == nullptr)))
+      return set_error(TADMM_EINVAL, "update: pair lists differ from the handle");
+    if (shape && b->pair_ij && !std::equal(b->pair_ij, b->pair_ij + 2 * po, shape->pair_ij_h.begin()))
+      return set_error(TADMM_EINVAL, "update: pair lists differ from the handle");
   }
   if (nps > 0 && !b->a) return set_error(TADMM_EINVAL, "a is NULL but the batch has pairs");
   const int nx = b->nx, nu = b->nu, dp = b->dp;
@@ -128,7 +156,7 @@ static void free_all(tadmm_handle* h) {
   void* ptrs0[] = {h->goff, h->gmem, h->gorder};
   for (void* p : ptrs0)
     if (p) cudaFree(p);
-  void* ptrs[] = {h->meta,   h->order, h->pairs, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
+  void* ptrs[] = {h->meta,   h->order, h->pairs, h->deg, h->adj_ptr, h->adj, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
                   h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->X,      h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
                   h->res,    h->eqp,   h->fact,  h->rho_out, h->rho_chg, h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
@@ -234,13 +262,21 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   h->N.assign(b->N, b->N + b->n_scen);
   h->T.assign(b->T, b->T + b->n_scen);
   h->meta_h.resize(b->n_scen);
-  std::vector<int32_t> pairs, pair_scen, agent_scen;
+  std::vector<int32_t> pairs, pair_scen, agent_scen, deg, adj_ptr, adj;
+  if (b->pair_count) {
+    h->pair_count_h.assign(b->pair_count, b->pair_count + b->n_scen);
+    int64_t tp = 0;
+    for (int s = 0; s < b->n_scen; ++s) tp += b->pair_count[s];
+    h->pair_ij_h.assign(b->pair_ij, b->pair_ij + 2 * tp);
+  }
+  adj_ptr.push_back(0);
+  int64_t lpo = 0;  // offset of the scenario's listed pairs
   for (int s = 0; s < b->n_scen; ++s) {
     tadmm::ScenMeta& m = h->meta_h[s];
     m.N = h->N[s];
     m.T = h->T[s];
-    m.P = m.N * (m.N - 1) / 2;
-    m.pad = 0;
+    m.P = b->pair_count ? b->pair_count[s] : m.N * (m.N - 1) / 2;
+    m.sparse = b->pair_count ? 1 : 0;
     m.agent_off = h->tot_agents;
     m.as_off = h->tot_as;
     m.ps_off = h->tot_ps;
@@ -253,12 +289,35 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
     h->tot_ps += (int64_t)m.P * m.T;
     h->tot_xs += (int64_t)m.N * (m.T + 1);
     h->tot_pairs += m.P;
-    for (int i = 0; i < m.N; ++i) {
-      agent_scen.push_back(s);
-      for (int j = i + 1; j < m.N; ++j) {
+    if (!m.sparse) {
+      for (int i = 0; i < m.N; ++i) {
+        agent_scen.push_back(s);
+        deg.push_back(m.N - 1);
+        adj_ptr.push_back((int32_t)adj.size());
+        for (int j = i + 1; j < m.N; ++j) {
+          pairs.push_back(i | (j << 16));
+          pair_scen.push_back(s);
+        }
+      }
+    } else {
+      // listed pairs; per agent, its pairs by increasing partner (sign bit: the
+      // agent is the second of the pair)
+      std::vector<std::vector<std::pair<int, int32_t>>> inc(m.N);
+      for (int k = 0; k < m.P; ++k) {
+        const int i = b->pair_ij[2 * (lpo + k)], j = b->pair_ij[2 * (lpo + k) + 1];
         pairs.push_back(i | (j << 16));
         pair_scen.push_back(s);
+        inc[i].push_back({j, (int32_t)k});
+        inc[j].push_back({i, (int32_t)(k | 0x80000000u)});
       }
+      for (int i = 0; i < m.N; ++i) {
+        agent_scen.push_back(s);
+        std::sort(inc[i].begin(), inc[i].end());
+        deg.push_back((int32_t)inc[i].size());
+        for (const auto& e : inc[i]) adj.push_back(e.second);
+        adj_ptr.push_back((int32_t)adj.size());
+      }
+      lpo += m.P;
     }
   }
   // processing order of the persistent kernel: largest estimated work first
@@ -337,7 +396,8 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   if ((rc = dmalloc(&h->goff, 4 * goff.size())) || (rc = dmalloc(&h->gmem, 4 * gmem.size())) ||
       (rc = dmalloc(&h->gorder, 4 * order.size())) ||
       (rc = dmalloc(&h->meta, sizeof(tadmm::ScenMeta) * h->n_scen)) || (rc = dmalloc(&h->order, 4 * order.size())) ||
-      (rc = dmalloc(&h->pairs, 4 * pairs.size())) || (rc = dmalloc(&h->pair_scen, 4 * pair_scen.size())) ||
+      (rc = dmalloc(&h->pairs, 4 * pairs.size())) || (rc = dmalloc(&h->deg, 4 * deg.size())) ||
+      (rc = dmalloc(&h->adj_ptr, 4 * adj_ptr.size())) || (rc = dmalloc(&h->adj, 4 * std::max<size_t>(adj.size(), 1))) || (rc = dmalloc(&h->pair_scen, 4 * pair_scen.size())) ||
       (rc = dmalloc(&h->agent_scen, 4 * agent_scen.size())) ||
       (rc = dmalloc(&h->model, fs * (nx * nx + nx * nu + 2 * nu))) || (rc = dmalloc(&h->Qd, fs * na * nx)) ||
       (rc = dmalloc(&h->Rd, fs * na * nu)) || (rc = dmalloc(&h->Qfd, fs * na * nx)) ||
@@ -375,6 +435,9 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   cudaMemcpyAsync(h->gmem, gmem.data(), 4 * gmem.size(), cudaMemcpyHostToDevice, st);
   if (!pairs.empty()) {
     cudaMemcpyAsync(h->pairs, pairs.data(), 4 * pairs.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->deg, deg.data(), 4 * deg.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->adj_ptr, adj_ptr.data(), 4 * adj_ptr.size(), cudaMemcpyHostToDevice, st);
+    if (!adj.empty()) cudaMemcpyAsync(h->adj, adj.data(), 4 * adj.size(), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->pair_scen, pair_scen.data(), 4 * pair_scen.size(), cudaMemcpyHostToDevice, st);
   }
   cudaMemcpyAsync(h->agent_scen, agent_scen.data(), 4 * agent_scen.size(), cudaMemcpyHostToDevice, st);

@@ -37,7 +37,8 @@ enum { START_COLD = 0, START_HOT = 1, START_TURBO = 2 };
 enum { QP_COLD = 0, QP_LQR = 1, QP_GIVEN = 2 };
 
 struct ScenMeta {
-  int32_t N, T, P, pad;
+  int32_t N, T, P;
+  int32_t sparse;     // 1: listed pairs (per-agent adjacency), 0: all pairs
   int64_t agent_off;  // first agent of the scenario (sum of N)
   int64_t as_off;     // agent-step offset (sum of N*T)
   int64_t ps_off;     // pair-step offset (sum of P*T)
@@ -91,6 +92,9 @@ struct Dev {
   double adapt_mu, adapt_tau;
   double* rho_out;           // [n_scen] final rho (batched mode), or nullptr
   int32_t* rho_chg;          // [n_scen] number of rho changes
+  const int32_t* deg;        // [agents] consensus copies n_c of each agent (its pairs)
+  const int32_t* adj_ptr;    // [agents + 1] listed-pair adjacency of sparse scenarios
+  const int32_t* adj;        // scenario-local pair index, bit 31 set when the agent is second
 };
 
 // Per-stage factor cache of one agent (stage t):
@@ -175,6 +179,35 @@ __device__ __forceinline__ int pair_index(int N, int i, int j) {  // i < j
   return i * N - (i * (i + 1)) / 2 + (j - i - 1);
 }
 
+// Consensus copies n_c of agent i: its number of coupled pairs.
+template <typename F>
+__device__ __forceinline__ int agent_nc(const Dev<F>& D, const ScenMeta& s, int i) {
+  return s.sparse ? D.deg[s.agent_off + i] : s.N - 1;
+}
+
+// Calls ea(pair, first) for agent i's pairs in increasing partner order (all
+// pairs, or the listed ones); `pair` is the scenario-local pair index and
+// `first` tells whether i is the pair's first agent.
+template <typename F, class EA>
+__device__ __forceinline__ void for_partners(const Dev<F>& D, const ScenMeta& s, int i, EA&& ea) {
+  if (s.sparse) {
+    const int64_t ga = s.agent_off + i;
+    const int e1 = D.adj_ptr[ga + 1];
+    for (int e = D.adj_ptr[ga]; e < e1; ++e) {
+      const uint32_t ent = (uint32_t)D.adj[e];
+      ea((int)(ent & 0x7FFFFFFFu), (ent >> 31) == 0u);
+    }
+  } else {
+    const int N = s.N;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      const bool first = i < j;
+      ea(first ? pair_index(N, i, j) : pair_index(N, j, i), first);
+    }
+  }
+}
+
+
 // ---------------------------------------------------------------------------
 // K-a: per-agent x-update
 // ---------------------------------------------------------------------------
@@ -229,6 +262,7 @@ struct AgentCtx {
   const F* xr;
   const F* xi;
   int coop;          // cooperative refactorization allowed (uniform over the warp)
+  int nc;            // consensus copies of the agent (its number of pairs)
 
   __device__ __forceinline__ F k(int e) const { return kc[e * ks]; }
 
@@ -242,7 +276,7 @@ struct AgentCtx {
   __device__ __forceinline__ F& x(int t, int r) const { return Xo[((size_t)t * NX + r) * N + i]; }
   // Hessian diagonal of x_T
   __device__ __forceinline__ F qbarT(int r) const {
-    return F(2) * qf[r] + (r < DP ? k(AgentConst<NX, NU>::RHO) * F(N - 1) : F(0));
+    return F(2) * qf[r] + (r < DP ? k(AgentConst<NX, NU>::RHO) * F(nc) : F(0));
   }
   // h_t component r (r < DP) of stage t = 1..T
   __device__ __forceinline__ F hv(int t, int r) const { return h[((size_t)(t - 1) * DP + r) * N + i]; }
@@ -1289,9 +1323,9 @@ __device__ void init_phase(const Dev<F>& D, const ScenMeta& s, int64_t t0, int64
   F* h = D.h + s.as_off * DP;
   const F* w0 = D.w0 + s.as_off * DP;
   F* U = D.U + s.as_off * NU;
-  const F nc = F(N - 1);
   for (int64_t idx = t0; idx < (int64_t)N * T; idx += stride) {
     const int tm1 = (int)(idx / N), i = (int)(idx - (int64_t)tm1 * N);
+    const F nc = F(agent_nc(D, s, i));
 #pragma unroll
     for (int c = 0; c < DP; ++c) {
       const F w = w0[((size_t)tm1 * DP + c) * N + i];
@@ -1335,7 +1369,8 @@ __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, c
   A.qf = D.Qfd + ag * NX;
   A.xr = D.x_ref + ag * NX;
   A.xi = D.x_init + ag * NX;
-  const F rnc = F(rho) * F(s.N - 1);
+  A.nc = agent_nc(D, s, i);
+  const F rnc = F(rho) * F(A.nc);
   kc[AC::RHO * ks] = F(rho);
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
@@ -1369,6 +1404,7 @@ __device__ __forceinline__ AgentCtx<F, NX, NU, DP> idle_agent(const Model<F, NX,
   A.xr = nullptr;
   A.xi = nullptr;
   A.coop = coop;
+  A.nc = 0;
   return A;
 }
 
@@ -1487,22 +1523,19 @@ __device__ void gather_phase(const Dev<F>& D, const ScenMeta& s, int xl_new, int
   const F* tho = D.theta + (size_t)tk * D.tot_ps + s.ps_off;
   const F* a = D.a + s.ps_off * DP;
   F* h = D.h + s.as_off * DP;
-  const F nc = F(N - 1);
   for (int64_t idx = t0; idx < (int64_t)N * s.T; idx += stride) {
     const int tm1 = (int)(idx / N), i = (int)(idx - (int64_t)tm1 * N);
+    const F nc = F(agent_nc(D, s, i));
     F acc[DP];
 #pragma unroll
     for (int c = 0; c < DP; ++c) acc[c] = nc * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
     const size_t qb = (size_t)tm1 * P;
-    for (int j = 0; j < N; ++j) {
-      if (j == i) continue;
-      const bool first = i < j;
-      const int pair = first ? pair_index(N, i, j) : pair_index(N, j, i);
+    for_partners(D, s, i, [&](int pair, bool first) {
       F e = fma(F(2), thn[qb + pair], -tho[qb + pair]);
       if (!first) e = -e;
 #pragma unroll
       for (int c = 0; c < DP; ++c) acc[c] = fma(e, a[((size_t)tm1 * DP + c) * P + pair], acc[c]);
-    }
+    });
 #pragma unroll
     for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
   }
@@ -1537,7 +1570,22 @@ __device__ void gather_tile(const Dev<F>& D, const ScenMeta& s, int xl_new, int 
   const int rows = min(32, N - i0);
   F acc[DP];
 #pragma unroll
-  for (int c = 0; c < DP; ++c) acc[c] = own ? F(N - 1) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i] : F(0);
+  for (int c = 0; c < DP; ++c) acc[c] = own ? F(agent_nc(D, s, i)) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i] : F(0);
+  if (s.sparse) {
+    // listed pairs: each lane sums its own agent's pairs (no tile)
+    if (own) {
+      for_partners(D, s, i, [&](int pair, bool first) {
+        F e = fma(F(2), thn[pair], -tho[pair]);
+        if (!first) e = -e;
+#pragma unroll
+        for (int c = 0; c < DP; ++c) acc[c] = fma(e, a[(size_t)c * P + pair], acc[c]);
+      });
+      F* h = D.h + s.as_off * DP;
+#pragma unroll
+      for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+    }
+    return;
+  }
   for (int j0 = 0; j0 < N; j0 += 32) {
     const int cols = min(32, N - j0);
     __syncwarp();
@@ -1601,7 +1649,7 @@ __device__ void pair_gather_fused(const Dev<F>& D, const ScenMeta& s, int xl, in
   F* h = D.h + s.as_off * DP;
   F* smE = sm;
   F* smA = sm + P;
-  const F d = F(s.d), nc = F(N - 1);
+  const F d = F(s.d);
   for (int tm1 = 0; tm1 < s.T; ++tm1) {
     const size_t qb = (size_t)tm1 * P;
     for (int pair = tid; pair < P; pair += nt) {
@@ -1628,18 +1676,16 @@ __device__ void pair_gather_fused(const Dev<F>& D, const ScenMeta& s, int xl, in
     }
     __syncthreads();
     for (int i = tid; i < N; i += nt) {
+      const F nc = F(agent_nc(D, s, i));
       F acc[DP];
 #pragma unroll
       for (int c = 0; c < DP; ++c) acc[c] = nc * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
-      for (int j = 0; j < N; ++j) {
-        if (j == i) continue;
-        const bool first = i < j;
-        const int pair = first ? pair_index(N, i, j) : pair_index(N, j, i);
+      for_partners(D, s, i, [&](int pair, bool first) {
         F e = smE[pair];
         if (!first) e = -e;
 #pragma unroll
         for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * P + pair], acc[c]);
-      }
+      });
 #pragma unroll
       for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
     }
@@ -1938,16 +1984,14 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
         const int N = s.N, i = my_i, base = gs.poff[my_m];
         F acc[DP];
 #pragma unroll
-        for (int c = 0; c < DP; ++c) acc[c] = F(N - 1) * st.pos[c][tid];
-        for (int j = 0; j < N; ++j) {
-          if (j == i) continue;
-          const bool first = i < j;
-          const int pair = base + (first ? pair_index(N, i, j) : pair_index(N, j, i));
+        for (int c = 0; c < DP; ++c) acc[c] = F(agent_nc(D, s, i)) * st.pos[c][tid];
+        for_partners(D, s, i, [&](int lp, bool first) {
+          const int pair = base + lp;
           F e = smE[pair];
           if (!first) e = -e;
 #pragma unroll
           for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * nP + pair], acc[c]);
-        }
+        });
         F* h = D.h + s.as_off * DP;
 #pragma unroll
         for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
@@ -2068,16 +2112,14 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
           F acc[DP];
 #pragma unroll
-          for (int c = 0; c < DP; ++c) acc[c] = F(N - 1) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
-          for (int j = 0; j < N; ++j) {
-            if (j == i) continue;
-            const bool first = i < j;
-            const int pair = base + (first ? pair_index(N, i, j) : pair_index(N, j, i));
+          for (int c = 0; c < DP; ++c) acc[c] = F(agent_nc(D, s, i)) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
+          for_partners(D, s, i, [&](int lp, bool first) {
+            const int pair = base + lp;
             F e = smE[pair];
             if (!first) e = -e;
 #pragma unroll
             for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * nP + pair], acc[c]);
-          }
+          });
           F* h = D.h + s.as_off * DP;
 #pragma unroll
           for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];

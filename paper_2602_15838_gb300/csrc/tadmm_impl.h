@@ -38,6 +38,10 @@ struct tadmm_handle {
   int n_groups = 0;
   int max_group_pairs = 0;
   int32_t* pairs = nullptr;
+  int32_t* deg = nullptr;       // [tot_agents] copies per agent
+  int32_t* adj_ptr = nullptr;   // [tot_agents + 1]
+  int32_t* adj = nullptr;       // listed-pair adjacency (sparse scenarios)
+  std::vector<int32_t> pair_count_h, pair_ij_h;  // caller's pair lists (empty: all pairs)
   int32_t* pair_scen = nullptr;
   int32_t* agent_scen = nullptr;
   void* model = nullptr;

@@ -484,6 +484,9 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.adapt_tau = h->opt.adapt_tau;
   D.rho_out = h->rho_out;
   D.rho_chg = h->rho_chg;
+  D.deg = h->deg;
+  D.adj_ptr = h->adj_ptr;
+  D.adj = h->adj;
   return D;
 }
 

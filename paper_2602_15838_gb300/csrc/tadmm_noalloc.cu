@@ -73,7 +73,7 @@ __global__ void k_noalloc_setup(ScenMeta* meta, int32_t* order, int32_t* pairs, 
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
   if (tid == 0) {
     ScenMeta m;
-    m.N = N; m.T = T; m.P = P; m.pad = 0;
+    m.N = N; m.T = T; m.P = P; m.sparse = 0;
     m.agent_off = 0; m.as_off = 0; m.ps_off = 0; m.xs_off = 0; m.pair_off = 0;
     m.d = d; m.rho = rho;
     *meta = m;

@@ -53,7 +53,8 @@ def _create_rc(tg, batch, **opt):
     return rc, tg.lib().tadmm_last_error().decode()
 
 
-@pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec", "adapt_mode", "adapt_mu"])
+@pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec", "adapt_mode", "adapt_mu",
+                                   "pair_dup", "pair_order"])
 def test_invalid_inputs_rejected_on_host(libtadmm, fault):
     tg, _ = libtadmm
     from instances import make_workload
@@ -78,6 +79,12 @@ def test_invalid_inputs_rejected_on_host(libtadmm, fault):
         opt["adapt"] = (5, 10.0, 2.0)
     elif fault == "adapt_mu":
         opt["adapt"] = (5, 1.0, 2.0)
+    elif fault in ("pair_dup", "pair_order"):   # listed pairs: each once, i < j < N
+        import dataclasses
+        b = make_workload("ring14")
+        pl = np.array([[0, 1], [0, 1]] if fault == "pair_dup" else [[1, 0], [2, 3]], dtype=np.int32)
+        b = dataclasses.replace(b, pair_count=np.array([2], dtype=np.int32), pair_ij=pl,
+                                a=b.a[:2 * int(b.T[0])])
     rc, msg = _create_rc(tg, b, **opt)
     assert rc == tg.EINVAL, msg
     assert msg

@@ -465,3 +465,32 @@ def test_relinearized_solve_matches_oracle(tg):
     s.close()
     dist = np.linalg.norm(g["X"][0, 1:, :2] - g["X"][1, 1:, :2], axis=-1)
     assert dist.min() >= p.d_min[0] - 1e-3
+
+
+def test_sparse_coupling_matches_oracle(tg):
+    """Listed coupling pairs (each agent's 3 nearest neighbours): every iterate
+    of the batched, plain and graph modes within 1e-9 of the oracle's, and
+    an explicit list of all pairs runs bit for bit like the default all-pairs
+    coupling."""
+    from instances import nearest_neighbour_pairs, pair_list
+    import dataclasses
+    b = nearest_neighbour_pairs(make_workload("mixed", n_scen=8), 3)
+    assert (b.P < make_workload("mixed", n_scen=8).P).any()
+    for it in (1, 7):
+        ref = [oracle.admm(b, k, tol=0.0, max_iter=it) for k in range(b.n_scen)]
+        for mode in ("batched", "plain", "graph"):
+            g, _ = gpu_run(tg, b, 0.0, it, mode=mode)
+            for k in range(b.n_scen):
+                assert rel(g[k]["X"], ref[k]["X"]) <= 1e-9, (mode, it, k)
+                assert rel(g[k]["U"], ref[k]["U"]) <= 1e-9, (mode, it, k)
+                assert rel(g[k]["theta"], ref[k]["theta"]) <= 1e-9, (mode, it, k)
+    d = make_workload("mixed", n_scen=8)
+    full = dataclasses.replace(d, pair_count=d.P.astype(np.int32),
+                               pair_ij=np.concatenate([pair_list(int(n)) for n in d.N]))
+    for mode in ("batched", "graph"):
+        g0, c0 = gpu_run(tg, d, 1e-4, 200, mode=mode)
+        g1, c1 = gpu_run(tg, full, 1e-4, 200, mode=mode)
+        for k in range(d.n_scen):
+            assert g0[k]["iters"] == g1[k]["iters"] and g0[k]["status"] == g1[k]["status"], (mode, k)
+            assert np.array_equal(g0[k]["X"], g1[k]["X"]), (mode, k)
+            assert np.array_equal(g0[k]["theta"], g1[k]["theta"]), (mode, k)
