@@ -967,16 +967,41 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
     pn = terminal_lin(qf[rr], xr[rr]);
     if (rr < DP) pn = lin_term(pn, rho, hp[((size_t)(T - 1) * DP + rr) * N + ai]);
   }
+  // this lane's operands of a stage, loaded one stage ahead: mask, row rr of
+  // P_{t+1}B, row ra of S^{-1}, column rr of K, h_t[rr]
+  uint16_t mk_n = 0;
+  F pb_n[NU], si_n[NU], kq_n[NU], h_n = F(0);
+  auto load_back = [&](int t) {
+    const bool act = gact && t >= 0 && t < T;
+    mk_n = act ? Wm[(size_t)t * N + ai] : (uint16_t)0;
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      pb_n[a] = act ? C(t, CL::PB + rr * NU + a) : F(0);
+      si_n[a] = act ? C(t, CL::L + (a <= ra ? ra * NU + a : a * NU + ra)) : F(0);
+      kq_n[a] = act ? C(t, CL::K + a * NX + rr) : F(0);
+    }
+    h_n = (act && t >= 1 && rr < DP) ? hp[((size_t)(t - 1) * DP + rr) * N + ai] : F(0);
+  };
+  load_back(Tm - 1);
   for (int t = Tm - 1; t >= 0; --t) {
     const bool act = gact && t < T;
-    const uint16_t mask = act ? Wm[(size_t)t * N + ai] : (uint16_t)0;
+    const uint16_t mask = mk_n;
+    F pbv[NU], si[NU], kq[NU];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      pbv[a] = pb_n[a];
+      si[a] = si_n[a];
+      kq[a] = kq_n[a];
+    }
+    const F hv = h_n;
+    if (t >= 1) load_back(t - 1);
     F Pcp = pn;
     if (mask) {
 #pragma unroll
       for (int a = 0; a < NU; ++a) {
         if (!(mask & (0x101u << a))) continue;
         const F ub = (mask & (1u << a)) ? Mo.umin[a] : Mo.umax[a];
-        Pcp = fma(C(t, CL::PB + rr * NU + a), ub, Pcp);
+        Pcp = fma(pbv[a], ub, Pcp);
       }
     }
     // rows H + ra of p_{t+1} and of P_{t+1} c + p_{t+1}
@@ -1000,9 +1025,6 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
     for (int b = 0; b < NU; ++b) sv[b] = shfl_f(svl, gbase + b);
     if (act && r < NU) {
       // k_t row ra = -(S^{-1} s)[ra]
-      F si[NU];
-#pragma unroll
-      for (int b = 0; b < NU; ++b) si[b] = C(t, CL::L + (b <= ra ? ra * NU + b : b * NU + ra));
       F acc = si[0] * sv[0];
 #pragma unroll
       for (int b = 1; b < NU; ++b) acc = fma(si[b], sv[b], acc);
@@ -1012,7 +1034,7 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
       const F Pcpl = shfl_f(Pcp, gbase + (rr >= H ? rr - H : rr));
       if (act) {
         F acc = kc[(AC::QL + rr) * ks];
-        if (rr < DP) acc = lin_term(acc, rho, hp[((size_t)(t - 1) * DP + rr) * N + ai]);
+        if (rr < DP) acc = lin_term(acc, rho, hv);
         if (rr < H) {
           acc = acc + Pcp;
         } else {
@@ -1020,7 +1042,7 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
           acc = acc + Pcp;
         }
 #pragma unroll
-        for (int k = 0; k < NU; ++k) acc = fma(C(t, CL::K + k * NX + rr), sv[k], acc);
+        for (int k = 0; k < NU; ++k) acc = fma(kq[k], sv[k], acc);
         pn = acc;
       }
     }
@@ -1033,9 +1055,33 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
   const unsigned long long kmin = mono_key(Mo.umin[ra]), kmax = mono_key(Mo.umax[ra]);
   F xl = gact ? xi[rr] : F(0);
   if (row) Xo[(size_t)rr * N + ai] = xl;
+  // this lane's operands of a stage, loaded one stage ahead: mask, k_t[ra],
+  // row ra of K_t, B'p_{t+1}[ra], column ra of P_{t+1}B
+  uint16_t fm_n = 0;
+  F kf_n = F(0), Kr_n[NX], bp_n = F(0), pbc_n[NX];
+  auto load_fwd = [&](int t) {
+    const bool act = gact && t < T;
+    fm_n = act ? Wm[(size_t)t * N + ai] : (uint16_t)0;
+    kf_n = act ? C(t, CL::k + ra) : F(0);
+    bp_n = act ? C(t, CL::bp + ra) : F(0);
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      Kr_n[c] = act ? C(t, CL::K + ra * NX + c) : F(0);
+      pbc_n[c] = act ? C(t, CL::PB + c * NU + ra) : F(0);
+    }
+  };
+  load_fwd(0);
   for (int t = 0; t < Tm; ++t) {
     const bool act = gact && t < T;
-    const uint16_t mask = act ? Wm[(size_t)t * N + ai] : (uint16_t)0;
+    const uint16_t mask = fm_n;
+    const F kfv = kf_n, bpv = bp_n;
+    F Kr[NX], pbc[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      Kr[c] = Kr_n[c];
+      pbc[c] = pbc_n[c];
+    }
+    if (t + 1 < Tm) load_fwd(t + 1);
     F xv[NX];
 #pragma unroll
     for (int c = 0; c < NX; ++c) xv[c] = shfl_f(xl, gbase + c);
@@ -1043,9 +1089,9 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
     if (mask & (1u << ra)) ul = Mo.umin[ra];
     else if (mask & (0x100u << ra)) ul = Mo.umax[ra];
     else {
-      F acc = act ? C(t, CL::k + ra) : F(0);
+      F acc = kfv;
 #pragma unroll
-      for (int c = 0; c < NX; ++c) acc = fma(act ? C(t, CL::K + ra * NX + c) : F(0), xv[c], acc);
+      for (int c = 0; c < NX; ++c) acc = fma(Kr[c], xv[c], acc);
       ul = acc;
       const unsigned long long ku = mono_key(acc);
       if (act && r < NU) o.out |= (ku < kmin) | (ku > kmax);
@@ -1062,9 +1108,9 @@ __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
     for (int c = 0; c < NX; ++c) xnv[c] = shfl_f(xn, gbase + c);
     if (mask) {
       if (act && r < NU && (mask & (0x101u << ra))) {
-        F gg = C(t, CL::bp + ra);
+        F gg = bpv;
 #pragma unroll
-        for (int c = 0; c < NX; ++c) gg = fma(C(t, CL::PB + c * NU + ra), xnv[c], gg);
+        for (int c = 0; c < NX; ++c) gg = fma(pbc[c], xnv[c], gg);
         gg = fma(kc[(AC::RB + ra) * ks], ul, gg);
         const F mu = (mask & (1u << ra)) ? gg : -gg;
         const unsigned long long ab = abs_bits(mu);
