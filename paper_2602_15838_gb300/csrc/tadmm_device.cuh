@@ -1638,6 +1638,7 @@ __device__ void gather_tile(const Dev<F>& D, const ScenMeta& s, int xl_new, int 
     if (i0 < j0 + cols - 1) {
       // pairs (i, j) with i < j: row r = own agent, lane = partner
       const int j = j0 + lane;
+#pragma unroll 8
       for (int r = 0; r < rows; ++r) {
         const int ii = i0 + r;
         if (lane < cols && ii < j) {
@@ -1650,6 +1651,7 @@ __device__ void gather_tile(const Dev<F>& D, const ScenMeta& s, int xl_new, int 
     }
     if (j0 < i0 + rows - 1) {
       // pairs (j, i) with j < i: row r = partner, lane = own agent (transposed)
+#pragma unroll 8
       for (int r = 0; r < cols; ++r) {
         const int jj = j0 + r;
         if (own && jj < i) {
