@@ -1,14 +1,17 @@
 // Device code of the batched ADMM hot path (arXiv 2602.15838, Sec. III.B-IV).
 //
 // Three phases per ADMM iteration, written as device functions so that the
-// batched persistent kernel (one CTA per scenario) and the per-phase kernels of
-// the plain mode share them:
-//   x-update  (K-a)  one thread per agent: Riccati-factorized primal active set
-//                    for the box-constrained local QP (Sec. IV.A-C);
-//   pair      (K-b)  one thread per (pair, step): halfspace projection of the
-//                    consensus copies, scaled dual update and residuals;
-//   gather    (K-b') one thread per (agent, step): the aggregate linear term of
-//                    the next x-update.
+// batched persistent kernel (scenario groups, one CTA each) and the per-phase
+// kernels of the plain and graph modes share them:
+//   x-update  (K-a)  one lane per agent, all lanes of a warp together:
+//                    Riccati-factorized primal active set for the
+//                    box-constrained local QP (Sec. IV.A-C); stage
+//                    refactorizations (and, in the per-phase kernels, EQP
+//                    passes) spread over lane groups when few agents need them;
+//   pair      (K-b)  per (pair, step): halfspace projection of the consensus
+//                    copies, scaled dual update and residuals;
+//   gather    (K-b') per (agent, step): the aggregate linear term of the next
+//                    x-update, over the agent's pairs in partner order.
 //
 // Per-scenario internal layouts (agent index fastest, so that consecutive
 // threads touch consecutive words):
@@ -16,8 +19,8 @@
 //   h       [T][DP][N]     sum over partners of (w - y), t = 1..T
 //   U, Us   [T][NU][N]     current active-set iterate and EQP solution
 //   Wm, Cm  [T][N]         working-set and cached-factor bit masks
-//   cache   [T+1][E][N]    Riccati cache per stage: P, K, L (Cholesky of the
-//                          reduced S with inverted diagonal), k, p
+//   cache   [T+1][E][N]    Riccati cache per stage (CacheLayout): P_t, K_t,
+//                          S_t^{-1}, k_t, P_{t+1}B, B'p_{t+1}
 //   theta   [slot][T][P]   projection steps theta^k (multiplier / rho), three
 //                          slots rotating with k mod 3
 //   a       [T][DP][P]     halfspace normals

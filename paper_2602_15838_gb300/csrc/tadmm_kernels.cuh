@@ -10,9 +10,10 @@
 namespace tadmm {
 
 // ---------------------------------------------------------------------------
-// Batched persistent kernel: each CTA repeatedly takes the next scenario from
-// a work queue (largest estimated work first) and runs every ADMM iteration of
-// it on-chip, phases separated by CTA barriers.
+// Batched persistent kernel: each CTA repeatedly takes the next scenario group
+// (same-horizon scenarios of at most 32 agents in total, or one larger
+// scenario) from a work queue, largest estimated work first, and runs every
+// ADMM iteration of it on-chip, phases separated by CTA barriers.
 // ---------------------------------------------------------------------------
 // Register-budget variants of the persistent kernel (chosen by the autotuner):
 // (max threads per CTA, min resident CTAs per SM) for __launch_bounds__.
