@@ -415,6 +415,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   double* pos = (double*)malloc(sizeof(double) * ((size_t)N * T * dp + 1));
   int64_t as_total = 0;
   orc_scenario sc = *s; /* the penalty changes under residual balancing */
+  const double alpha = (o->relax_alpha == 0.0) ? 1.0 : o->relax_alpha;
   res->rho_final = s->rho;
   res->rho_changes = 0;
   res->status = ORC_NOT_CONVERGED;
@@ -485,10 +486,15 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
           const double* a = s->a + o2;
           const double* pi = pos + ((size_t)i * T + t) * dp;
           const double* pj = pos + ((size_t)j * T + t) * dp;
-          double vi[3], vj[3], nwi[3], nwj[3];
+          /* over-relaxation (Boyd et al. 2011, Sec. 3.4.3): the relaxed positions
+           * alpha p + (1 - alpha) w^k replace p in the projection and the dual
+           * update; the residuals keep p */
+          double hi[3], hj[3], vi[3], vj[3], nwi[3], nwj[3];
           for (int c = 0; c < dp; ++c) {
-            vi[c] = pi[c] + yi[o2 + c];
-            vj[c] = pj[c] + yj[o2 + c];
+            hi[c] = (alpha == 1.0) ? pi[c] : alpha * pi[c] + (1.0 - alpha) * wi[o2 + c];
+            hj[c] = (alpha == 1.0) ? pj[c] : alpha * pj[c] + (1.0 - alpha) * wj[o2 + c];
+            vi[c] = hi[c] + yi[o2 + c];
+            vj[c] = hj[c] + yj[o2 + c];
           }
           double th = orc_halfspace_project(dp, a, s->d_min, vi, vj, nwi, nwj);
           for (int c = 0; c < dp; ++c) {
@@ -498,8 +504,8 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
             sd = fmax(sd, fabs(nwj[c] - wj[o2 + c]));
             wi[o2 + c] = nwi[c];
             wj[o2 + c] = nwj[c];
-            yi[o2 + c] += pi[c] - nwi[c];
-            yj[o2 + c] += pj[c] - nwj[c];
+            yi[o2 + c] += hi[c] - nwi[c];
+            yj[o2 + c] += hj[c] - nwj[c];
             dev = fmax(dev, fabs(yi[o2 + c] + th * a[c]));
             dev = fmax(dev, fabs(yj[o2 + c] - th * a[c]));
           }

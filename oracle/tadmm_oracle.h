@@ -87,6 +87,8 @@ typedef struct {
   int adapt_every;    /* residual balancing of rho every this many iterations (0: fixed rho) */
   double adapt_mu;    /* imbalance ratio that triggers a change */
   double adapt_tau;   /* factor of a change */
+  double relax_alpha; /* over-relaxation: the projection and the dual update use
+                         alpha p + (1 - alpha) w^k instead of p (0 or 1: none) */
 } orc_options;
 
 typedef struct {

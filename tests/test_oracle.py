@@ -344,6 +344,72 @@ def test_residual_balancing_never_due_is_plain_admm():
     assert np.array_equal(r0["X"], r1["X"]) and np.array_equal(r0["theta"], r1["theta"])
 
 
+def test_over_relaxation_alpha_one_is_plain_admm():
+    """alpha = 1 is no relaxation, bit for bit."""
+    b = random_scenario(seed=3, N=3, T=8, box=1.5, rho=0.5)
+    r0 = oracle.admm(b, 0, tol=0.0, max_iter=30)
+    r1 = oracle.admm(b, 0, tol=0.0, max_iter=30, alpha=1.0)
+    assert np.array_equal(r0["X"], r1["X"]) and np.array_equal(r0["theta"], r1["theta"])
+
+
+@pytest.mark.parametrize("alpha", [0.7, 1.6])
+def test_over_relaxation_keeps_the_fixed_point(alpha):
+    """Over-relaxed ADMM (Boyd et al. 2011, Sec. 3.4.3; an extension, off by
+    default) has the same fixed point: it converges to the global QP optimum,
+    with the halfspace multipliers rho * theta and y = -theta a intact."""
+    b = random_scenario(seed=3, N=3, T=8, box=1.5, rho=20.0)
+    g = oracle.global_qp(b, 0)
+    assert g["status"] == oracle.CONVERGED and g["act_h"].sum() > 0
+    r = oracle.admm(b, 0, tol=1e-10, max_iter=40000, alpha=alpha)
+    assert r["status"] == oracle.CONVERGED
+    assert np.abs(r["X"] - g["X"]).max() <= 1e-7
+    assert np.abs(b.rho[0] * r["theta"] - g["mu_h"]).max() <= 1e-5 * max(1, g["mu_h"].max())
+    assert np.array_equal(r["W"], g["W"])
+    assert r["inv_dev"] <= 1e-10
+
+
+def test_over_relaxation_theta_form_equals_vector_form():
+    """The pair-scalar form of over-relaxed ADMM that the GPU path runs, written
+    here with numpy around the oracle's own x-update: with y_i = -theta a and the
+    consensus copies w_i = s_i + phi a, w_j = s_j - phi a (s per agent and step,
+    phi per pair and step), one iteration is
+        theta' = max(0, theta + (d - alpha a.(p_i - p_j) - (1 - alpha)(a.(s_i - s_j) + 2 phi)) / 2)
+        phi'   = (1 - alpha) phi + theta' - theta,   s' = alpha p + (1 - alpha) s
+        h_i    = n_c s_i' + sum_j sigma_ij (phi' + theta') a_ij.
+    Its iterates must equal the literal vector-form ADMM (per-side copies and
+    scaled duals) to rounding."""
+    alpha = 1.6
+    b = random_scenario(seed=3, N=3, T=8, box=1.5, rho=1.0)
+    N, T, dp = int(b.N[0]), int(b.T[0]), b.dp
+    pl = pair_list(N)
+    P = len(pl)
+    a = b.a.reshape(P, T, dp)
+    d = float(b.d_min[0])
+    s = b.w0.reshape(N, T, dp).copy()
+    phi = np.zeros((P, T))
+    th = np.zeros((P, T))
+    K = 25
+    for k in range(K):
+        h = (N - 1) * s.copy()
+        for q, (i, j) in enumerate(pl):
+            h[i] += (phi[q] + th[q])[:, None] * a[q]
+            h[j] -= (phi[q] + th[q])[:, None] * a[q]
+        X = np.stack([oracle.agent_xupdate(b, 0, i, h[i], start=oracle.QP_LQR)["x"] for i in range(N)])
+        p = X[:, 1:, :dp]
+        for q, (i, j) in enumerate(pl):
+            ahat = alpha * np.einsum("tc,tc->t", a[q], p[i] - p[j]) \
+                + (1 - alpha) * (np.einsum("tc,tc->t", a[q], s[i] - s[j]) + 2 * phi[q])
+            tn = np.maximum(0.0, th[q] + (d - ahat) / 2)
+            phi[q] = (1 - alpha) * phi[q] + tn - th[q]
+            th[q] = tn
+        s = alpha * p + (1 - alpha) * s
+    r = oracle.admm(b, 0, tol=0.0, max_iter=K, alpha=alpha)
+    assert r["iters"] == K
+    assert np.abs(r["X"] - X).max() <= 1e-10 * max(1.0, np.abs(X).max())
+    assert np.abs(r["theta"] - th).max() <= 1e-10 * max(1.0, np.abs(th).max())
+    assert th.max() > 0  # halfspaces active: the test exercises the projection
+
+
 def test_relinearization_at_the_guess_reproduces_the_normals():
     """Re-linearizing at the guess lines (the zero-input trajectories the
     instances are built from) gives back the instance's own halfspace normals
