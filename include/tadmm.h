@@ -112,6 +112,12 @@ typedef struct {
   int32_t adapt_every;
   double adapt_mu;         /* > 1 */
   double adapt_tau;        /* > 1 */
+  /* Over-relaxation (an extension: the paper's ADMM is unrelaxed; Boyd et al.
+   * 2011, Sec. 3.4.3): the consensus projection and the scaled-dual update take
+   * alpha p + (1 - alpha) w^k in place of the new positions p; the residuals
+   * keep p.  0 or 1: off; otherwise 0 < alpha < 2.  Batched mode only, on the
+   * group path (scenarios of at most 32 agents); EINVAL otherwise. */
+  double relax_alpha;
 } tadmm_options;
 
 /* option flags (results are the same either way; for testing and measurement) */

@@ -39,7 +39,8 @@ class TadmmOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("start_mode", C.c_int32), ("as_max", C.c_int32),
                 ("eps_rel", C.c_double), ("mode", C.c_int32), ("threads_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("kernel_variant", C.c_int32), ("flags", C.c_int32),
-                ("adapt_every", C.c_int32), ("adapt_mu", C.c_double), ("adapt_tau", C.c_double)]
+                ("adapt_every", C.c_int32), ("adapt_mu", C.c_double), ("adapt_tau", C.c_double),
+                ("relax_alpha", C.c_double)]
 
 
 class TadmmError(RuntimeError):
@@ -131,8 +132,9 @@ class Solver:
 
     def __init__(self, batch, precision: int = 64, start: str = "turbo", mode: str = "batched",
                  as_max: int = 0, eps_rel: float = 0.0, threads_per_cta: int = 0, ctas_per_sm: int = 0,
-                 kernel_variant: int = 0, flags: int = 0, adapt=None):
-        """adapt = (every, mu, tau) turns on residual balancing of rho (batched mode)."""
+                 kernel_variant: int = 0, flags: int = 0, adapt=None, relax: float = 1.0):
+        """adapt = (every, mu, tau) turns on residual balancing of rho (batched mode);
+        relax = alpha in (0, 2) over-relaxes the consensus and dual update (batched mode)."""
         import torch
         if not torch.cuda.is_available():
             raise TadmmError("no CUDA device: the solver has no CPU path")
@@ -141,7 +143,7 @@ class Solver:
         self._hb = _HostBatch(batch)
         ae, am, at = (0, 10.0, 2.0) if adapt is None else adapt
         opt = TadmmOptions(precision, START[start], as_max, eps_rel, MODE[mode], threads_per_cta, ctas_per_sm,
-                           kernel_variant, flags, int(ae), float(am), float(at))
+                           kernel_variant, flags, int(ae), float(am), float(at), float(relax))
         h = C.c_void_p()
         _check(lib().tadmm_create(C.byref(self._hb.s), C.byref(opt), C.byref(h)), "tadmm_create")
         self.h = h

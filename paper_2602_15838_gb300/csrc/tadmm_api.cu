@@ -157,7 +157,7 @@ static void free_all(tadmm_handle* h) {
   for (void* p : ptrs0)
     if (p) cudaFree(p);
   void* ptrs[] = {h->meta,   h->order, h->pairs, h->deg, h->adj_ptr, h->adj, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
-                  h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->X,      h->h,
+                  h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->phi, h->sx, h->X,      h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
                   h->res,    h->eqp,   h->fact,  h->rho_out, h->rho_chg, h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
                   h->ex_buf, h->flag,  h->red2};
@@ -245,6 +245,16 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
       return set_error(TADMM_EINVAL, "residual balancing runs on the group path (no NO_GROUPING / NO_FUSED flags)");
     for (int s2 = 0; s2 < b->n_scen; ++s2)
       if (b->N[s2] > 32) return set_error(TADMM_EINVAL, "residual balancing supports scenarios of at most 32 agents");
+  }
+  if (o.relax_alpha == 0.0) o.relax_alpha = 1.0;
+  if (!(o.relax_alpha > 0.0 && o.relax_alpha < 2.0))
+    return set_error(TADMM_EINVAL, "relax_alpha must be 0 (off) or in (0, 2)");
+  if (o.relax_alpha != 1.0) {
+    if (o.mode != TADMM_MODE_BATCHED) return set_error(TADMM_EINVAL, "over-relaxation runs in the batched mode");
+    if (o.flags & (TADMM_FLAG_NO_GROUPING | TADMM_FLAG_NO_FUSED_PAIR_GATHER))
+      return set_error(TADMM_EINVAL, "over-relaxation runs on the group path (no NO_GROUPING / NO_FUSED flags)");
+    for (int s2 = 0; s2 < b->n_scen; ++s2)
+      if (b->N[s2] > 32) return set_error(TADMM_EINVAL, "over-relaxation supports scenarios of at most 32 agents");
   }
   if ((o.flags & TADMM_FLAG_DOUBLE_FLOAT) && (o.precision != 64 || b->nx != 4))
     return set_error(TADMM_EINVAL, "TADMM_FLAG_DOUBLE_FLOAT needs precision 64 and (nx, nu, dp) = (4, 2, 2)");
@@ -416,7 +426,8 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
       (rc = dmalloc(&h->st_model, 8 * (nx * nx + nx * nu + 2 * nu))) ||
       (rc = dmalloc(&h->st_agent, 8 * na * (4 * nx + nu))) || (rc = dmalloc(&h->st_a, 8 * h->tot_ps * dp)) ||
       (rc = dmalloc(&h->st_w0, 8 * h->tot_as * dp)) || (rc = dmalloc(&h->ex_buf, h->ex_bytes + h->tot_as * nu + 16)) ||
-      (rc = dmalloc(&h->flag, 16)) || (rc = dmalloc(&h->red2, 16))) {
+      (rc = dmalloc(&h->flag, 16)) || (rc = dmalloc(&h->red2, 16)) ||
+      (o.relax_alpha != 1.0 && ((rc = dmalloc(&h->phi, fs * h->tot_ps)) || (rc = dmalloc(&h->sx, fs * h->tot_as * dp))))) {
     free_all(h);
     return rc;
   }

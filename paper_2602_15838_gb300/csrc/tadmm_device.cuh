@@ -93,6 +93,10 @@ struct Dev {
   int32_t coop;              // 1: refactorizations may be spread over lane groups
   int32_t adapt_every;       // residual balancing of rho every adapt_every iterations (0: off)
   double adapt_mu, adapt_tau;
+  int32_t relax;             // 1: over-relaxed consensus/dual update with factor alpha (group path)
+  double alpha;
+  F* phi;                    // [tot_ps] pair part phi of the consensus copies w = s +/- phi a
+  F* sx;                     // [tot_as][dp] agent part s of the consensus copies
   double* rho_out;           // [n_scen] final rho (batched mode), or nullptr
   int32_t* rho_chg;          // [n_scen] number of rho changes
   const int32_t* deg;        // [agents] consensus copies n_c of each agent (its pairs)
@@ -1390,6 +1394,13 @@ __device__ void init_phase(const Dev<F>& D, const ScenMeta& s, int64_t t0, int64
     F* th = D.theta + (size_t)l * D.tot_ps + s.ps_off;
     for (int64_t q = t0; q < (int64_t)P * T; q += stride) th[q] = 0;
   }
+  if (D.relax) {
+    // over-relaxation: consensus copies w^0 = s^0 = the guess positions, phi^0 = 0
+    F* sx = D.sx + s.as_off * DP;
+    for (int64_t q = t0; q < (int64_t)N * T * DP; q += stride) sx[q] = w0[q];
+    F* ph = D.phi + s.ps_off;
+    for (int64_t q = t0; q < (int64_t)P * T; q += stride) ph[q] = 0;
+  }
 }
 
 // Agent context of agent i; its constants are written to the thread's column
@@ -1852,6 +1863,7 @@ struct GroupStage {
   uint32_t pair[kGroupPairs];   // flattened agent indices fi | fj << 8 of every member pair
   uint8_t mem[kGroupPairs];     // member of every flattened pair
   F pos[DP][kGroupMax];         // positions p^{k+1} of the group's agents at the current step
+  F sxs[DP][kGroupMax];         // over-relaxation: agent parts s^k of the consensus copies at that step
 };
 
 struct GroupSm {
@@ -1877,6 +1889,116 @@ __device__ __forceinline__ int member_of(const int* off, int G, int u) {
   int m = 0;
   while (m + 1 < G && off[m + 1] <= u) ++m;
   return m;
+}
+
+// Over-relaxed consensus projection, dual update and gather of a group, step by
+// step (an extension; Boyd et al. 2011, Sec. 3.4.3): the relaxed positions
+// alpha p + (1 - alpha) w^k take the place of p in the projection and in the
+// dual update.  The scaled duals stay y_i = -theta a, y_j = theta a, and the
+// consensus copies split into w_i = s_i + phi a, w_j = s_j - phi a, with s per
+// agent and step and phi per pair and step, so that one iteration reads
+//   theta' = max(0, theta + (d - alpha a.(p_i - p_j) - (1 - alpha)(a.(s_i - s_j) + 2 phi)) / 2),
+//   phi'   = (1 - alpha) phi + theta' - theta,   s' = alpha p + (1 - alpha) s,
+//   h_i    = n_c s_i' + sum_j sigma_ij (phi' + theta') a_ij
+// (alpha = 1 gives back s = p, phi' = theta' - theta).  The residuals keep the
+// unrelaxed p: r = max |p - w'| = max |(1 - alpha)(p - s) -/+ phi' a| and the
+// dual residual max |w' - w| = max |alpha (p - s) +/- (phi' - phi) a|, both
+// formed in this sweep.
+template <typename F, int NX, int DP>
+__device__ void group_relaxed_sweep(const Dev<F>& D, GroupSm& gs, GroupStage<F, DP>& st, F* smE, F* smA,
+                                    int my_m, int my_i, int xl, int tk, int tkp1) {
+  const int tid = threadIdx.x, nt = blockDim.x, nP = gs.nP, T = gs.T;
+  const F al = F(D.alpha), om = F(1.0 - D.alpha);
+  const bool mine = my_m >= 0 && gs.active[my_m];
+  const F* Xm = nullptr;
+  F* Sm = nullptr;
+  int Nm = 1;
+  if (mine) {
+    const ScenMeta& s = gs.meta[my_m];
+    Xm = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+    Sm = D.sx + s.as_off * DP;
+    Nm = s.N;
+  }
+  for (int tm1 = 0; tm1 < T; ++tm1) {
+    if (mine) {
+#pragma unroll
+      for (int c = 0; c < DP; ++c) {
+        st.pos[c][tid] = Xm[((size_t)(tm1 + 1) * NX + c) * Nm + my_i];
+        st.sxs[c][tid] = Sm[((size_t)tm1 * DP + c) * Nm + my_i];
+      }
+    }
+    __syncthreads();
+    for (int u = tid; u < nP; u += nt) {
+      const int m = st.mem[u];
+      if (!gs.active[m]) continue;
+      const ScenMeta& s = gs.meta[m];
+      const int P = s.P, pair = u - gs.poff[m];
+      const size_t q = s.ps_off + (size_t)tm1 * P + pair;
+      const F* a = D.a + s.ps_off * DP;
+      const uint32_t fij = st.pair[u];
+      const int fi = fij & 0xFF, fj = fij >> 8;
+      const F th = D.theta[(size_t)tk * D.tot_ps + q];
+      const F ph = D.phi[q];
+      F av[DP];
+      F ap = F(0), as = F(0);  // a.(p_i - p_j), a.(s_i - s_j)
+#pragma unroll
+      for (int c = 0; c < DP; ++c) {
+        av[c] = a[((size_t)tm1 * DP + c) * P + pair];
+        smA[c * nP + u] = av[c];
+        ap = fma(av[c], st.pos[c][fi] - st.pos[c][fj], ap);
+        as = fma(av[c], st.sxs[c][fi] - st.sxs[c][fj], as);
+      }
+      const F ahat = fma(al, ap, om * fma(F(2), ph, as));
+      F tn = fma(F(s.d) - ahat, F(0.5), th);
+      if (sign_set(tn)) tn = F(0);
+      const F pn = fma(om, ph, tn - th);
+      D.theta[(size_t)tkp1 * D.tot_ps + q] = tn;
+      D.phi[q] = pn;
+      smE[u] = pn + tn;
+      const F dph = pn - ph;
+      unsigned long long rv = 0, sv = 0;
+#pragma unroll
+      for (int c = 0; c < DP; ++c) {
+        const F ei = st.pos[c][fi] - st.sxs[c][fi], ej = st.pos[c][fj] - st.sxs[c][fj];
+        const unsigned long long r1 = abs_bits(fma(-pn, av[c], om * ei));
+        const unsigned long long r2 = abs_bits(fma(pn, av[c], om * ej));
+        const unsigned long long s1 = abs_bits(fma(dph, av[c], al * ei));
+        const unsigned long long s2 = abs_bits(fma(-dph, av[c], al * ej));
+        rv = r1 > rv ? r1 : rv;
+        rv = r2 > rv ? r2 : rv;
+        sv = s1 > sv ? s1 : sv;
+        sv = s2 > sv ? s2 : sv;
+      }
+      if (rv > gs.rb[m]) atomicMax(&gs.rb[m], rv);
+      if (sv > gs.sb[m]) atomicMax(&gs.sb[m], sv);
+    }
+    __syncthreads();
+    if (mine) {
+      const ScenMeta& s = gs.meta[my_m];
+      const int N = s.N, i = my_i, base = gs.poff[my_m];
+      const F nc = F(agent_nc(D, s, i));
+      F sn[DP], acc[DP];
+#pragma unroll
+      for (int c = 0; c < DP; ++c) {
+        sn[c] = fma(al, st.pos[c][tid], om * st.sxs[c][tid]);
+        acc[c] = nc * sn[c];
+      }
+      for_partners(D, s, i, [&](int lp, bool first) {
+        const int pair = base + lp;
+        F e = smE[pair];
+        if (!first) e = -e;
+#pragma unroll
+        for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * nP + pair], acc[c]);
+      });
+      F* h = D.h + s.as_off * DP;
+#pragma unroll
+      for (int c = 0; c < DP; ++c) {
+        h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+        Sm[((size_t)tm1 * DP + c) * N + i] = sn[c];
+      }
+    }
+    __syncthreads();
+  }
 }
 
 template <typename F, int NX, int NU, int DP, bool DI>
@@ -1961,95 +2083,100 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     // next step's positions, and the operands of each batch of kPairBatch
     // pairs, are loaded ahead of their use so that the load latency overlaps
     // the arithmetic.
-    const bool mine = my_m >= 0 && gs.active[my_m];
-    const F* Xmine = nullptr;
-    int Nmine = 1;
-    F pnext[DP];
-    if (mine) {
-      const ScenMeta& s = gs.meta[my_m];
-      Xmine = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
-      Nmine = s.N;
-#pragma unroll
-      for (int c = 0; c < DP; ++c) pnext[c] = Xmine[((size_t)NX + c) * Nmine + my_i];
-    }
-    for (int tm1 = 0; tm1 < T; ++tm1) {
-      if (mine) {
-#pragma unroll
-        for (int c = 0; c < DP; ++c) st.pos[c][tid] = pnext[c];
-      }
-      __syncthreads();
-      for (int ub = tid; ub < nP; ub += kPairBatch * nt) {
-        F av[kPairBatch][DP], thv[kPairBatch];
-        int mk[kPairBatch];
-#pragma unroll
-        for (int b = 0; b < kPairBatch; ++b) {
-          const int u = ub + b * nt;
-          mk[b] = -1;
-          if (u < nP) {
-            const int m = st.mem[u];
-            if (gs.active[m]) {
-              mk[b] = m;
-              const ScenMeta& s = gs.meta[m];
-              const int P = s.P, pair = u - gs.poff[m];
-              const F* a = D.a + s.ps_off * DP;
-#pragma unroll
-              for (int c = 0; c < DP; ++c) av[b][c] = a[((size_t)tm1 * DP + c) * P + pair];
-              thv[b] = D.theta[(size_t)tk * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair];
-            }
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < kPairBatch; ++b) {
-          if (mk[b] < 0) continue;
-          const int u = ub + b * nt, m = mk[b];
-          const ScenMeta& s = gs.meta[m];
-          const int P = s.P, pair = u - gs.poff[m];
-          const uint32_t fij = st.pair[u];
-          const int fi = fij & 0xFF, fj = fij >> 8;
-          F g = F(s.d);  // d - a'(p_i - p_j)
-          unsigned long long amax = 0;
-#pragma unroll
-          for (int c = 0; c < DP; ++c) {
-            const F avc = av[b][c];
-            smA[c * nP + u] = avc;
-            g = fma(-avc, st.pos[c][fi] - st.pos[c][fj], g);
-            const unsigned long long ab = abs_bits(avc);
-            amax = ab > amax ? ab : amax;
-          }
-          const F th = thv[b];
-          F tn = fma(g, F(0.5), th);
-          if (sign_set(tn)) tn = F(0);
-          D.theta[(size_t)tkp1 * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair] = tn;
-          smE[u] = fma(F(2), tn, -th);
-          const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
-          if (v > gs.rb[m]) atomicMax(&gs.rb[m], v);
-        }
-      }
-      __syncthreads();
-      if (mine && tm1 + 1 < T) {
-#pragma unroll
-        for (int c = 0; c < DP; ++c) pnext[c] = Xmine[((size_t)(tm1 + 2) * NX + c) * Nmine + my_i];
-      }
+    if (D.relax) {
+      group_relaxed_sweep<F, NX, DP>(D, gs, st, smE, smA, my_m, my_i, xl, tk, tkp1);
+    } else {
+      const bool mine = my_m >= 0 && gs.active[my_m];
+      const F* Xmine = nullptr;
+      int Nmine = 1;
+      F pnext[DP];
       if (mine) {
         const ScenMeta& s = gs.meta[my_m];
-        const int N = s.N, i = my_i, base = gs.poff[my_m];
-        F acc[DP];
+        Xmine = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+        Nmine = s.N;
 #pragma unroll
-        for (int c = 0; c < DP; ++c) acc[c] = F(agent_nc(D, s, i)) * st.pos[c][tid];
-        for_partners(D, s, i, [&](int lp, bool first) {
-          const int pair = base + lp;
-          F e = smE[pair];
-          if (!first) e = -e;
-#pragma unroll
-          for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * nP + pair], acc[c]);
-        });
-        F* h = D.h + s.as_off * DP;
-#pragma unroll
-        for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+        for (int c = 0; c < DP; ++c) pnext[c] = Xmine[((size_t)NX + c) * Nmine + my_i];
       }
-      __syncthreads();
+      for (int tm1 = 0; tm1 < T; ++tm1) {
+        if (mine) {
+#pragma unroll
+          for (int c = 0; c < DP; ++c) st.pos[c][tid] = pnext[c];
+        }
+        __syncthreads();
+        for (int ub = tid; ub < nP; ub += kPairBatch * nt) {
+          F av[kPairBatch][DP], thv[kPairBatch];
+          int mk[kPairBatch];
+#pragma unroll
+          for (int b = 0; b < kPairBatch; ++b) {
+            const int u = ub + b * nt;
+            mk[b] = -1;
+            if (u < nP) {
+              const int m = st.mem[u];
+              if (gs.active[m]) {
+                mk[b] = m;
+                const ScenMeta& s = gs.meta[m];
+                const int P = s.P, pair = u - gs.poff[m];
+                const F* a = D.a + s.ps_off * DP;
+#pragma unroll
+                for (int c = 0; c < DP; ++c) av[b][c] = a[((size_t)tm1 * DP + c) * P + pair];
+                thv[b] = D.theta[(size_t)tk * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair];
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < kPairBatch; ++b) {
+            if (mk[b] < 0) continue;
+            const int u = ub + b * nt, m = mk[b];
+            const ScenMeta& s = gs.meta[m];
+            const int P = s.P, pair = u - gs.poff[m];
+            const uint32_t fij = st.pair[u];
+            const int fi = fij & 0xFF, fj = fij >> 8;
+            F g = F(s.d);  // d - a'(p_i - p_j)
+            unsigned long long amax = 0;
+#pragma unroll
+            for (int c = 0; c < DP; ++c) {
+              const F avc = av[b][c];
+              smA[c * nP + u] = avc;
+              g = fma(-avc, st.pos[c][fi] - st.pos[c][fj], g);
+              const unsigned long long ab = abs_bits(avc);
+              amax = ab > amax ? ab : amax;
+            }
+            const F th = thv[b];
+            F tn = fma(g, F(0.5), th);
+            if (sign_set(tn)) tn = F(0);
+            D.theta[(size_t)tkp1 * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair] = tn;
+            smE[u] = fma(F(2), tn, -th);
+            const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
+            if (v > gs.rb[m]) atomicMax(&gs.rb[m], v);
+          }
+        }
+        __syncthreads();
+        if (mine && tm1 + 1 < T) {
+#pragma unroll
+          for (int c = 0; c < DP; ++c) pnext[c] = Xmine[((size_t)(tm1 + 2) * NX + c) * Nmine + my_i];
+        }
+        if (mine) {
+          const ScenMeta& s = gs.meta[my_m];
+          const int N = s.N, i = my_i, base = gs.poff[my_m];
+          F acc[DP];
+#pragma unroll
+          for (int c = 0; c < DP; ++c) acc[c] = F(agent_nc(D, s, i)) * st.pos[c][tid];
+          for_partners(D, s, i, [&](int lp, bool first) {
+            const int pair = base + lp;
+            F e = smE[pair];
+            if (!first) e = -e;
+#pragma unroll
+            for (int c = 0; c < DP; ++c) acc[c] = fma(e, smA[c * nP + pair], acc[c]);
+          });
+          F* h = D.h + s.as_off * DP;
+#pragma unroll
+          for (int c = 0; c < DP; ++c) h[((size_t)tm1 * DP + c) * N + i] = acc[c];
+        }
+        __syncthreads();
+      }
     }
     // primal residual tests, then the dual residual only where it decides
+    // (the over-relaxed sweep has formed both)
     if (tid < G) {
       gs.need[tid] = 0;
       if (gs.active[tid]) {
@@ -2073,7 +2200,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
       gs.any = any;
     }
     __syncthreads();
-    if (gs.any) {
+    if (gs.any && !D.relax) {
       for (int tm1 = 0; tm1 < T; ++tm1) {
         for (int u = tid; u < nP; u += nt) {
           const int m = st.mem[u];
@@ -2148,10 +2275,15 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           F* const t0p = D.theta + (size_t)tk * D.tot_ps + q;
           const F th1 = *t1p, th0 = *t0p;
           const F t1 = th1 / F(gs.scale[m]);
-          const F t0 = (th0 - th1) + t1;
           *t1p = t1;
-          *t0p = t0;
-          smE[u] = fma(F(2), t1, -t0);
+          if (D.relax) {
+            // w = s + phi a does not hold theta: only the duals change
+            smE[u] = D.phi[q] + t1;
+          } else {
+            const F t0 = (th0 - th1) + t1;
+            *t0p = t0;
+            smE[u] = fma(F(2), t1, -t0);
+          }
           const F* a = D.a + s.ps_off * DP;
 #pragma unroll
           for (int c = 0; c < DP; ++c) smA[c * nP + u] = a[((size_t)tm1 * DP + c) * P + pair];
@@ -2161,9 +2293,12 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           const ScenMeta& s = gs.meta[my_m];
           const int N = s.N, i = my_i, base = gs.poff[my_m];
           const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
+          const F* Sx = D.relax ? D.sx + s.as_off * DP : nullptr;
           F acc[DP];
 #pragma unroll
-          for (int c = 0; c < DP; ++c) acc[c] = F(agent_nc(D, s, i)) * Xn[((size_t)(tm1 + 1) * NX + c) * N + i];
+          for (int c = 0; c < DP; ++c)
+            acc[c] = F(agent_nc(D, s, i)) * (D.relax ? Sx[((size_t)tm1 * DP + c) * N + i]
+                                                     : Xn[((size_t)(tm1 + 1) * NX + c) * N + i]);
           for_partners(D, s, i, [&](int lp, bool first) {
             const int pair = base + lp;
             F e = smE[pair];

@@ -53,6 +53,8 @@ struct tadmm_handle {
   void* a = nullptr;
   void* w0 = nullptr;
   void* theta = nullptr;
+  void* phi = nullptr;           // over-relaxation: [tot_ps] pair part of the consensus copies
+  void* sx = nullptr;            // over-relaxation: [tot_as][dp] agent part of the consensus copies
   void* X = nullptr;
   void* h = nullptr;
   void* U = nullptr;

@@ -483,6 +483,10 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.adapt_every = h->opt.adapt_every;
   D.adapt_mu = h->opt.adapt_mu;
   D.adapt_tau = h->opt.adapt_tau;
+  D.relax = h->opt.relax_alpha != 1.0 ? 1 : 0;
+  D.alpha = h->opt.relax_alpha;
+  D.phi = (F*)h->phi;
+  D.sx = (F*)h->sx;
   D.rho_out = h->rho_out;
   D.rho_chg = h->rho_chg;
   D.deg = h->deg;

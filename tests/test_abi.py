@@ -46,15 +46,15 @@ def test_version_and_last_error(libtadmm):
 def _create_rc(tg, batch, **opt):
     hb = tg._HostBatch(batch)
     ae, am, at = opt.get("adapt", (0, 10.0, 2.0))
-    o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0, 0, 0,
-                        ae, am, at)
+    o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0, 0,
+                        opt.get("flags", 0), ae, am, at, opt.get("relax", 0.0))
     h = C.c_void_p()
     rc = tg.lib().tadmm_create(C.byref(hb.s), C.byref(o), C.byref(h))
     return rc, tg.lib().tadmm_last_error().decode()
 
 
 @pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec", "adapt_mode", "adapt_mu",
-                                   "pair_dup", "pair_order"])
+                                   "pair_dup", "pair_order", "relax_range", "relax_mode", "relax_flags"])
 def test_invalid_inputs_rejected_on_host(libtadmm, fault):
     tg, _ = libtadmm
     from instances import make_workload
@@ -79,6 +79,14 @@ def test_invalid_inputs_rejected_on_host(libtadmm, fault):
         opt["adapt"] = (5, 10.0, 2.0)
     elif fault == "adapt_mu":
         opt["adapt"] = (5, 1.0, 2.0)
+    elif fault == "relax_range":   # over-relaxation factor in (0, 2)
+        opt["relax"] = 2.0
+    elif fault == "relax_mode":    # over-relaxation runs in the batched mode only
+        opt["mode"] = 1
+        opt["relax"] = 1.5
+    elif fault == "relax_flags":   # ... on the group path
+        opt["flags"] = 4
+        opt["relax"] = 1.5
     elif fault in ("pair_dup", "pair_order"):   # listed pairs: each once, i < j < N
         import dataclasses
         b = make_workload("ring14")

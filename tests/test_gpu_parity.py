@@ -428,6 +428,41 @@ def test_residual_balancing_faster_convergence(tg):
         assert rel(g[k]["X"], o["X"]) <= 1e-6, k
 
 
+@pytest.mark.parametrize("it,adapt", [(7, None), (23, None), (23, (5, 10.0, 2.0))])
+def test_over_relaxation_matches_oracle(tg, it, adapt):
+    """Over-relaxed ADMM (alpha 1.6; alone and with residual balancing) on the
+    GPU's pair-scalar form against the oracle's literal vector form: every
+    iterate within 1e-9 on X, U and theta."""
+    b = make_workload("mixed", n_scen=8)
+    s = tg.Solver(b, relax=1.6, adapt=adapt)
+    s.solve(0.0, it)
+    g = s.split(s.solution())
+    s.close()
+    for k in range(b.n_scen):
+        o = oracle.admm(b, k, tol=0.0, max_iter=it, alpha=1.6, adapt=adapt)
+        assert g[k]["iters"] == o["iters"] == it, k
+        assert rel(g[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(g[k]["U"], o["U"]) <= 1e-9, k
+        assert rel(g[k]["theta"], o["theta"]) <= 1e-9, k
+
+
+def test_over_relaxation_converged_against_oracle(tg):
+    """The 14-agent ring with residual balancing and alpha 1.6 run to tol 1e-4:
+    the same stopping iteration as the oracle (fewer than without relaxation),
+    the converged solution within 1e-6, and the final working sets equal."""
+    b = make_workload("ring14")
+    adapt = (10, 10.0, 2.0)
+    g = gpu_run(tg, b, 1e-4, 3000, relax=1.6, adapt=adapt)[0][0]
+    o = oracle.admm(b, 0, tol=1e-4, max_iter=3000, alpha=1.6, adapt=adapt)
+    o1 = oracle.admm(b, 0, tol=1e-4, max_iter=3000, adapt=adapt)
+    assert o["status"] == oracle.CONVERGED and g["status"] == tg.CONVERGED
+    assert g["iters"] == o["iters"] < o1["iters"]
+    assert rel(g["X"], o["X"]) <= 1e-6
+    assert rel(g["U"], o["U"]) <= 1e-6
+    ok, _ = nondegenerate_w_equal(g["W"], o, b)
+    assert ok
+
+
 def test_relinearized_solve_matches_oracle(tg):
     """One outer linearize-and-solve step: solve, re-linearize the collision
     halfspaces at the solution on the device (C ABI), solve again; against the
