@@ -403,6 +403,9 @@ def extras(tg, torch, batch, args):
     out["residual_balancing"]["note"] = ("rho balanced every 10 iterations (mu 10, tau 2; Boyd et al. 2011, "
                                          "Sec. 3.4.1), an extension beyond the fixed rho = 1 of the workload; "
                                          "parity against the oracle's balancing 1e-9")
+    out["balancing_relaxed"] = timed_solves(tg, torch, batch, args, precision=64, adapt=(10, 10.0, 2.0), relax=1.6)
+    out["balancing_relaxed"]["note"] = ("residual balancing as above plus over-relaxation alpha = 1.6 (Boyd et al. "
+                                        "2011, Sec. 3.4.3), an extension; parity against the oracle 1e-9")
     # one 512-agent 3D scenario (130816 pairs x 40 steps): graph mode vs plain mode per iteration
     from instances import make_workload
     sw = make_workload("swarm3d")
