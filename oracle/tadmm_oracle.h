@@ -13,7 +13,10 @@
  *     Numerical Optimization, Alg. 16.3) where every working-set iterate solves
  *     the full dense KKT system by LU with partial pivoting.
  *   - orc_admm: the ADMM iteration of Sec. III.B / IV.A (x-update, consensus
- *     projection, dual update, residuals) in its literal per-side vector form.
+ *     projection, dual update, residuals) in its literal per-side vector form,
+ *     optionally with residual balancing of rho (Boyd et al. 2011, Sec. 3.4.1)
+ *     and over-relaxation (Sec. 3.4.3 there), extensions the paper names as
+ *     future work on the iteration count.
  *   - orc_global_qp: the centralized linearized QP of Eq. (1) condensed in all
  *     inputs and solved by the same active-set method (the ADMM fixed point).
  *   - orc_agent_bruteforce: exhaustive active-set enumeration for tiny QPs.
