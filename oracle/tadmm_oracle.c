@@ -413,11 +413,23 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   double* yi = (double*)calloc(PS + 1, sizeof(double));
   double* yj = (double*)calloc(PS + 1, sizeof(double));
   double* pos = (double*)malloc(sizeof(double) * ((size_t)N * T * dp + 1));
+  /* accelerated ADMM with restart: extrapolated copies and duals, previous iterates */
+  const int fast = o->restart_eta > 0.0;
+  double* whi = (double*)malloc(sizeof(double) * (PS + 1));
+  double* whj = (double*)malloc(sizeof(double) * (PS + 1));
+  double* yhi = (double*)calloc(PS + 1, sizeof(double));
+  double* yhj = (double*)calloc(PS + 1, sizeof(double));
+  double* wpi = (double*)malloc(sizeof(double) * (PS + 1));
+  double* wpj = (double*)malloc(sizeof(double) * (PS + 1));
+  double* ypi = (double*)calloc(PS + 1, sizeof(double));
+  double* ypj = (double*)calloc(PS + 1, sizeof(double));
+  double acc_a = 1.0, c_prev = INFINITY;
   int64_t as_total = 0;
   orc_scenario sc = *s; /* the penalty changes under residual balancing */
   const double alpha = (o->relax_alpha == 0.0) ? 1.0 : o->relax_alpha;
   res->rho_final = s->rho;
   res->rho_changes = 0;
+  res->restarts = 0;
   res->status = ORC_NOT_CONVERGED;
   res->iters = 0;
   res->r = INFINITY;
@@ -436,6 +448,10 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
           wj[((size_t)pk * T + t) * dp + c] = s->w0[((size_t)j * T + t) * dp + c];
         }
     }
+  for (size_t q = 0; q < PS; ++q) {
+    whi[q] = wpi[q] = wi[q];
+    whj[q] = wpj[q] = wj[q];
+  }
   for (size_t k = 0; k < (size_t)P * T; ++k) res->theta[k] = 0.0;
   for (size_t k = 0; k < (size_t)N * T * nu; ++k) { res->U[k] = 0.0; res->W[k] = 0; res->mu[k] = 0.0; }
   for (int i = 0; i < N; ++i) simulate(T, nx, nu, s->A, s->B, s->x_init + (size_t)i * nx,
@@ -452,8 +468,8 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
         if (j == i) continue;
         const int pk = ptab[(size_t)i * N + j];
         if (pk < 0) continue;
-        const double* w = (i < j) ? wi : wj;
-        const double* y = (i < j) ? yi : yj;
+        const double* w = fast ? ((i < j) ? whi : whj) : ((i < j) ? wi : wj);
+        const double* y = fast ? ((i < j) ? yhi : yhj) : ((i < j) ? yi : yj);
         for (int t = 0; t < T; ++t)
           for (int c = 0; c < dp; ++c)
             h[t * dp + c] += w[((size_t)pk * T + t) * dp + c] - y[((size_t)pk * T + t) * dp + c];
@@ -478,7 +494,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
           pos[((size_t)i * T + (t - 1)) * dp + c] = res->X[((size_t)i * (T + 1) + t) * nx + c];
 
     /* --- consensus projection and scaled dual update, per pair and step --- */
-    double r = 0.0, sd = 0.0, dev = res->inv_dev;
+    double r = 0.0, sd = 0.0, cdu = 0.0, dev = res->inv_dev;
     for (int pk = 0; pk < P; ++pk) {
         const int i = plist[2 * pk], j = plist[2 * pk + 1];
         for (int t = 0; t < T; ++t) {
@@ -493,19 +509,27 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
           for (int c = 0; c < dp; ++c) {
             hi[c] = (alpha == 1.0) ? pi[c] : alpha * pi[c] + (1.0 - alpha) * wi[o2 + c];
             hj[c] = (alpha == 1.0) ? pj[c] : alpha * pj[c] + (1.0 - alpha) * wj[o2 + c];
-            vi[c] = hi[c] + yi[o2 + c];
-            vj[c] = hj[c] + yj[o2 + c];
+            vi[c] = hi[c] + (fast ? yhi[o2 + c] : yi[o2 + c]);
+            vj[c] = hj[c] + (fast ? yhj[o2 + c] : yj[o2 + c]);
           }
           double th = orc_halfspace_project(dp, a, s->d_min, vi, vj, nwi, nwj);
           for (int c = 0; c < dp; ++c) {
             r = fmax(r, fabs(pi[c] - nwi[c]));
             r = fmax(r, fabs(pj[c] - nwj[c]));
-            sd = fmax(sd, fabs(nwi[c] - wi[o2 + c]));
-            sd = fmax(sd, fabs(nwj[c] - wj[o2 + c]));
+            /* dual residual against the copies the x-update used */
+            sd = fmax(sd, fabs(nwi[c] - (fast ? whi[o2 + c] : wi[o2 + c])));
+            sd = fmax(sd, fabs(nwj[c] - (fast ? whj[o2 + c] : wj[o2 + c])));
+            if (fast) {
+              yi[o2 + c] = yhi[o2 + c] + hi[c] - nwi[c];
+              yj[o2 + c] = yhj[o2 + c] + hj[c] - nwj[c];
+              cdu = fmax(cdu, fabs(yi[o2 + c] - yhi[o2 + c]));
+              cdu = fmax(cdu, fabs(yj[o2 + c] - yhj[o2 + c]));
+            } else {
+              yi[o2 + c] += hi[c] - nwi[c];
+              yj[o2 + c] += hj[c] - nwj[c];
+            }
             wi[o2 + c] = nwi[c];
             wj[o2 + c] = nwj[c];
-            yi[o2 + c] += hi[c] - nwi[c];
-            yj[o2 + c] += hj[c] - nwj[c];
             dev = fmax(dev, fabs(yi[o2 + c] + th * a[c]));
             dev = fmax(dev, fabs(yj[o2 + c] - th * a[c]));
           }
@@ -519,6 +543,40 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
     if (res->trace) { res->trace[2 * k] = r; res->trace[2 * k + 1] = sres; }
     if (!isfinite(r) || !isfinite(sres)) { res->status = ORC_NUMERIC; break; }
     if (r <= o->tol && sres <= o->tol) { res->status = ORC_CONVERGED; break; }
+    if (fast) {
+      /* Goldstein et al. 2014, fast ADMM with restart: combined residual (here
+       * in the max norm), Nesterov extrapolation while it falls by eta, else a
+       * restart from the previous iterate */
+      const double ck = fmax(cdu, sd);
+      if (ck < o->restart_eta * c_prev) {
+        const double a1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * acc_a * acc_a));
+        const double beta = (acc_a - 1.0) / a1;
+        for (size_t q = 0; q < PS; ++q) {
+          whi[q] = wi[q] + beta * (wi[q] - wpi[q]);
+          whj[q] = wj[q] + beta * (wj[q] - wpj[q]);
+          yhi[q] = yi[q] + beta * (yi[q] - ypi[q]);
+          yhj[q] = yj[q] + beta * (yj[q] - ypj[q]);
+        }
+        acc_a = a1;
+        c_prev = ck;
+      } else {
+        for (size_t q = 0; q < PS; ++q) {
+          whi[q] = wpi[q];
+          whj[q] = wpj[q];
+          yhi[q] = ypi[q];
+          yhj[q] = ypj[q];
+        }
+        acc_a = 1.0;
+        c_prev = c_prev / o->restart_eta;
+        res->restarts++;
+      }
+      for (size_t q = 0; q < PS; ++q) {
+        wpi[q] = wi[q];
+        wpj[q] = wj[q];
+        ypi[q] = yi[q];
+        ypj[q] = yj[q];
+      }
+    }
     /* residual balancing (Boyd et al. 2011, Sec. 3.4.1): raise rho when the
      * primal residual dominates, lower it when the dual one does; the scaled
      * duals y = lambda / rho are rescaled so that lambda is unchanged */
@@ -530,7 +588,13 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
         for (size_t q = 0; q < PS; ++q) {
           yi[q] /= scale;
           yj[q] /= scale;
+          yhi[q] /= scale;
+          yhj[q] /= scale;
+          ypi[q] /= scale;
+          ypj[q] /= scale;
         }
+        acc_a = 1.0; /* the accelerated iteration starts afresh at the new penalty */
+        c_prev = INFINITY;
         sc.rho *= scale;
         res->rho_changes++;
       }
@@ -539,6 +603,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   res->rho_final = sc.rho;
   res->as_iters = as_total;
   free(wi); free(wj); free(yi); free(yj); free(pos); free(plist); free(ptab);
+  free(whi); free(whj); free(yhi); free(yhj); free(wpi); free(wpj); free(ypi); free(ypj);
   return 0;
 }
 

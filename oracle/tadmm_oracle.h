@@ -15,8 +15,9 @@
  *   - orc_admm: the ADMM iteration of Sec. III.B / IV.A (x-update, consensus
  *     projection, dual update, residuals) in its literal per-side vector form,
  *     optionally with residual balancing of rho (Boyd et al. 2011, Sec. 3.4.1)
- *     and over-relaxation (Sec. 3.4.3 there), extensions the paper names as
- *     future work on the iteration count.
+ *     over-relaxation (Sec. 3.4.3 there) and acceleration with restart
+ *     (Goldstein et al. 2014), extensions toward the iteration-count work the
+ *     paper names as future work.
  *   - orc_global_qp: the centralized linearized QP of Eq. (1) condensed in all
  *     inputs and solved by the same active-set method (the ADMM fixed point).
  *   - orc_agent_bruteforce: exhaustive active-set enumeration for tiny QPs.
@@ -92,6 +93,8 @@ typedef struct {
   double adapt_tau;   /* factor of a change */
   double relax_alpha; /* over-relaxation: the projection and the dual update use
                          alpha p + (1 - alpha) w^k instead of p (0 or 1: none) */
+  double restart_eta; /* accelerated ADMM with restart (0: off; in (0, 1): the
+                         restart factor) */
 } orc_options;
 
 typedef struct {
@@ -108,6 +111,7 @@ typedef struct {
   double inv_dev;     /* max |y_i + theta a| and |y_j - theta a| over the run */
   double rho_final;   /* penalty at the end of the run */
   int rho_changes;    /* number of penalty changes */
+  int restarts;       /* restarts of the accelerated iteration */
 } orc_result;
 
 /* Projection of (v_i, v_j) onto {a'(w_i - w_j) >= d}; returns theta >= 0 with
