@@ -16,4 +16,5 @@ from .generator import (  # noqa: F401
     random_scenario,
     build_scenario,
     nearest_neighbour_pairs,
+    heterogeneous_agents,
 )

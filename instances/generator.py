@@ -132,6 +132,10 @@ class Batch:
     # pair-step rows of `a` follow this list
     pair_count: Optional[np.ndarray] = None
     pair_ij: Optional[np.ndarray] = None
+    # heterogeneous agents: per-agent dynamics A_agent [sum N, nx, nx] and
+    # B_agent [sum N, nx, nu]; None = every agent has the shared A, B
+    A_agent: Optional[np.ndarray] = None
+    B_agent: Optional[np.ndarray] = None
 
     @property
     def n_scen(self) -> int:
@@ -184,6 +188,8 @@ class Batch:
             meta=dict(self.meta),
             pair_count=None if self.pair_count is None else self.pair_count[list(idx)].copy(),
             pair_ij=None if self.pair_ij is None else cat(self.pair_ij, self.pair_off),
+            A_agent=None if self.A_agent is None else cat(self.A_agent, ao),
+            B_agent=None if self.B_agent is None else cat(self.B_agent, ao),
         )
 
     def contiguous(self) -> "Batch":
@@ -291,6 +297,29 @@ def nearest_neighbour_pairs(batch: Batch, k: int) -> Batch:
                                pair_count=np.asarray(counts, dtype=np.int32),
                                pair_ij=(np.concatenate(lists).astype(np.int32) if lists else
                                         np.zeros((0, 2), dtype=np.int32)))
+
+
+def heterogeneous_agents(batch: Batch, seed: int, damping=(0.0, 0.5), mass=(0.8, 1.25)) -> Batch:
+    """Mixed models: agent i of the batch gets velocity damping c_i and mass m_i
+    (seeded, uniform in the given ranges) on the batch's double integrator,
+    v_{t+1} = (1 - c_i dt) v_t + (dt / m_i) u_t and p_{t+1} = p_t + dt v_t +
+    (dt^2 / 2m_i) u_t; everything else (costs, guesses, normals) unchanged."""
+    rng = np.random.default_rng(seed)
+    na = int(batch.N.sum())
+    dp, nx = batch.dp, batch.nx
+    dt = float(batch.A[0, dp])
+    c = rng.uniform(damping[0], damping[1], na)
+    m = rng.uniform(mass[0], mass[1], na)
+    I = np.eye(dp)
+    A = np.zeros((na, nx, nx))
+    B = np.zeros((na, nx, dp))
+    for i in range(na):
+        A[i, :dp, :dp] = I
+        A[i, :dp, dp:] = dt * I
+        A[i, dp:, dp:] = (1.0 - c[i] * dt) * I
+        B[i, :dp] = 0.5 * dt * dt / m[i] * I
+        B[i, dp:] = dt / m[i] * I
+    return dataclasses.replace(batch, A_agent=A, B_agent=B)
 
 
 WORKLOADS = {"pair": 1, "ring14": 2, "mixed": 3, "swarm3d": 4, "diff": 5}

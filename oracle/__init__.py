@@ -37,7 +37,7 @@ class Scenario(C.Structure):
                 ("A", _dp), ("B", _dp), ("Qd", _dp), ("Rd", _dp), ("Qfd", _dp),
                 ("x_init", _dp), ("x_ref", _dp), ("umin", _dp), ("umax", _dp),
                 ("a", _dp), ("w0", _dp), ("d_min", C.c_double), ("rho", C.c_double),
-                ("P", C.c_int), ("pairs", C.POINTER(C.c_int))]
+                ("P", C.c_int), ("pairs", C.POINTER(C.c_int)), ("Ai", _dp), ("Bi", _dp)]
 
 
 class Options(C.Structure):
@@ -165,12 +165,17 @@ class _ScenarioData:
         if listed:
             pl = np.ascontiguousarray(batch.pairs_of(k), dtype=np.int32).reshape(-1)
             self.keep["pairs"] = pl if pl.size else np.zeros(2, dtype=np.int32)
+        hetero = getattr(batch, "A_agent", None) is not None
+        if hetero:
+            self.keep["Ai"] = sl(batch.A_agent.reshape(-1, batch.nx * batch.nx), ao)
+            self.keep["Bi"] = sl(batch.B_agent.reshape(-1, batch.nx * batch.nu), ao)
         kp = self.keep
         self.s = Scenario(N, T, batch.nx, batch.nu, batch.dp, _d(kp["A"]), _d(kp["B"]), _d(kp["Qd"]),
                           _d(kp["Rd"]), _d(kp["Qfd"]), _d(kp["x_init"]), _d(kp["x_ref"]),
                           _d(kp["umin"]), _d(kp["umax"]), _d(kp["a"]), _d(kp["w0"]),
                           float(batch.d_min[k]), float(batch.rho[k]), self.P,
-                          kp["pairs"].ctypes.data_as(C.POINTER(C.c_int)) if listed else None)
+                          kp["pairs"].ctypes.data_as(C.POINTER(C.c_int)) if listed else None,
+                          _d(kp["Ai"]) if hetero else None, _d(kp["Bi"]) if hetero else None)
 
 
 class _ResultData:

@@ -38,6 +38,14 @@
 
 #define IDX2(i, j, ld) ((size_t)(i) * (size_t)(ld) + (size_t)(j))
 
+/* dynamics of agent i: its own (heterogeneous agents) or the shared model */
+static const double* agent_A(const orc_scenario* s, int i) {
+  return s->Ai ? s->Ai + (size_t)i * s->nx * s->nx : s->A;
+}
+static const double* agent_B(const orc_scenario* s, int i) {
+  return s->Bi ? s->Bi + (size_t)i * s->nx * s->nu : s->B;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Dense linear algebra                                                        */
 /* ------------------------------------------------------------------------- */
@@ -395,7 +403,7 @@ int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, 
     }
   }
   for (int c = 0; c < nu; ++c) Hu[c] = 2.0 * s->Rd[(size_t)i * nu + c];
-  orc_agent_qp q = {T, nx, nu, s->A, s->B, Hx, gx, Hu, s->x_init + (size_t)i * nx, s->umin, s->umax};
+  orc_agent_qp q = {T, nx, nu, agent_A(s, i), agent_B(s, i), Hx, gx, Hu, s->x_init + (size_t)i * nx, s->umin, s->umax};
   int st = orc_agent_qp_solve(&q, start, as_max, eps_rel, u, W, x, mu, n_eqp);
   free(Hx);
   free(gx);
@@ -454,7 +462,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   }
   for (size_t k = 0; k < (size_t)P * T; ++k) res->theta[k] = 0.0;
   for (size_t k = 0; k < (size_t)N * T * nu; ++k) { res->U[k] = 0.0; res->W[k] = 0; res->mu[k] = 0.0; }
-  for (int i = 0; i < N; ++i) simulate(T, nx, nu, s->A, s->B, s->x_init + (size_t)i * nx,
+  for (int i = 0; i < N; ++i) simulate(T, nx, nu, agent_A(s, i), agent_B(s, i), s->x_init + (size_t)i * nx,
                                        res->U + (size_t)i * T * nu, res->X + (size_t)i * (T + 1) * nx);
 
   for (int k = 0; k < o->max_iter; ++k) {
@@ -630,8 +638,8 @@ int orc_admm_batch(const orc_scenario* s, int n_scen, const orc_options* o, orc_
 
 typedef struct {
   int N, T, nx, nu, dp, P, m, nU, nC;
-  double* Phi;   /* [T+1][nx][nx]  A^t */
-  double* G;     /* [T][T][nx][nu] G[t-1][s] = A^{t-1-s} B for s < t, else 0 */
+  double* Phi;   /* [N][T+1][nx][nx]  A_i^t */
+  double* G;     /* [N][T][T][nx][nu] G_i[t-1][s] = A_i^{t-1-s} B_i for s < t, else 0 */
   double* H;     /* [nU][nU] */
   double* g;     /* [nU] */
   double* Nc;    /* [nC][nU] constraint rows, c_k(U) = Nc_k' U - bc_k >= 0 */
@@ -651,6 +659,10 @@ static void matmul(int n, int k, int m, const double* X, const double* Y, double
     }
 }
 
+/* agent i's blocks: Phi_t [nx][nx] for t = 0..T and G for x_t (t = 1..T) and u_s [nx][nu] */
+#define PHI(Q, i, t) ((Q)->Phi + ((size_t)(i) * ((Q)->T + 1) + (t)) * (Q)->nx * (Q)->nx)
+#define GM(Q, i, t, s) ((Q)->G + (((size_t)(i) * (Q)->T + (t) - 1) * (Q)->T + (s)) * (Q)->nx * (Q)->nu)
+
 /* Builds prediction matrices, the condensed Hessian/gradient of Eq. (1) (exact
  * objective, written as 1/2 U'HU + g'U + const) and all constraint rows:
  * bounds (agent, t, c; lower then upper) followed by halfspaces (pair, t). */
@@ -662,19 +674,20 @@ static int global_build(const orc_scenario* s, global_qp* Q) {
   if (Q->P < 0) return -1;
   free(ptab);
   Q->m = T * nu; Q->nU = N * Q->m; Q->nC = 2 * Q->nU + Q->P * T;
-  Q->Phi = (double*)calloc((size_t)(T + 1) * nx * nx, sizeof(double));
-  Q->G = (double*)calloc((size_t)T * T * nx * nu, sizeof(double));
+  Q->Phi = (double*)calloc((size_t)N * (T + 1) * nx * nx, sizeof(double));
+  Q->G = (double*)calloc((size_t)N * T * T * nx * nu, sizeof(double));
   Q->H = (double*)calloc((size_t)Q->nU * Q->nU, sizeof(double));
   Q->g = (double*)calloc((size_t)Q->nU, sizeof(double));
   Q->Nc = (double*)calloc((size_t)Q->nC * Q->nU, sizeof(double));
   Q->bc = (double*)calloc((size_t)Q->nC, sizeof(double));
   if (!Q->Phi || !Q->G || !Q->H || !Q->g || !Q->Nc || !Q->bc) return -1;
-  for (int r = 0; r < nx; ++r) Q->Phi[IDX2(r, r, nx)] = 1.0;
-  for (int t = 1; t <= T; ++t) matmul(nx, nx, nx, s->A, Q->Phi + (size_t)(t - 1) * nx * nx, Q->Phi + (size_t)t * nx * nx);
-  for (int t = 1; t <= T; ++t)
-    for (int sidx = 0; sidx < t; ++sidx)
-      matmul(nx, nx, nu, Q->Phi + (size_t)(t - 1 - sidx) * nx * nx, s->B,
-             Q->G + ((size_t)(t - 1) * T + sidx) * nx * nu);
+  /* per agent: Phi_t = A^t and G[t-1][s] = A^(t-1-s) B, the response of x_t to u_s */
+  for (int i = 0; i < N; ++i) {
+    for (int r = 0; r < nx; ++r) PHI(Q, i, 0)[IDX2(r, r, nx)] = 1.0;
+    for (int t = 1; t <= T; ++t) matmul(nx, nx, nx, agent_A(s, i), PHI(Q, i, t - 1), PHI(Q, i, t));
+    for (int t = 1; t <= T; ++t)
+      for (int sidx = 0; sidx < t; ++sidx) matmul(nx, nx, nu, PHI(Q, i, t - 1 - sidx), agent_B(s, i), GM(Q, i, t, sidx));
+  }
   const int m = Q->m, nU = Q->nU;
   double* xf = (double*)malloc(sizeof(double) * nx);
   for (int i = 0; i < N; ++i) {
@@ -687,19 +700,19 @@ static int global_build(const orc_scenario* s, global_qp* Q) {
       const double* Qt = (t < T) ? Qi : Qfi;
       for (int r = 0; r < nx; ++r) {
         double acc = 0.0;
-        for (int c = 0; c < nx; ++c) acc += Q->Phi[(size_t)t * nx * nx + IDX2(r, c, nx)] * x0[c];
+        for (int c = 0; c < nx; ++c) acc += PHI(Q, i, t)[IDX2(r, c, nx)] * x0[c];
         xf[r] = acc - xr[r];
       }
       /* row r of x_t as a function of U_i: sum_s G[t-1][s][r][:] u_s */
       for (int r = 0; r < nx; ++r) {
         for (int s1 = 0; s1 < t; ++s1)
           for (int c1 = 0; c1 < nu; ++c1) {
-            double g1 = Q->G[((size_t)(t - 1) * T + s1) * nx * nu + IDX2(r, c1, nu)];
+            double g1 = GM(Q, i, t, s1)[IDX2(r, c1, nu)];
             if (g1 == 0.0) continue;
             Q->g[off + s1 * nu + c1] += 2.0 * Qt[r] * g1 * xf[r];
             for (int s2 = 0; s2 < t; ++s2)
               for (int c2 = 0; c2 < nu; ++c2) {
-                double g2 = Q->G[((size_t)(t - 1) * T + s2) * nx * nu + IDX2(r, c2, nu)];
+                double g2 = GM(Q, i, t, s2)[IDX2(r, c2, nu)];
                 Q->H[IDX2(off + s1 * nu + c1, off + s2 * nu + c2, nU)] += 2.0 * Qt[r] * g1 * g2;
               }
           }
@@ -728,15 +741,14 @@ static int global_build(const orc_scenario* s, global_qp* Q) {
         for (int c = 0; c < dp; ++c) {
           double fi = 0.0, fj = 0.0;
           for (int l = 0; l < nx; ++l) {
-            fi += Q->Phi[(size_t)t * nx * nx + IDX2(c, l, nx)] * s->x_init[(size_t)i * nx + l];
-            fj += Q->Phi[(size_t)t * nx * nx + IDX2(c, l, nx)] * s->x_init[(size_t)j * nx + l];
+            fi += PHI(Q, i, t)[IDX2(c, l, nx)] * s->x_init[(size_t)i * nx + l];
+            fj += PHI(Q, j, t)[IDX2(c, l, nx)] * s->x_init[(size_t)j * nx + l];
           }
           rhs -= a[c] * (fi - fj);
           for (int s1 = 0; s1 < t; ++s1)
             for (int c1 = 0; c1 < nu; ++c1) {
-              double gv = Q->G[((size_t)(t - 1) * T + s1) * nx * nu + IDX2(c, c1, nu)];
-              nr[i * m + s1 * nu + c1] += a[c] * gv;
-              nr[j * m + s1 * nu + c1] -= a[c] * gv;
+              nr[i * m + s1 * nu + c1] += a[c] * GM(Q, i, t, s1)[IDX2(c, c1, nu)];
+              nr[j * m + s1 * nu + c1] -= a[c] * GM(Q, j, t, s1)[IDX2(c, c1, nu)];
             }
         }
         Q->bc[row] = rhs;
@@ -784,7 +796,7 @@ static int global_eqp(const global_qp* Q, const uint8_t* Wset, double* U, double
 
 static void global_outputs(const orc_scenario* s, const global_qp* Q, const double* U, double* X) {
   for (int i = 0; i < s->N; ++i)
-    simulate(s->T, s->nx, s->nu, s->A, s->B, s->x_init + (size_t)i * s->nx, U + (size_t)i * Q->m,
+    simulate(s->T, s->nx, s->nu, agent_A(s, i), agent_B(s, i), s->x_init + (size_t)i * s->nx, U + (size_t)i * Q->m,
              X + (size_t)i * (s->T + 1) * s->nx);
 }
 
@@ -914,7 +926,7 @@ int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_
         for (int s1 = 0; s1 < t; ++s1)
           for (int c1 = 0; c1 < nu; ++c1)
             dl[i * m + s1 * nu + c1] +=
-                2.0 * e * Q.G[((size_t)(t - 1) * T + s1) * nx * nu + IDX2(c, c1, nu)];
+                2.0 * e * GM((&Q), i, t, s1)[IDX2(c, c1, nu)];
       }
   *loss = L;
   /* adjoint: K w = [dl/dU; 0] with the (symmetric) KKT matrix of the active set */
@@ -958,14 +970,14 @@ int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_
       for (int t = 1; t <= T; ++t) {
         double wt = (t < T) ? 1.0 : qf_tie;
         double xf = -xr[r];
-        for (int l = 0; l < nx; ++l) xf += Q.Phi[(size_t)t * nx * nx + IDX2(r, l, nx)] * x0[l];
+        for (int l = 0; l < nx; ++l) xf += PHI((&Q), i, t)[IDX2(r, l, nx)] * x0[l];
         for (int s1 = 0; s1 < t; ++s1)
           for (int c1 = 0; c1 < nu; ++c1) {
-            double g1 = Q.G[((size_t)(t - 1) * T + s1) * nx * nu + IDX2(r, c1, nu)];
+            double g1 = GM((&Q), i, t, s1)[IDX2(r, c1, nu)];
             dg[s1 * nu + c1] += 2.0 * wt * g1 * xf;
             for (int s2 = 0; s2 < t; ++s2)
               for (int c2 = 0; c2 < nu; ++c2) {
-                double g2 = Q.G[((size_t)(t - 1) * T + s2) * nx * nu + IDX2(r, c2, nu)];
+                double g2 = GM((&Q), i, t, s2)[IDX2(r, c2, nu)];
                 dH[IDX2(s1 * nu + c1, s2 * nu + c2, m)] += 2.0 * wt * g1 * g2;
               }
           }
@@ -991,7 +1003,7 @@ int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_
         double qt = (t < T) ? Qi[r] : qf_tie * Qi[r];
         for (int s1 = 0; s1 < t; ++s1)
           for (int c1 = 0; c1 < nu; ++c1)
-            dg[s1 * nu + c1] -= 2.0 * qt * Q.G[((size_t)(t - 1) * T + s1) * nx * nu + IDX2(r, c1, nu)];
+            dg[s1 * nu + c1] -= 2.0 * qt * GM((&Q), i, t, s1)[IDX2(r, c1, nu)];
       }
       double acc = 0.0;
       for (int a1 = 0; a1 < m; ++a1) acc += wi[a1] * dg[a1];

@@ -79,6 +79,8 @@ typedef struct {
   const int *pairs;                    /* [P][2] coupled pairs (i < j); NULL: all N(N-1)/2 pairs in
                                           lexicographic order.  Agent i's copy count n_c is its
                                           number of pairs. */
+  const double *Ai, *Bi;               /* heterogeneous agents: [N][nx][nx], [N][nx][nu] per-agent
+                                          dynamics; NULL: every agent has the shared A, B */
 } orc_scenario;
 
 typedef struct {

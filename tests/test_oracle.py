@@ -266,7 +266,9 @@ def _global_kkt_check(b, g, tol):
     for i in range(N):
         Hx = np.tile(2 * b.Qd[i], (T, 1))
         Hx[-1] = 2 * b.Qfd[i]
-        H, gg, F, G = agent_condensed_qp(b.A, b.B, Hx, -Hx * b.x_ref[i], 2 * b.Rd[i], b.x_init[i])
+        Ai = b.A if b.A_agent is None else b.A_agent[i]
+        Bi = b.B if b.B_agent is None else b.B_agent[i]
+        H, gg, F, G = agent_condensed_qp(Ai, Bi, Hx, -Hx * b.x_ref[i], 2 * b.Rd[i], b.x_init[i])
         Hs.append(H); gs.append(gg); Fs.append(F); Gs.append(G)
     U = g["U"].reshape(N, m)
     grad = np.stack([Hs[i] @ U[i] + gs[i] for i in range(N)])
@@ -342,6 +344,40 @@ def test_residual_balancing_never_due_is_plain_admm():
     r1 = oracle.admm(b, 0, tol=0.0, max_iter=30, adapt=(31, 10.0, 2.0))
     assert r1["rho_changes"] == 0 and r1["rho_final"] == b.rho[0]
     assert np.array_equal(r0["X"], r1["X"]) and np.array_equal(r0["theta"], r1["theta"])
+
+
+def test_heterogeneous_agents_equal_models_are_the_shared_run():
+    """Per-agent dynamics that all equal the shared model reproduce the shared
+    run bit for bit (ADMM iterates and the global QP)."""
+    b = random_scenario(seed=3, N=3, T=8, box=1.5, rho=0.5)
+    na = int(b.N.sum())
+    bh = dataclasses.replace(b, A_agent=np.tile(b.A, (na, 1, 1)), B_agent=np.tile(b.B, (na, 1, 1)))
+    r0 = oracle.admm(b, 0, tol=0.0, max_iter=30)
+    r1 = oracle.admm(bh, 0, tol=0.0, max_iter=30)
+    assert np.array_equal(r0["X"], r1["X"]) and np.array_equal(r0["theta"], r1["theta"])
+    g0, g1 = oracle.global_qp(b, 0), oracle.global_qp(bh, 0)
+    assert np.array_equal(g0["X"], g1["X"]) and np.array_equal(g0["mu_h"], g1["mu_h"])
+
+
+@pytest.mark.parametrize("seed,N,T", [(3, 3, 8), (5, 4, 10)])
+def test_heterogeneous_agents_global_qp_and_admm_fixed_point(seed, N, T):
+    """Mixed models (per-agent damping and mass): the oracle's condensed global
+    QP satisfies the KKT conditions written with each agent's own A_i, B_i
+    (numpy condensing), and its ADMM converges to that optimum."""
+    from instances import heterogeneous_agents
+    b = heterogeneous_agents(random_scenario(seed=seed, N=N, T=T, box=1.5, rho=20.0), seed=seed)
+    assert not np.allclose(b.A_agent[0], b.A_agent[1])
+    g = oracle.global_qp(b, 0)
+    assert g["status"] == oracle.CONVERGED and g["act_h"].sum() > 0
+    _global_kkt_check(b, g, 1e-8)
+    r = oracle.admm(b, 0, tol=1e-10, max_iter=40000)
+    assert r["status"] == oracle.CONVERGED
+    assert np.abs(r["X"] - g["X"]).max() <= 1e-7
+    assert np.abs(b.rho[0] * r["theta"] - g["mu_h"]).max() <= 1e-5 * max(1, g["mu_h"].max())
+    assert np.array_equal(r["W"], g["W"])
+    # the shared-model run is a different problem
+    g0 = oracle.global_qp(dataclasses.replace(b, A_agent=None, B_agent=None), 0)
+    assert np.abs(g0["X"] - g["X"]).max() > 1e-3
 
 
 def test_over_relaxation_alpha_one_is_plain_admm():
@@ -499,11 +535,15 @@ def _loss(X, targets, dp):
     return float(((X[:, 1:, :dp] - targets.reshape(N, T1 - 1, dp)) ** 2).sum())
 
 
-@pytest.mark.parametrize("seed", [1, 4])
-def test_gradient_matches_central_differences(seed):
+@pytest.mark.parametrize("seed,hetero", [(1, False), (4, False), (3, True)])
+def test_gradient_matches_central_differences(seed, hetero):
     """Implicit-KKT gradient at the final active set equals central finite
-    differences (h = 1e-6) of the re-solved centralized QP."""
+    differences (h = 1e-6) of the re-solved centralized QP (also with per-agent
+    dynamics)."""
     b = random_scenario(seed=seed, N=3, T=6, box=1.5)
+    if hetero:
+        from instances import heterogeneous_agents
+        b = heterogeneous_agents(b, seed=seed)
     rng = np.random.default_rng(seed)
     targets = rng.uniform(-2, 2, size=(3 * 6, 2))
     g = oracle.global_qp(b, 0)
