@@ -90,6 +90,13 @@ typedef struct {
    * of `a`; agent i's number of consensus copies n_c is its number of pairs. */
   const int32_t* pair_count;
   const int32_t* pair_ij;
+  /* Heterogeneous agents (an extension: the paper's agents share one model).
+   * NULL (both): every agent has A, B above.  Otherwise per-agent dynamics
+   * A_agent [sum N][nx][nx] and B_agent [sum N][nx][nu], row-major, agents in
+   * scenario order; the input box stays shared.  The products are then the
+   * dense ones; not with TADMM_FLAG_DOUBLE_FLOAT (EINVAL). */
+  const double* A_agent;
+  const double* B_agent;
 } tadmm_batch;
 
 typedef struct {

@@ -32,7 +32,8 @@ class TadmmBatch(C.Structure):
     _fields_ = [("n_scen", C.c_int32), ("nx", C.c_int32), ("nu", C.c_int32), ("dp", C.c_int32),
                 ("N", _i32p), ("T", _i32p), ("A", _dp), ("B", _dp), ("umin", _dp), ("umax", _dp),
                 ("Qd", _dp), ("Rd", _dp), ("Qfd", _dp), ("x_init", _dp), ("x_ref", _dp), ("a", _dp),
-                ("w0", _dp), ("d_min", _dp), ("rho", _dp), ("pair_count", _i32p), ("pair_ij", _i32p)]
+                ("w0", _dp), ("d_min", _dp), ("rho", _dp), ("pair_count", _i32p), ("pair_ij", _i32p),
+                ("A_agent", _dp), ("B_agent", _dp)]
 
 
 class TadmmOptions(C.Structure):
@@ -101,6 +102,9 @@ class _HostBatch:
                       Qfd=batch.Qfd, x_init=batch.x_init, x_ref=batch.x_ref,
                       a=batch.a if batch.a.size else np.zeros((1, batch.dp)), w0=batch.w0,
                       d_min=batch.d_min, rho=batch.rho)
+        hetero = getattr(batch, "A_agent", None) is not None
+        if hetero:
+            fields.update(A_agent=batch.A_agent, B_agent=batch.B_agent)
         self.keep = {k: _f64(v) for k, v in fields.items()}
         if pinned:
             import torch
@@ -120,7 +124,8 @@ class _HostBatch:
                             ptr["Qd"], ptr["Rd"], ptr["Qfd"], ptr["x_init"], ptr["x_ref"],
                             None if not batch.a.size else ptr["a"], ptr["w0"], ptr["d_min"], ptr["rho"],
                             self.pc.ctypes.data_as(_i32p) if listed else None,
-                            self.pij.ctypes.data_as(_i32p) if listed else None)
+                            self.pij.ctypes.data_as(_i32p) if listed else None,
+                            ptr["A_agent"] if hetero else None, ptr["B_agent"] if hetero else None)
 
 
 class Solver:

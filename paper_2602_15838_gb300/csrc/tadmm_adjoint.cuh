@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
         Pt[c][r] = v;
       };
       auto putB = [](int, int, F) {};
-      bad |= factor_stage<F, NX, NU, DI>(Mo, Pn, mask, rbar, t >= 1 ? qbar : nullptr, 1, put, putB, K, L);
+      bad |= factor_stage<F, NX, NU, DI>(agent_model<F, NX, NU>(D, Mo, s, i), Pn, mask, rbar, t >= 1 ? qbar : nullptr, 1, put, putB, K, L);
 #pragma unroll
       for (int r = 0; r < NU; ++r) {
 #pragma unroll
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
         }
       };
       auto outu = [&](int, const F (&)[NU]) {};
-      lq_solve<F, NX, NU, DI>(Mo, cache, Wm, N, i, T, lin, zero0, false, kk, outx, outu);
+      lq_solve<F, NX, NU, DI>(agent_model<F, NX, NU>(D, Mo, s, i), cache, Wm, N, i, T, lin, zero0, false, kk, outx, outu);
     }
   }
   __syncthreads();
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
       }
     };
     auto outu = [&](int, const F (&)[NU]) {};
-    lq_solve<F, NX, NU, DI>(Mo, cache, Wm, N, i, T, lin, x0, true, kk, outx, outu);
+    lq_solve<F, NX, NU, DI>(agent_model<F, NX, NU>(D, Mo, s, i), cache, Wm, N, i, T, lin, x0, true, kk, outx, outu);
   }
   __syncthreads();
 
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
 #pragma unroll
       for (int c = 0; c < NU; ++c) Up[(size_t)t * NU + c] = u[c];
     };
-    lq_solve<F, NX, NU, DI>(Mo, cache, Wm, N, i, T, lin, x0, true, kk, outx, outu);
+    lq_solve<F, NX, NU, DI>(agent_model<F, NX, NU>(D, Mo, s, i), cache, Wm, N, i, T, lin, x0, true, kk, outx, outu);
   }
   __syncthreads();
 
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
       }
     };
     auto outu = [&](int, const F (&)[NU]) {};
-    lq_solve<F, NX, NU, DI>(Mo, cache, Wm, N, i, T, lin, zero0, false, kk, outx, outu);
+    lq_solve<F, NX, NU, DI>(agent_model<F, NX, NU>(D, Mo, s, i), cache, Wm, N, i, T, lin, zero0, false, kk, outx, outu);
   }
   __syncthreads();
   for (int h = tid; h < m; h += nt) {
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
 #pragma unroll
       for (int c = 0; c < NU; ++c) Wu[(size_t)t * NU + c] = u[c];
     };
-    lq_solve<F, NX, NU, DI>(Mo, cache, Wm, N, i, T, lin, zero0, false, kk, outx, outu);
+    lq_solve<F, NX, NU, DI>(agent_model<F, NX, NU>(D, Mo, s, i), cache, Wm, N, i, T, lin, zero0, false, kk, outx, outu);
   }
   __syncthreads();
 

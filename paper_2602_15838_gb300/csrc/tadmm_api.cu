@@ -107,6 +107,12 @@ static int validate(const tadmm_batch* b, const tadmm_handle* shape) {
   }
   if (nps > 0 && !b->a) return set_error(TADMM_EINVAL, "a is NULL but the batch has pairs");
   const int nx = b->nx, nu = b->nu, dp = b->dp;
+  if ((b->A_agent == nullptr) != (b->B_agent == nullptr))
+    return set_error(TADMM_EINVAL, "A_agent and B_agent are both NULL or both set");
+  if (shape && (shape->hetero != 0) != (b->A_agent != nullptr))
+    return set_error(TADMM_EINVAL, "update: per-agent dynamics differ from the handle");
+  if (b->A_agent && (!finite_all(b->A_agent, na * nx * nx) || !finite_all(b->B_agent, na * nx * nu)))
+    return set_error(TADMM_EINVAL, "A_agent, B_agent must be finite");
   if (!finite_all(b->A, nx * nx) || !finite_all(b->B, nx * nu)) return set_error(TADMM_EINVAL, "A, B must be finite");
   for (int c = 0; c < nu; ++c)
     if (!std::isfinite(b->umin[c]) || !std::isfinite(b->umax[c]) || b->umin[c] > b->umax[c])
@@ -157,7 +163,7 @@ static void free_all(tadmm_handle* h) {
   for (void* p : ptrs0)
     if (p) cudaFree(p);
   void* ptrs[] = {h->meta,   h->order, h->pairs, h->deg, h->adj_ptr, h->adj, h->pair_scen, h->agent_scen, h->model, h->Qd,     h->Rd,
-                  h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->phi, h->sx, h->X,      h->h,
+                  h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->phi, h->sx, h->models, h->st_models, h->X, h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
                   h->res,    h->eqp,   h->fact,  h->rho_out, h->rho_chg, h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
                   h->ex_buf, h->flag,  h->red2};
@@ -211,6 +217,20 @@ static int upload_inputs(tadmm_handle* h, const tadmm_batch* b, cudaStream_t st)
   cudaMemcpyAsync(ag + 3 * na * nx + na * nu, b->x_ref, sizeof(double) * na * nx, cudaMemcpyHostToDevice, st);
   if (h->tot_ps > 0) cudaMemcpyAsync(h->st_a, b->a, sizeof(double) * h->tot_ps * dp, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(h->st_w0, b->w0, sizeof(double) * h->tot_as * dp, cudaMemcpyHostToDevice, st);
+  if (h->hetero) {
+    // per-agent models in the device layout [agent][A, B, umin, umax]
+    const int nm = nx * nx + nx * nu + 2 * nu;
+    cudaStreamSynchronize(st);  // the host packing may still feed an earlier copy
+    h->models_h.resize((size_t)na * nm);
+    for (int64_t i = 0; i < na; ++i) {
+      double* d = h->models_h.data() + (size_t)i * nm;
+      std::copy(b->A_agent + i * nx * nx, b->A_agent + (i + 1) * nx * nx, d);
+      std::copy(b->B_agent + i * nx * nu, b->B_agent + (i + 1) * nx * nu, d + nx * nx);
+      std::copy(b->umin, b->umin + nu, d + nx * nx + nx * nu);
+      std::copy(b->umax, b->umax + nu, d + nx * nx + nx * nu + nu);
+    }
+    cudaMemcpyAsync(h->st_models, h->models_h.data(), sizeof(double) * na * nm, cudaMemcpyHostToDevice, st);
+  }
   if ((rc = cuda_check(cudaGetLastError(), "input copies"))) return rc;
   TADMM_DISPATCH(h, import_inputs(h, st));
 }
@@ -256,6 +276,8 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
     for (int s2 = 0; s2 < b->n_scen; ++s2)
       if (b->N[s2] > 32) return set_error(TADMM_EINVAL, "over-relaxation supports scenarios of at most 32 agents");
   }
+  if ((o.flags & TADMM_FLAG_DOUBLE_FLOAT) && b->A_agent)
+    return set_error(TADMM_EINVAL, "TADMM_FLAG_DOUBLE_FLOAT does not take per-agent dynamics");
   if ((o.flags & TADMM_FLAG_DOUBLE_FLOAT) && (o.precision != 64 || b->nx != 4))
     return set_error(TADMM_EINVAL, "TADMM_FLAG_DOUBLE_FLOAT needs precision 64 and (nx, nu, dp) = (4, 2, 2)");
   tadmm_handle* h = new tadmm_handle();
@@ -268,7 +290,8 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   h->tpc = o.threads_per_cta;
   h->cps = o.ctas_per_sm;
   h->variant = o.kernel_variant;
-  h->di = (!(o.flags & TADMM_FLAG_NO_STRUCTURE) && is_double_integrator(b)) ? 1 : 0;
+  h->hetero = b->A_agent ? 1 : 0;
+  h->di = (!(o.flags & TADMM_FLAG_NO_STRUCTURE) && !h->hetero && is_double_integrator(b)) ? 1 : 0;
   h->N.assign(b->N, b->N + b->n_scen);
   h->T.assign(b->T, b->T + b->n_scen);
   h->meta_h.resize(b->n_scen);
@@ -427,7 +450,9 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
       (rc = dmalloc(&h->st_agent, 8 * na * (4 * nx + nu))) || (rc = dmalloc(&h->st_a, 8 * h->tot_ps * dp)) ||
       (rc = dmalloc(&h->st_w0, 8 * h->tot_as * dp)) || (rc = dmalloc(&h->ex_buf, h->ex_bytes + h->tot_as * nu + 16)) ||
       (rc = dmalloc(&h->flag, 16)) || (rc = dmalloc(&h->red2, 16)) ||
-      (o.relax_alpha != 1.0 && ((rc = dmalloc(&h->phi, fs * h->tot_ps)) || (rc = dmalloc(&h->sx, fs * h->tot_as * dp))))) {
+      (o.relax_alpha != 1.0 && ((rc = dmalloc(&h->phi, fs * h->tot_ps)) || (rc = dmalloc(&h->sx, fs * h->tot_as * dp)))) ||
+      (h->hetero && ((rc = dmalloc(&h->models, fs * na * (nx * nx + nx * nu + 2 * nu))) ||
+                     (rc = dmalloc(&h->st_models, 8 * na * (nx * nx + nx * nu + 2 * nu)))))) {
     free_all(h);
     return rc;
   }

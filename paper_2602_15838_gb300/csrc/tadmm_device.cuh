@@ -97,6 +97,7 @@ struct Dev {
   double alpha;
   F* phi;                    // [tot_ps] pair part phi of the consensus copies w = s +/- phi a
   F* sx;                     // [tot_as][dp] agent part s of the consensus copies
+  const F* models;           // heterogeneous agents: [agents] Model (A, B, umin, umax), or nullptr
   double* rho_out;           // [n_scen] final rho (batched mode), or nullptr
   int32_t* rho_chg;          // [n_scen] number of rho changes
   const int32_t* deg;        // [agents] consensus copies n_c of each agent (its pairs)
@@ -1403,15 +1404,23 @@ __device__ void init_phase(const Dev<F>& D, const ScenMeta& s, int64_t t0, int64
   }
 }
 
+// Dynamics of agent i of scenario s: its own when the batch has per-agent
+// models (heterogeneous agents), else the shared model M.
+template <typename F, int NX, int NU>
+__device__ __forceinline__ const Model<F, NX, NU>& agent_model(const Dev<F>& D, const Model<F, NX, NU>& M,
+                                                              const ScenMeta& s, int i) {
+  return D.models ? reinterpret_cast<const Model<F, NX, NU>*>(D.models)[s.agent_off + i] : M;
+}
+
 // Agent context of agent i; its constants are written to the thread's column
 // kc (stride ks) of a shared-memory table.
-template <typename F, int NX, int NU, int DP>
+template <typename F, int NX, int NU, int DP, bool DI>
 __device__ __forceinline__ AgentCtx<F, NX, NU, DP> make_agent(const Dev<F>& D, const Model<F, NX, NU>& M,
                                                               const ScenMeta& s, int i, int lvl_out, F* kc,
                                                               int ks, double rho) {
   using AC = AgentConst<NX, NU>;
   AgentCtx<F, NX, NU, DP> A;
-  A.M = &M;
+  A.M = DI ? &M : &agent_model<F, NX, NU>(D, M, s, i);  // the structured path has one model
   A.N = s.N;
   A.T = s.T;
   A.i = i;
@@ -1491,7 +1500,7 @@ __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const S
   for (int r = 0; r < rounds; ++r) {
     const bool has = r < mine;
     const AgentCtx<F, NX, NU, DP> A =
-        has ? make_agent<F, NX, NU, DP>(D, M, s, i0 + r * stride, lvl_out, kcs + threadIdx.x, blockDim.x, s.rho)
+        has ? make_agent<F, NX, NU, DP, DI>(D, M, s, i0 + r * stride, lvl_out, kcs + threadIdx.x, blockDim.x, s.rho)
             : idle_agent<F, NX, NU, DP>(M, kcs + threadIdx.x, blockDim.x, D.coop);
     const int res = xupdate_agent<F, NX, NU, DP, DI, COOP_EQP>(A, has, kind, as_max, eps, neqp, nfact);
     if (has && res > st) st = res;
@@ -2061,7 +2070,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     {
       const bool has = my_m >= 0 && gs.active[my_m] != 0;
       const ScenMeta& s = gs.meta[has ? my_m : 0];
-      const AgentCtx<F, NX, NU, DP> A = has ? make_agent<F, NX, NU, DP>(D, M, s, my_i, xl ^ 1, kcs + tid, nt,
+      const AgentCtx<F, NX, NU, DP> A = has ? make_agent<F, NX, NU, DP, DI>(D, M, s, my_i, xl ^ 1, kcs + tid, nt,
                                                                         gs.rho[my_m])
                                             : idle_agent<F, NX, NU, DP>(M, kcs + tid, nt, D.coop);
       const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;

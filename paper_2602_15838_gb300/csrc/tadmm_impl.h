@@ -53,6 +53,10 @@ struct tadmm_handle {
   void* a = nullptr;
   void* w0 = nullptr;
   void* theta = nullptr;
+  void* models = nullptr;        // heterogeneous agents: [tot_agents] per-agent model (A, B, umin, umax)
+  double* st_models = nullptr;   // their float64 staging
+  std::vector<double> models_h;  // host packing of the caller's per-agent A, B (kept for async copies)
+  int hetero = 0;                // 1: per-agent dynamics
   void* phi = nullptr;           // over-relaxation: [tot_ps] pair part of the consensus copies
   void* sx = nullptr;            // over-relaxation: [tot_as][dp] agent part of the consensus copies
   void* X = nullptr;

@@ -486,6 +486,7 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.relax = h->opt.relax_alpha != 1.0 ? 1 : 0;
   D.alpha = h->opt.relax_alpha;
   D.phi = (F*)h->phi;
+  D.models = (const F*)h->models;
   D.sx = (F*)h->sx;
   D.rho_out = h->rho_out;
   D.rho_chg = h->rho_chg;
@@ -542,6 +543,8 @@ int Impl<F, NX, NU, DP>::import_inputs(tadmm_handle* h, cudaStream_t st) {
     k_import_a<F, DP><<<grid_for(h->tot_pairs, 256), 256, 0, st>>>(h->meta, h->pair_scen, h->st_a, (F*)h->a,
                                                                     h->tot_pairs);
   k_import_w0<F, DP><<<grid_for(na, 128), 128, 0, st>>>(h->meta, h->agent_scen, h->st_w0, (F*)h->w0, na);
+  if (h->hetero)
+    k_convert<F><<<grid_for(na * nm, 256), 256, 0, st>>>(h->st_models, (F*)h->models, na * nm);
   return cuda_check(cudaGetLastError(), "import kernels");
 }
 

@@ -45,6 +45,8 @@ def test_version_and_last_error(libtadmm):
 
 def _create_rc(tg, batch, **opt):
     hb = tg._HostBatch(batch)
+    if opt.get("null_B_agent"):
+        hb.s.B_agent = None
     ae, am, at = opt.get("adapt", (0, 10.0, 2.0))
     o = tg.TadmmOptions(opt.get("precision", 64), opt.get("start", 2), 0, 0.0, opt.get("mode", 0), 0, 0, 0,
                         opt.get("flags", 0), ae, am, at, opt.get("relax", 0.0))
@@ -54,7 +56,8 @@ def _create_rc(tg, batch, **opt):
 
 
 @pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec", "adapt_mode", "adapt_mu",
-                                   "pair_dup", "pair_order", "relax_range", "relax_mode", "relax_flags"])
+                                   "pair_dup", "pair_order", "relax_range", "relax_mode", "relax_flags",
+                                   "hetero_half", "hetero_nan", "hetero_df64"])
 def test_invalid_inputs_rejected_on_host(libtadmm, fault):
     tg, _ = libtadmm
     from instances import make_workload
@@ -79,6 +82,15 @@ def test_invalid_inputs_rejected_on_host(libtadmm, fault):
         opt["adapt"] = (5, 10.0, 2.0)
     elif fault == "adapt_mu":
         opt["adapt"] = (5, 1.0, 2.0)
+    elif fault in ("hetero_half", "hetero_nan", "hetero_df64"):   # per-agent dynamics
+        from instances import heterogeneous_agents
+        b = heterogeneous_agents(b, seed=1)
+        if fault == "hetero_half":
+            opt["null_B_agent"] = True
+        elif fault == "hetero_nan":
+            b.A_agent[1, 0, 0] = np.nan
+        else:
+            opt["flags"] = 8
     elif fault == "relax_range":   # over-relaxation factor in (0, 2)
         opt["relax"] = 2.0
     elif fault == "relax_mode":    # over-relaxation runs in the batched mode only

@@ -51,21 +51,25 @@ def _rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(1.0, np.abs(np.asarray(b)).max()))
 
 
-def _case(N, T, n_scen=2, knn=None):
+def _case(N, T, n_scen=2, knn=None, hetero=False):
     b = make_workload("diff", n_scen=n_scen, N_override=N, T_override=T)
     if knn is not None:
         from instances import nearest_neighbour_pairs
         b = nearest_neighbour_pairs(b, knn)
+    if hetero:
+        from instances import heterogeneous_agents
+        b = heterogeneous_agents(b, seed=11)
     return b
 
 
-@pytest.mark.parametrize("precision,tol,N,T,iters,n_scen,knn", [
-    (64, 1e-6, 6, 12, 40, 2, None), (64, 1e-6, 10, 20, 300, 2, None),
-    (32, 1e-3, 6, 12, 40, 2, None), (32, 1e-3, 10, 20, 300, 2, None),
-    (64, 1e-6, 10, 20, 300, 2, 3)])
-def test_gradient_matches_oracle_dense_kkt(tg, precision, tol, N, T, iters, n_scen, knn):
-    """(knn: coupling only each agent's knn nearest neighbours.)"""
-    b = _case(N, T, n_scen, knn)
+@pytest.mark.parametrize("precision,tol,N,T,iters,n_scen,knn,hetero", [
+    (64, 1e-6, 6, 12, 40, 2, None, False), (64, 1e-6, 10, 20, 300, 2, None, False),
+    (32, 1e-3, 6, 12, 40, 2, None, False), (32, 1e-3, 10, 20, 300, 2, None, False),
+    (64, 1e-6, 10, 20, 300, 2, 3, False), (64, 1e-6, 10, 20, 300, 2, None, True)])
+def test_gradient_matches_oracle_dense_kkt(tg, precision, tol, N, T, iters, n_scen, knn, hetero):
+    """(knn: coupling only each agent's knn nearest neighbours; hetero: per-agent
+    dynamics.)"""
+    b = _case(N, T, n_scen, knn, hetero)
     s = tg.Solver(b, precision=precision)
     s.solve(0.0, iters)
     sol = s.solution()

@@ -463,6 +463,36 @@ def test_over_relaxation_converged_against_oracle(tg):
     assert ok
 
 
+@pytest.mark.parametrize("mode,it", [("batched", 7), ("batched", 23), ("plain", 9), ("graph", 9)])
+def test_heterogeneous_agents_match_oracle(tg, mode, it):
+    """Per-agent dynamics (seeded damping and mass per agent) in every mode:
+    every iterate within 1e-9 of the oracle's, which condenses and solves with
+    each agent's own A_i, B_i."""
+    from instances import heterogeneous_agents
+    b = heterogeneous_agents(make_workload("mixed", n_scen=6), seed=7)
+    g = gpu_run(tg, b, 0.0, it, mode=mode)[0]
+    for k in range(b.n_scen):
+        o = oracle.admm(b, k, tol=0.0, max_iter=it)
+        assert g[k]["iters"] == o["iters"] == it, k
+        assert rel(g[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(g[k]["U"], o["U"]) <= 1e-9, k
+        assert rel(g[k]["theta"], o["theta"]) <= 1e-9, k
+
+
+def test_heterogeneous_agents_equal_models_equal_shared_run(tg):
+    """Per-agent models that all equal the shared one give the dense shared-model
+    run (TADMM_FLAG_NO_STRUCTURE) bit for bit."""
+    b = make_workload("mixed", n_scen=4)
+    na = int(b.N.sum())
+    import dataclasses
+    bh = dataclasses.replace(b, A_agent=np.tile(b.A, (na, 1, 1)), B_agent=np.tile(b.B, (na, 1, 1)))
+    g0 = gpu_run(tg, b, 0.0, 12, flags=tg.FLAG_NO_STRUCTURE)[0]
+    g1 = gpu_run(tg, bh, 0.0, 12)[0]
+    for k in range(b.n_scen):
+        assert np.array_equal(g0[k]["X"], g1[k]["X"]), k
+        assert np.array_equal(g0[k]["theta"], g1[k]["theta"]), k
+
+
 def test_relinearized_solve_matches_oracle(tg):
     """One outer linearize-and-solve step: solve, re-linearize the collision
     halfspaces at the solution on the device (C ABI), solve again; against the
