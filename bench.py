@@ -406,6 +406,27 @@ def extras(tg, torch, batch, args):
     out["balancing_relaxed"] = timed_solves(tg, torch, batch, args, precision=64, adapt=(10, 10.0, 2.0), relax=1.6)
     out["balancing_relaxed"]["note"] = ("residual balancing as above plus over-relaxation alpha = 1.6 (Boyd et al. "
                                         "2011, Sec. 3.4.3), an extension; parity against the oracle 1e-9")
+    from instances import heterogeneous_agents, nearest_neighbour_pairs
+    out["heterogeneous_agents"] = timed_solves(tg, torch, heterogeneous_agents(batch, seed=7), args, precision=64)
+    out["heterogeneous_agents"]["note"] = ("per-agent dynamics (seeded velocity damping and mass per agent, dense "
+                                           "products) on the same workload, an extension; parity 1e-9")
+    knn = nearest_neighbour_pairs(batch, 4)
+    out["knn_coupling"] = timed_solves(tg, torch, knn, args, precision=64)
+    out["knn_coupling"]["note"] = ("listed pairs: each agent coupled to its 4 nearest agents at t = 0 (%d of %d "
+                                   "pairs), an extension; parity 1e-9" % (int(knn.pair_count.sum()), int(batch.P.sum())))
+    # one outer linearize-and-solve step: the device-side re-linearization of every halfspace
+    s = tg.Solver(batch, precision=64)
+    s.solve(args.tol, 20)
+    s.relinearize()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.relinearize()
+    e1.record()
+    torch.cuda.synchronize()
+    s.close()
+    out["relinearize"] = {"ms": e0.elapsed_time(e1), "pair_steps": int((batch.P * batch.T).sum()),
+                          "note": "normals and guesses re-formed at the last iterate, whole batch, one call"}
     # one 512-agent 3D scenario (130816 pairs x 40 steps): graph mode vs plain mode per iteration
     from instances import make_workload
     sw = make_workload("swarm3d")
