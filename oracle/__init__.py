@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-START_COLD, START_HOT, START_TURBO = 0, 1, 2
+START_COLD, START_HOT, START_TURBO, START_HOMOTOPY = 0, 1, 2, 3
 QP_COLD, QP_LQR, QP_GIVEN = 0, 1, 2
 CONVERGED, NOT_CONVERGED, QP_FAIL, NUMERIC = 0, 1, 2, 3
 
@@ -51,7 +51,7 @@ class Result(C.Structure):
     _fields_ = [("X", _dp), ("U", _dp), ("theta", _dp), ("W", _i8p), ("mu", _dp), ("trace", _dp),
                 ("iters", C.c_int), ("status", C.c_int), ("r", C.c_double), ("s", C.c_double),
                 ("as_iters", C.c_int64), ("inv_dev", C.c_double), ("rho_final", C.c_double),
-                ("rho_changes", C.c_int), ("restarts", C.c_int)]
+                ("rho_changes", C.c_int), ("restarts", C.c_int), ("homotopy_steps", C.c_int64)]
 
 
 class GlobalResult(C.Structure):
@@ -70,6 +70,8 @@ def lib():
         _LIB.orc_agent_qp_solve.argtypes = [C.POINTER(AgentQP), C.c_int, C.c_int, C.c_double, _dp, _i8p,
                                             _dp, _dp, C.POINTER(C.c_int)]
         _LIB.orc_agent_eqp.argtypes = [C.POINTER(AgentQP), _i8p, _dp, _dp, _dp]
+        _LIB.orc_agent_qp_homotopy.argtypes = [C.POINTER(AgentQP), _dp, C.c_int, C.c_double, _dp, _i8p, _dp, _dp,
+                                               C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _LIB.orc_agent_bruteforce.argtypes = [C.POINTER(AgentQP), C.c_double, _dp, _i8p]
         _LIB.orc_halfspace_project.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp]
         _LIB.orc_halfspace_project.restype = C.c_double
@@ -117,6 +119,22 @@ def agent_qp_solve(A, B, Hx, gx, Hu, x0, umin, umax, start=QP_LQR, as_max=1000, 
     st = lib().orc_agent_qp_solve(C.byref(q.s), start, as_max, eps_rel, _d(u), W.ctypes.data_as(_i8p),
                                   _d(x), _d(mu), C.byref(n))
     return dict(status=st, u=u, W=W, x=x, mu=mu, n_eqp=n.value)
+
+
+def agent_qp_homotopy(A, B, Hx, gx_old, gx, Hu, x0, umin, umax, u, W, mu, as_max=1000, eps_rel=1e-12):
+    """Homotopy hot start from the optimum (u, W, mu) for the state linear term
+    gx_old to the QP with gx (qpOASES-style parametric active set)."""
+    q = _AgentQPData(A, B, Hx, gx, Hu, x0, umin, umax)
+    T, nx, nu = q.T, q.nx, q.nu
+    g0 = _f64(gx_old).reshape(T, nx)
+    u = _f64(u).copy()
+    W = np.ascontiguousarray(W, dtype=np.int8).copy()
+    mu = _f64(mu).copy()
+    x = np.zeros((T + 1, nx))
+    n, ns = C.c_int(0), C.c_int(0)
+    st = lib().orc_agent_qp_homotopy(C.byref(q.s), _d(g0), as_max, eps_rel, _d(u), W.ctypes.data_as(_i8p),
+                                     _d(x), _d(mu), C.byref(n), C.byref(ns))
+    return dict(status=st, u=u, W=W, x=x, mu=mu, n_eqp=n.value, n_steps=ns.value)
 
 
 def agent_eqp(A, B, Hx, gx, Hu, x0, umin, umax, W=None):
@@ -196,7 +214,7 @@ class _ResultData:
         out = dict(X=self.X, U=self.U, theta=self.theta[:self.P], W=self.W, mu=self.mu,
                    iters=r.iters, status=r.status, r=r.r, s=r.s, as_iters=int(r.as_iters),
                    inv_dev=r.inv_dev, rho_final=r.rho_final, rho_changes=r.rho_changes,
-                    restarts=r.restarts)
+                    restarts=r.restarts, homotopy_steps=int(r.homotopy_steps))
         if self.trace is not None:
             out["trace"] = self.trace[:r.iters]
         return out

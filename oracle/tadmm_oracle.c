@@ -375,12 +375,80 @@ double orc_halfspace_project(int dp, const double* a, double d, const double* vi
  * h_t = sum_{j != i} (w_ij,t - y_ij,t), t = 1..T, assembled in the compact form
  * (Hessian 2Q, 2Q_T, 2R plus rho n_c C'C on positions; linear term
  * -2 Q_t x_ref - rho C' h_t) and solved by the active-set method. */
-int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, int as_max, double eps_rel,
-                      double* u, int8_t* W, double* x, double* mu, int* n_eqp) {
+int orc_agent_qp_homotopy(const orc_agent_qp* q, const double* gx_old, int as_max, double eps_rel, double* u,
+                          int8_t* W, double* x, double* mu, int* n_eqp, int* n_steps) {
+  const int T = q->T, nx = q->nx, nu = q->nu, nU = T * nu;
+  double* dgx = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double* du = (double*)malloc(sizeof(double) * nU);
+  double* dmu = (double*)malloc(sizeof(double) * nU);
+  double* dx = (double*)malloc(sizeof(double) * (size_t)(T + 1) * nx);
+  double zero[16] = {0.0};
+  int steps = 0, st = ORC_CONVERGED;
+  *n_eqp = 0;
+  if (!dgx || !du || !dmu || !dx) { st = ORC_NUMERIC; goto done; }
+  for (size_t k = 0; k < (size_t)T * nx; ++k) dgx[k] = q->gx[k] - gx_old[k];
+  {
+    /* the direction problem: linear term d gx, x_0 = 0, fixed inputs at 0 */
+    orc_agent_qp qd = *q;
+    qd.gx = dgx;
+    qd.x0 = zero;
+    qd.umin = zero;
+    qd.umax = zero;
+    double tau = 0.0;
+    while (steps < as_max) {
+      if (orc_agent_eqp(&qd, W, du, dx, dmu) != 0) { st = ORC_NUMERIC; goto done; }
+      ++steps;
+      /* largest step along the segment: a free input meets a bound (ties: first
+       * index), a multiplier meets zero, or the segment ends */
+      double best = 1.0 - tau;
+      int bk = -1, side = 0;
+      for (int k = 0; k < nU; ++k) {
+        const int c = k % nu;
+        double t;
+        int sd;
+        if (!W[k]) {
+          if (du[k] > 0.0) { t = (q->umax[c] - u[k]) / du[k]; sd = 2; }
+          else if (du[k] < 0.0) { t = (q->umin[c] - u[k]) / du[k]; sd = 1; }
+          else continue;
+        } else {
+          if (!(dmu[k] < 0.0)) continue;
+          t = mu[k] / -dmu[k];
+          sd = 0;
+        }
+        if (t < 0.0) t = 0.0;
+        if (t < best) { best = t; bk = k; side = sd; }
+      }
+      for (int k = 0; k < nU; ++k) {
+        if (!W[k]) u[k] += best * du[k];
+        else mu[k] += best * dmu[k];
+      }
+      tau += best;
+      if (bk < 0) break; /* tau = 1 reached */
+      if (side) {
+        W[bk] = (int8_t)side;
+        u[bk] = (side == 1) ? q->umin[bk % nu] : q->umax[bk % nu];
+      } else {
+        W[bk] = 0;
+      }
+      mu[bk] = 0.0;
+    }
+  }
+  {
+    int ne = 0;
+    st = orc_agent_qp_solve(q, ORC_QP_GIVEN, as_max, eps_rel, u, W, x, mu, &ne);
+    *n_eqp = steps + ne;
+  }
+done:
+  if (st == ORC_NUMERIC) *n_eqp = steps;
+  *n_steps = steps;
+  free(dgx); free(du); free(dmu); free(dx);
+  return st;
+}
+
+/* Local QP data of agent i (Sec. IV.A) for the coupling term h: Hessian
+ * diagonals Hx [T][nx], Hu [nu] and the state linear term gx [T][nx]. */
+static void agent_qp_data(const orc_scenario* s, int i, const double* h, double* Hx, double* gx, double* Hu) {
   const int N = s->N, T = s->T, nx = s->nx, nu = s->nu, dp = s->dp;
-  double* Hx = (double*)malloc(sizeof(double) * (size_t)T * nx);
-  double* gx = (double*)malloc(sizeof(double) * (size_t)T * nx);
-  double Hu[16];
   int nc = N - 1;
   if (s->pairs) {
     nc = 0;
@@ -403,10 +471,39 @@ int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, 
     }
   }
   for (int c = 0; c < nu; ++c) Hu[c] = 2.0 * s->Rd[(size_t)i * nu + c];
+}
+
+int orc_agent_xupdate(const orc_scenario* s, int i, const double* h, int start, int as_max, double eps_rel,
+                      double* u, int8_t* W, double* x, double* mu, int* n_eqp) {
+  const int T = s->T, nx = s->nx, nu = s->nu;
+  double* Hx = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double* gx = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double Hu[16];
+  agent_qp_data(s, i, h, Hx, gx, Hu);
   orc_agent_qp q = {T, nx, nu, agent_A(s, i), agent_B(s, i), Hx, gx, Hu, s->x_init + (size_t)i * nx, s->umin, s->umax};
   int st = orc_agent_qp_solve(&q, start, as_max, eps_rel, u, W, x, mu, n_eqp);
   free(Hx);
   free(gx);
+  return st;
+}
+
+/* x-update of agent i by the homotopy from its previous coupling term h_old
+ * (whose optimum u, W, mu are given) to h. */
+static int agent_xupdate_homotopy(const orc_scenario* s, int i, const double* h_old, const double* h, int as_max,
+                                  double eps_rel, double* u, int8_t* W, double* x, double* mu, int* n_eqp,
+                                  int* n_steps) {
+  const int T = s->T, nx = s->nx, nu = s->nu;
+  double* Hx = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double* gx = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double* gx0 = (double*)malloc(sizeof(double) * (size_t)T * nx);
+  double Hu[16];
+  agent_qp_data(s, i, h_old, Hx, gx0, Hu);
+  agent_qp_data(s, i, h, Hx, gx, Hu);
+  orc_agent_qp q = {T, nx, nu, agent_A(s, i), agent_B(s, i), Hx, gx, Hu, s->x_init + (size_t)i * nx, s->umin, s->umax};
+  int st = orc_agent_qp_homotopy(&q, gx0, as_max, eps_rel, u, W, x, mu, n_eqp, n_steps);
+  free(Hx);
+  free(gx);
+  free(gx0);
   return st;
 }
 
@@ -432,12 +529,18 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   double* ypi = (double*)calloc(PS + 1, sizeof(double));
   double* ypj = (double*)calloc(PS + 1, sizeof(double));
   double acc_a = 1.0, c_prev = INFINITY;
+  /* homotopy hot start: each agent's coupling term of the previous x-update */
+  const int homotopy = o->start_mode == ORC_START_HOMOTOPY;
+  double* h_prev = homotopy ? (double*)calloc((size_t)N * T * dp + 1, sizeof(double)) : NULL;
+  int64_t hom_steps = 0;
+  int hom_ok = 1; /* 0 right after a penalty change: the Hessian moved, so that x-update starts as a hot start */
   int64_t as_total = 0;
   orc_scenario sc = *s; /* the penalty changes under residual balancing */
   const double alpha = (o->relax_alpha == 0.0) ? 1.0 : o->relax_alpha;
   res->rho_final = s->rho;
   res->rho_changes = 0;
   res->restarts = 0;
+  res->homotopy_steps = 0;
   res->status = ORC_NOT_CONVERGED;
   res->iters = 0;
   res->r = INFINITY;
@@ -469,7 +572,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
     int fail = 0;
     /* --- x-update: N independent per-agent QPs --- */
 #pragma omp parallel for schedule(dynamic) num_threads(o->nthreads > 0 ? o->nthreads : 1) \
-    reduction(+ : as_total) reduction(max : fail)
+    reduction(+ : as_total, hom_steps) reduction(max : fail)
     for (int i = 0; i < N; ++i) {
       double* h = (double*)calloc((size_t)T * dp, sizeof(double));
       for (int j = 0; j < N; ++j) {
@@ -484,17 +587,27 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
       }
       int start;
       if (o->start_mode == ORC_START_COLD) start = ORC_QP_COLD;
-      else if (k == 0) start = (o->start_mode == ORC_START_TURBO) ? ORC_QP_LQR : ORC_QP_COLD;
+      else if (k == 0) start = (o->start_mode != ORC_START_HOT) ? ORC_QP_LQR : ORC_QP_COLD;
       else start = ORC_QP_GIVEN;
-      int neqp = 0;
-      int st = orc_agent_xupdate(&sc, i, h, start, o->as_max, o->eps_rel, res->U + (size_t)i * T * nu,
-                                 res->W + (size_t)i * T * nu, res->X + (size_t)i * (T + 1) * nx,
-                                 res->mu + (size_t)i * T * nu, &neqp);
+      int neqp = 0, st;
+      if (homotopy && k > 0 && hom_ok) {
+        int nst = 0;
+        st = agent_xupdate_homotopy(&sc, i, h_prev + (size_t)i * T * dp, h, o->as_max, o->eps_rel,
+                                    res->U + (size_t)i * T * nu, res->W + (size_t)i * T * nu,
+                                    res->X + (size_t)i * (T + 1) * nx, res->mu + (size_t)i * T * nu, &neqp, &nst);
+        hom_steps += nst;
+      } else {
+        st = orc_agent_xupdate(&sc, i, h, start, o->as_max, o->eps_rel, res->U + (size_t)i * T * nu,
+                               res->W + (size_t)i * T * nu, res->X + (size_t)i * (T + 1) * nx,
+                               res->mu + (size_t)i * T * nu, &neqp);
+      }
+      if (homotopy) memcpy(h_prev + (size_t)i * T * dp, h, sizeof(double) * (size_t)T * dp);
       as_total += neqp;
       if (st > fail) fail = st;
       free(h);
     }
     res->iters = k + 1;
+    hom_ok = 1;
     if (fail) { res->status = fail; break; }
     for (int i = 0; i < N; ++i)
       for (int t = 1; t <= T; ++t)
@@ -605,6 +718,7 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
         c_prev = INFINITY;
         sc.rho *= scale;
         res->rho_changes++;
+        hom_ok = 0;
       }
     }
   }
@@ -612,6 +726,8 @@ int orc_admm(const orc_scenario* s, const orc_options* o, orc_result* res) {
   res->as_iters = as_total;
   free(wi); free(wj); free(yi); free(yj); free(pos); free(plist); free(ptab);
   free(whi); free(whj); free(yhi); free(yhj); free(wpi); free(wpj); free(ypi); free(ypj);
+  free(h_prev);
+  res->homotopy_steps = hom_steps;
   return 0;
 }
 

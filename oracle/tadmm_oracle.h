@@ -18,6 +18,8 @@
  *     over-relaxation (Sec. 3.4.3 there) and acceleration with restart
  *     (Goldstein et al. 2014), extensions toward the iteration-count work the
  *     paper names as future work.
+ *   - orc_agent_qp_homotopy: the parametric hot start of qpOASES (Sec. IV.C
+ *     names its hot start) as a homotopy in the QP's linear term.
  *   - orc_global_qp: the centralized linearized QP of Eq. (1) condensed in all
  *     inputs and solved by the same active-set method (the ADMM fixed point).
  *   - orc_agent_bruteforce: exhaustive active-set enumeration for tiny QPs.
@@ -39,7 +41,7 @@ extern "C" {
 #endif
 
 enum { ORC_CONVERGED = 0, ORC_NOT_CONVERGED = 1, ORC_QP_FAIL = 2, ORC_NUMERIC = 3 };
-enum { ORC_START_COLD = 0, ORC_START_HOT = 1, ORC_START_TURBO = 2 };
+enum { ORC_START_COLD = 0, ORC_START_HOT = 1, ORC_START_TURBO = 2, ORC_START_HOMOTOPY = 3 };
 /* per-agent QP start kinds */
 enum { ORC_QP_COLD = 0, ORC_QP_LQR = 1, ORC_QP_GIVEN = 2 };
 
@@ -59,6 +61,16 @@ typedef struct {
 /* Working-set codes per input component: 0 free, 1 at lower bound, 2 at upper. */
 int orc_agent_qp_solve(const orc_agent_qp* q, int start, int as_max, double eps_rel,
                        double* u, int8_t* W, double* x, double* mu, int* n_eqp);
+
+/* Parametric (homotopy) hot start in the manner of qpOASES: from the optimum
+ * (u, W, mu) of the same QP with state linear term gx_old, follow the optimum
+ * along gx(tau) = gx_old + tau (q->gx - gx_old), tau from 0 to 1, changing the
+ * working set at each breakpoint (a free input reaching a bound, or a bound
+ * multiplier reaching zero); then the primal active-set method from the end
+ * point confirms optimality.  n_steps = direction solves of the homotopy,
+ * n_eqp = all EQP solves. */
+int orc_agent_qp_homotopy(const orc_agent_qp* q, const double* gx_old, int as_max, double eps_rel, double* u,
+                          int8_t* W, double* x, double* mu, int* n_eqp, int* n_steps);
 
 /* Equality-constrained QP with inputs in W fixed at their bounds (dense KKT). */
 int orc_agent_eqp(const orc_agent_qp* q, const int8_t* W, double* u, double* x, double* mu);
@@ -114,6 +126,7 @@ typedef struct {
   double rho_final;   /* penalty at the end of the run */
   int rho_changes;    /* number of penalty changes */
   int restarts;       /* restarts of the accelerated iteration */
+  int64_t homotopy_steps; /* direction solves of the homotopy hot starts (ORC_START_HOMOTOPY) */
 } orc_result;
 
 /* Projection of (v_i, v_j) onto {a'(w_i - w_j) >= d}; returns theta >= 0 with

@@ -589,3 +589,37 @@ def test_gradient_matches_central_differences(seed, hetero):
                 assert abs(fd - gr["gR"][i, c]) <= 1e-5 * max(1.0, abs(fd)), (i, c)
                 checked += 1
     assert checked >= 20
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_homotopy_hot_start_reaches_the_new_optimum(seed):
+    """Parametric (homotopy) hot start, qpOASES-style (evaluated on the oracle
+    only): from the optimum of a box QP, following the linear term to a new one
+    ends at the new QP's optimum (SciPy BVLS), with at least one direction solve
+    per working-set change and none left for the confirming active-set pass
+    beyond one solve."""
+    rng = np.random.default_rng(300 + seed)
+    T = 8 + seed
+    A, B, Hx, gx0, Hu, x0, umin, umax = random_agent_qp(rng, T, box=0.4)
+    first = oracle.agent_qp_solve(A, B, Hx, gx0, Hu, x0, umin, umax, start=oracle.QP_COLD)
+    assert first["status"] == oracle.CONVERGED
+    gx1 = gx0 + rng.normal(0, 2.0, gx0.shape)
+    h = oracle.agent_qp_homotopy(A, B, Hx, gx0, gx1, Hu, x0, umin, umax, first["u"], first["W"], first["mu"])
+    assert h["status"] == oracle.CONVERGED
+    u_ref, _, _ = _bvls(A, B, Hx, gx1, Hu, x0, umin, umax)
+    assert np.abs(h["u"] - u_ref).max() <= 1e-8 * max(1.0, np.abs(u_ref).max())
+    changes = int((h["W"] != first["W"]).sum())
+    assert h["n_steps"] >= 1 and h["n_steps"] >= changes // 2
+    assert h["n_eqp"] - h["n_steps"] == 1     # the end point is already optimal
+
+
+def test_homotopy_admm_equals_primal_hot_start():
+    """ADMM with the homotopy hot start gives the primal hot start's iterates
+    (the per-agent QP solution is unique; here bit for bit, since both end with
+    the same final equality-constrained solve)."""
+    b = make_workload("ring14")
+    r0 = oracle.admm(b, 0, tol=0.0, max_iter=60, start_mode=oracle.START_TURBO)
+    r1 = oracle.admm(b, 0, tol=0.0, max_iter=60, start_mode=oracle.START_HOMOTOPY)
+    assert r1["homotopy_steps"] > 0
+    assert np.array_equal(r0["W"], r1["W"])
+    assert np.abs(r0["X"] - r1["X"]).max() <= 1e-12 * max(1.0, np.abs(r0["X"]).max())
