@@ -42,6 +42,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "multi-agent QP solves/sec at residual 1e-4 (batched vs plain GPU); ms/solve"
 UNIT = "solves/s"
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_batched launch of the 4096-scenario
+# mixed batch (FP64, 500 iterations, 32 threads per CTA, register variant 0), one ncu pass
+K_BATCHED_TRAFFIC_BYTES = 888.24e9 + 321.96e9
 PEAK_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 1.259
 # Solves per scenario-iteration of the 4096-scenario mixed batch at tol 1e-4,
 # max_iter 500: 194 solves in 1 955 163 scenario-iterations.  A property of the
@@ -339,6 +342,10 @@ def run_ours(args, rank, world):
         ext = None if args.no_extras else extras(tg, torch, batch, args)
         clk = clocks.summary()
         launches = args.steps * solver_launches(solver)
+        # DRAM bytes of one launch of this exact workload and launch shape, from the
+        # committed ncu capture (profiles/k_batched_mixed4096_traffic.md); null otherwise
+        traffic = (K_BATCHED_TRAFFIC_BYTES if (args.n_scen, args.max_iter, args.precision, tpc, var) ==
+                   (4096, 500, 64, 32, 0) else None)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -357,7 +364,7 @@ def run_ours(args, rank, world):
             "clocks": clk,
             "roofline": {"bound": "alu", "kernel": "k_batched (FP64 pipe)", "achieved": achieved,
                          "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
-                         "traffic": None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                         "traffic": traffic, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
                          "algorithmic_units": units, "algorithmic_flops_per_step": flops},
             "plain_gpu": plain,
             "cpu_baseline": cpu,
