@@ -1551,7 +1551,7 @@ __device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tk, i
 // over pairs, steps, sides and components (the change of the consensus copies).
 template <typename F, int NX, int NU, int DP>
 __device__ void dual_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tkm1, int tk, int tkp1, int64_t q0,
-                           int64_t stride, unsigned long long& sb) {
+                           int64_t stride, unsigned long long& sb, unsigned long long* rb = nullptr) {
   const int N = s.N, P = s.P;
   const int64_t PT = (int64_t)P * s.T;
   const F* Xn = D.X + (size_t)(xl ^ 1) * D.tot_xs * NX + s.xs_off * NX;
@@ -1571,6 +1571,12 @@ __device__ void dual_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tkm1,
 #pragma unroll
     for (int c = 0; c < DP; ++c) {
       const F av = a[((size_t)tm1 * DP + c) * P + pair];
+      if (rb) {
+        // primal residual term |(theta' - theta) a_c|: their maximum has the bits
+        // of the product with max_c |a_c| (rounding is monotone)
+        const unsigned long long rv = abs_bits((thn[q] - th) * av);
+        *rb = rv > *rb ? rv : *rb;
+      }
       const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
       const unsigned long long v1 = abs_bits(fma(e2, av, Xn[ro + i] - Xc[ro + i]));
       const unsigned long long v2 = abs_bits(fma(-e2, av, Xn[ro + j] - Xc[ro + j]));
@@ -1883,8 +1889,9 @@ struct GroupSm {
   int active[kGroupMax];
   int flag[kGroupMax];
   int need[kGroupMax];
-  unsigned long long rb[kGroupMax];
+  unsigned long long rb[kGroupMax];  // primal residual key (unrelaxed: max |theta' - theta|, a bound)
   unsigned long long sb[kGroupMax];
+  unsigned long long rx[kGroupMax];  // exact primal residual key from the lazy pass
   unsigned long long cnt[kGroupMax][2];
   double rho[kGroupMax];    // current penalty per member (residual balancing)
   double scale[kGroupMax];  // this iteration's penalty factor per member
@@ -2023,6 +2030,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
     gs.need[tid] = 0;
     gs.rb[tid] = 0;
     gs.sb[tid] = 0;
+    gs.rx[tid] = 0;
     gs.cnt[tid][0] = 0;
     gs.cnt[tid][1] = 0;
     gs.rho[tid] = gs.meta[tid].rho;
@@ -2141,21 +2149,20 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
             const uint32_t fij = st.pair[u];
             const int fi = fij & 0xFF, fj = fij >> 8;
             F g = F(s.d);  // d - a'(p_i - p_j)
-            unsigned long long amax = 0;
 #pragma unroll
             for (int c = 0; c < DP; ++c) {
               const F avc = av[b][c];
               smA[c * nP + u] = avc;
               g = fma(-avc, st.pos[c][fi] - st.pos[c][fj], g);
-              const unsigned long long ab = abs_bits(avc);
-              amax = ab > amax ? ab : amax;
             }
             const F th = thv[b];
             F tn = fma(g, F(0.5), th);
             if (sign_set(tn)) tn = F(0);
             D.theta[(size_t)tkp1 * D.tot_ps + s.ps_off + (size_t)tm1 * P + pair] = tn;
             smE[u] = fma(F(2), tn, -th);
-            const unsigned long long v = abs_bits((tn - th) * from_bits(amax, F(0)));
+            // max |theta' - theta| bounds the primal residual r = max |(theta' - theta) a_c|
+            // (|a| = 1): r <= it <= sqrt(dp) r; the exact r is formed in the lazy pass
+            const unsigned long long v = abs_bits(tn - th);
             if (v > gs.rb[m]) atomicMax(&gs.rb[m], v);
           }
         }
@@ -2197,7 +2204,9 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           D.iters[sc] = k + 1;
           D.cur_lvl[sc] = (xl ^ 1) | (tkp1 << 1);
           D.res[2 * sc] = double(r);
-        } else if (r <= F(D.tol) || last || adapt_iter) {
+        } else if ((D.relax ? r <= F(D.tol) : r <= F(2) * F(D.tol)) || last || adapt_iter) {
+          // unrelaxed: the bound max |dtheta| is at most sqrt(dp) < 2 times the exact r,
+          // so every scenario whose exact r may pass the test takes the lazy pass
           gs.need[tid] = 1;
         }
       }
@@ -2215,17 +2224,18 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
           const int m = st.mem[u];
           if (!gs.need[m]) continue;
           const ScenMeta& s = gs.meta[m];
-          unsigned long long sb = 0;
+          unsigned long long sb = 0, rx = 0;
           dual_phase<F, NX, NU, DP>(D, s, xl, tkm1, tk, tkp1, (int64_t)tm1 * s.P + (u - gs.poff[m]),
-                                    (int64_t)s.P * s.T, sb);
+                                    (int64_t)s.P * s.T, sb, &rx);
           if (sb > gs.sb[m]) atomicMax(&gs.sb[m], sb);
+          if (rx > gs.rx[m]) atomicMax(&gs.rx[m], rx);
         }
       }
       __syncthreads();
     }
     if (tid < G && gs.active[tid]) {
       const int sc = gs.sid[tid];
-      const F r = from_bits(gs.rb[tid], F(0));
+      const F r = from_bits((gs.need[tid] && !D.relax) ? gs.rx[tid] : gs.rb[tid], F(0));
       D.res[2 * sc] = double(r);
       if (gs.need[tid]) {
         const F sres = F(gs.rho[tid]) * from_bits(gs.sb[tid], F(0));
@@ -2254,6 +2264,7 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
       }
       gs.rb[tid] = 0;
       gs.sb[tid] = 0;
+      gs.rx[tid] = 0;
     }
     __syncthreads();
     if (tid == 0) {
