@@ -261,6 +261,28 @@ def test_swarm3d_full_size_graph_mode_sampled(tg):
     assert (gg[0]["theta"] >= 0).all()
 
 
+def test_reported_residuals_match_oracle(tg):
+    """The primal and dual residuals the solver reports (the grouped kernel forms
+    the exact primal residual in its lazy pass) against the oracle's: after a
+    fixed number of iterations on mixed scenarios, and at convergence."""
+    b = make_workload("mixed", n_scen=8)
+    g = gpu_run(tg, b, 0.0, 9)[0]
+    for k in range(b.n_scen):
+        o = oracle.admm(b, k, tol=0.0, max_iter=9)
+        assert abs(g[k]["r"] - o["r"]) <= 1e-9 * max(1.0, o["r"]), k
+        assert abs(g[k]["s"] - o["s"]) <= 1e-9 * max(1.0, o["s"]), k
+    # scenarios of the mixed batch that converge after 478 and 13 iterations and
+    # one that does not within the cap, run to tol 1e-4 together
+    sub = make_workload("mixed", n_scen=256).subset([107, 242, 2])
+    g = gpu_run(tg, sub, 1e-4, 500)[0]
+    for k in range(sub.n_scen):
+        o = oracle.admm(sub, k, tol=1e-4, max_iter=500)
+        assert g[k]["status"] == o["status"] and g[k]["iters"] == o["iters"], k
+        assert abs(g[k]["r"] - o["r"]) <= 1e-9 * max(1.0, o["r"]), k
+        assert abs(g[k]["s"] - o["s"]) <= 1e-9 * max(1.0, o["s"]), k
+    assert [x["iters"] for x in g] == [478, 13, 500]
+
+
 def test_scenario_groups_equal_one_scenario_per_cta(tg):
     """Packing several same-horizon scenarios into one CTA changes nothing in
     any scenario's arithmetic: iterates, statuses and counters are equal to the
