@@ -68,8 +68,10 @@ extern "C" {
 typedef struct {
   int32_t n_scen;
   int32_t nx, nu, dp;
-  const int32_t* N;      /* [n_scen] agents per scenario, >= 1 */
-  const int32_t* T;      /* [n_scen] horizon per scenario, >= 1 */
+  const int32_t* N;      /* [n_scen] agents per scenario, 1..32767 */
+  const int32_t* T;      /* [n_scen] horizon per scenario, 1..100000; with N also
+                            (T + 1) * N * 87 < 2^31 (the per-stage arrays of one
+                            scenario are indexed in 32 bits), else EINVAL */
   const double* A;       /* [nx*nx] dynamics x_{t+1} = A x_t + B u_t */
   const double* B;       /* [nx*nu] */
   const double* umin;    /* [nu] */

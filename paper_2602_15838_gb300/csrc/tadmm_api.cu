@@ -69,6 +69,10 @@ static int validate(const tadmm_batch* b, const tadmm_handle* shape) {
     const int N = b->N[s], T = b->T[s];
     if (N < 1 || N > 32767) return set_error(TADMM_EINVAL, "scenario " + std::to_string(s) + ": N must be in [1, 32767]");
     if (T < 1 || T > 100000) return set_error(TADMM_EINVAL, "scenario " + std::to_string(s) + ": T must be in [1, 100000]");
+    // the agent kernels index a scenario's per-stage arrays in 32 bits: the
+    // largest is the factor cache, (T + 1) stages x at most 87 words x N agents
+    if ((int64_t)(T + 1) * 87 * N >= (int64_t)1 << 31)
+      return set_error(TADMM_EINVAL, "scenario " + std::to_string(s) + ": N * (T + 1) too large (per-scenario arrays over 2^31 elements)");
     if (shape && (shape->N[s] != N || shape->T[s] != T))
       return set_error(TADMM_EINVAL, "update: N/T differ from the handle");
     if (!std::isfinite(b->d_min[s])) return set_error(TADMM_EINVAL, "d_min must be finite");

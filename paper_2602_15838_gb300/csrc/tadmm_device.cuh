@@ -274,20 +274,22 @@ struct AgentCtx {
 
   __device__ __forceinline__ F k(int e) const { return kc[e * ks]; }
 
+  // 32-bit indices within the scenario (the host rejects scenarios whose
+  // per-stage arrays would need more than 2^31 elements)
   __device__ __forceinline__ F& C(int t, int e) const {
-    return cache[((size_t)t * CacheLayout<NX, NU>::E + e) * N + i];
+    return cache[(t * CacheLayout<NX, NU>::E + e) * N + i];
   }
-  __device__ __forceinline__ uint16_t& W(int t) const { return Wm[(size_t)t * N + i]; }
-  __device__ __forceinline__ uint16_t& CM(int t) const { return Cm[(size_t)t * N + i]; }
-  __device__ __forceinline__ F& u(int t, int c) const { return U[((size_t)t * NU + c) * N + i]; }
-  __device__ __forceinline__ F& us(int t, int c) const { return Us[((size_t)t * NU + c) * N + i]; }
-  __device__ __forceinline__ F& x(int t, int r) const { return Xo[((size_t)t * NX + r) * N + i]; }
+  __device__ __forceinline__ uint16_t& W(int t) const { return Wm[t * N + i]; }
+  __device__ __forceinline__ uint16_t& CM(int t) const { return Cm[t * N + i]; }
+  __device__ __forceinline__ F& u(int t, int c) const { return U[(t * NU + c) * N + i]; }
+  __device__ __forceinline__ F& us(int t, int c) const { return Us[(t * NU + c) * N + i]; }
+  __device__ __forceinline__ F& x(int t, int r) const { return Xo[(t * NX + r) * N + i]; }
   // Hessian diagonal of x_T
   __device__ __forceinline__ F qbarT(int r) const {
     return F(2) * qf[r] + (r < DP ? k(AgentConst<NX, NU>::RHO) * F(nc) : F(0));
   }
   // h_t component r (r < DP) of stage t = 1..T
-  __device__ __forceinline__ F hv(int t, int r) const { return h[((size_t)(t - 1) * DP + r) * N + i]; }
+  __device__ __forceinline__ F hv(int t, int r) const { return h[((t - 1) * DP + r) * N + i]; }
   // linear term of x_t, t < T, from a loaded h_t component
   __device__ __forceinline__ F q_h(int r, F hr) const {
     using AC = AgentConst<NX, NU>;

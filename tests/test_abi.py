@@ -115,3 +115,23 @@ def test_null_batch_rejected(libtadmm):
     h = C.c_void_p()
     assert L.tadmm_create(None, None, C.byref(h)) == tg.EINVAL
     assert L.tadmm_solve(None, 1e-4, 10, None) == tg.EINVAL
+
+
+def test_scenario_over_the_32_bit_index_limit_rejected(libtadmm):
+    """A scenario whose per-stage arrays would exceed 2^31 elements (here
+    N = 32767 agents, T = 1000) is refused on the host before any of its data is
+    read beyond the per-scenario scalars."""
+    tg, L = libtadmm
+    one = np.ones(64)
+    keep = [one]
+    dp_ = one.ctypes.data_as(C.POINTER(C.c_double))
+    N = np.array([32767], dtype=np.int32)
+    T = np.array([1000], dtype=np.int32)
+    keep += [N, T]
+    i32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    bs = tg.TadmmBatch(1, 4, 2, 2, i32(N), i32(T), dp_, dp_, dp_, dp_, dp_, dp_, dp_, dp_, dp_, dp_, dp_,
+                       dp_, dp_, None, None, None, None)
+    o = tg.TadmmOptions(64, 2, 0, 0.0, 0, 0, 0, 0, 0, 0, 10.0, 2.0, 0.0)
+    h = C.c_void_p()
+    assert L.tadmm_create(C.byref(bs), C.byref(o), C.byref(h)) == tg.EINVAL
+    assert b"2^31" in L.tadmm_last_error()
