@@ -44,7 +44,7 @@ METRIC = "multi-agent QP solves/sec at residual 1e-4 (batched vs plain GPU); ms/
 UNIT = "solves/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_batched launch of the 4096-scenario
 # mixed batch (FP64, 500 iterations, 32 threads per CTA, register variant 0), one ncu pass
-K_BATCHED_TRAFFIC_BYTES = 895.48e9 + 321.98e9
+K_BATCHED_TRAFFIC_BYTES = 893.11e9 + 321.97e9
 PEAK_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 1.259
 # Solves per scenario-iteration of the 4096-scenario mixed batch at tol 1e-4,
 # max_iter 500: 194 solves in 1 955 163 scenario-iterations.  A property of the
