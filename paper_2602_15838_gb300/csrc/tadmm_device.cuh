@@ -1550,7 +1550,8 @@ __device__ void pair_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tk, i
 }
 
 // Dual residual s / rho = max |Delta p +- (theta^{k+1} - 2 theta^k + theta^{k-1}) a|
-// over pairs, steps, sides and components (the change of the consensus copies).
+// over pairs, steps, sides and components (the change of the consensus copies);
+// with rb, also the exact primal residual max |(theta^{k+1} - theta^k) a_c|.
 template <typename F, int NX, int NU, int DP>
 __device__ void dual_phase(const Dev<F>& D, const ScenMeta& s, int xl, int tkm1, int tk, int tkp1, int64_t q0,
                            int64_t stride, unsigned long long& sb, unsigned long long* rb = nullptr) {
@@ -2193,8 +2194,9 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
         __syncthreads();
       }
     }
-    // primal residual tests, then the dual residual only where it decides
-    // (the over-relaxed sweep has formed both)
+    // primal residual tests on the bound, then the exact primal and the dual
+    // residual in a lazy pass only where they decide (the over-relaxed sweep has
+    // formed both exactly)
     if (tid < G) {
       gs.need[tid] = 0;
       if (gs.active[tid]) {
