@@ -151,7 +151,9 @@ int tadmm_create(const tadmm_batch* batch, const tadmm_options* opt, tadmm_handl
 
 /* Re-uploads new problem data with the same shapes (N, T per scenario and the
  * dimensions must match the handle) from host memory, asynchronously on
- * `stream`; host arrays must stay valid until the stream reaches the copies. */
+ * `stream`; host arrays must stay valid until the stream reaches the copies.
+ * With per-agent dynamics the call first synchronizes `stream` (the library
+ * repacks the models in a host buffer that an earlier copy may still read). */
 int tadmm_update(tadmm_handle* h, const tadmm_batch* batch, void* stream);
 
 /* Runs ADMM from its initial point (consensus copies = w0, duals = 0) until
