@@ -623,3 +623,29 @@ def test_homotopy_admm_equals_primal_hot_start():
     assert r1["homotopy_steps"] > 0
     assert np.array_equal(r0["W"], r1["W"])
     assert np.abs(r0["X"] - r1["X"]).max() <= 1e-12 * max(1.0, np.abs(r0["X"]).max())
+
+
+def test_heterogeneous_agents_generator_recipe():
+    """The mixed-model generator is seeded and gives each agent the damped,
+    mass-scaled double integrator it states: p' = p + dt v + dt^2/(2m) u,
+    v' = (1 - c dt) v + dt/m u, with c in [0, 0.5) and m in [0.8, 1.25)."""
+    from instances import heterogeneous_agents
+    b = make_workload("mixed", n_scen=5)
+    h1 = heterogeneous_agents(b, seed=4)
+    h2 = heterogeneous_agents(b, seed=4)
+    assert np.array_equal(h1.A_agent, h2.A_agent) and np.array_equal(h1.B_agent, h2.B_agent)
+    na, dp, dt = int(b.N.sum()), b.dp, float(b.A[0, b.dp])
+    assert h1.A_agent.shape == (na, b.nx, b.nx) and h1.B_agent.shape == (na, b.nx, b.nu)
+    I = np.eye(dp)
+    for i in range(na):
+        A, B = h1.A_agent[i], h1.B_agent[i]
+        c = (1.0 - A[dp, dp]) / dt
+        m = dt / B[dp, 0]
+        assert 0.0 <= c < 0.5 and 0.8 <= m < 1.25
+        assert np.allclose(A[:dp, :dp], I) and np.allclose(A[:dp, dp:], dt * I) and np.allclose(A[dp:, :dp], 0)
+        assert np.allclose(A[dp:, dp:], (1 - c * dt) * I)
+        assert np.allclose(B[:dp], 0.5 * dt * dt / m * I) and np.allclose(B[dp:], dt / m * I)
+    # a subset keeps its agents' models
+    sub = h1.subset([1, 3])
+    ao = b.agent_off
+    assert np.array_equal(sub.A_agent, np.concatenate([h1.A_agent[ao[1]:ao[2]], h1.A_agent[ao[3]:ao[4]]]))
