@@ -82,7 +82,7 @@ def lib():
                                         C.POINTER(Result), C.c_int]
         _LIB.orc_global_qp.argtypes = [C.POINTER(Scenario), C.c_int, C.c_double, C.POINTER(GlobalResult)]
         _LIB.orc_global_gradient.argtypes = [C.POINTER(Scenario), _u8p, _i8p, _dp, C.c_double, _dp, _dp,
-                                             _dp, _dp, _dp, _dp]
+                                             _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_int)]
     return _LIB
 
 
@@ -288,7 +288,11 @@ def global_qp(batch, k: int = 0, as_max=100000, eps_rel=1e-12):
 
 
 def global_gradient(batch, k: int, act_h, W, targets, qf_tie=10.0):
-    """Polished solution at the active set and the implicit-KKT loss gradient."""
+    """Polished solution at the active set and the implicit-KKT loss gradient.
+
+    Also returns the polished point's multipliers (mu_h [P, T] of the
+    halfspaces, mu_u [N, T, nu] of the held bounds) and the number of active
+    halfspace rows found linearly dependent on the others."""
     sd = _ScenarioData(batch, k)
     N, T, nx, nu, P = sd.N, sd.T, sd.nx, sd.nu, sd.P
     act = np.zeros((max(P, 1), T), dtype=np.uint8)
@@ -297,11 +301,14 @@ def global_gradient(batch, k: int, act_h, W, targets, qf_tie=10.0):
     tg = _f64(targets).reshape(N, T, sd.dp)
     X = np.zeros((N, T + 1, nx)); U = np.zeros((N, T, nu)); loss = np.zeros(1)
     gQ = np.zeros((N, nx)); gR = np.zeros((N, nu)); gG = np.zeros((N, nx))
+    mu_h = np.zeros((max(P, 1), T)); mu_u = np.zeros((N, T, nu)); ndep = C.c_int(0)
     rc = lib().orc_global_gradient(C.byref(sd.s), act.ctypes.data_as(_u8p), Wc.ctypes.data_as(_i8p),
-                                   _d(tg), qf_tie, _d(X), _d(U), _d(loss), _d(gQ), _d(gR), _d(gG))
+                                   _d(tg), qf_tie, _d(X), _d(U), _d(loss), _d(gQ), _d(gR), _d(gG),
+                                   _d(mu_h), _d(mu_u), C.byref(ndep))
     if rc != 0:
         raise RuntimeError(f"gradient failed ({rc})")
-    return dict(X=X, U=U, loss=float(loss[0]), gQ=gQ, gR=gR, gGoal=gG)
+    return dict(X=X, U=U, loss=float(loss[0]), gQ=gQ, gR=gR, gGoal=gG, mu_h=mu_h[:P], mu_u=mu_u,
+                n_dependent=int(ndep.value))
 
 
 def relinearize(batch, X_list):

@@ -1010,9 +1010,200 @@ out:
 /* Implicit differentiation of the global KKT system at a fixed active set     */
 /* ------------------------------------------------------------------------- */
 
+/* Relative size below which an active halfspace row, orthogonalized against
+ * the rows already chosen, counts as linearly dependent on them. */
+#define ORC_RANK_TOL 1e-10
+
+/* Polished point of the global QP at a fixed active set (bounds W held at
+ * their values, halfspaces act_h held as equalities).  The held inputs are
+ * substituted, leaving on the free inputs U_F the problem
+ *     min 1/2 U_F' H_FF U_F + g_F' U_F   s.t.   G U_F = d
+ * with one row of G per active halfspace.  The rows of G may be linearly
+ * dependent (several halfspaces through the same agents and steps, or rows
+ * whose agents' positions are fixed by held inputs); then the multipliers are
+ * not unique and the system may be inconsistent.  The polished point is
+ * defined as the minimizer subject to G U_F = d_hat, d_hat the Euclidean
+ * projection of d onto the range of G (d_hat = d when consistent), which is
+ * unique.  It is computed by a row-pivoted Gram-Schmidt (largest remaining row
+ * first) that picks an independent subset B of the rows; the dependent rows
+ * are G_D = C G_B with C = G_D G_B' (G_B G_B')^-1; the projection is
+ * [y; C y] with (I + C'C) y = d_B + C' d_D; and the EQP
+ *     [H_FF G_B'; G_B 0] [U_F; om] = [-g_F; y]
+ * is solved by LU.  On return Kf holds that KKT matrix (factor-free copy) for
+ * the adjoint solve, Uout the full inputs, mu_all the multipliers of every
+ * constraint row (0 for dependent and inactive rows). */
+typedef struct {
+  int nF, r, m;
+  int* free_idx;   /* [nF] */
+  int* rows;       /* [m] constraint row of each active halfspace */
+  int* basis;      /* [r] indices into rows of the chosen independent subset */
+  double* K;       /* [(nF + r)^2] KKT matrix of the reduced EQP */
+} reduced_eqp;
+
+static void reduced_free(reduced_eqp* R) {
+  free(R->free_idx); free(R->rows); free(R->basis); free(R->K);
+}
+
+static int global_eqp_polished(const global_qp* Q, const uint8_t* Wset, double* Uout, double* mu_all,
+                               reduced_eqp* R) {
+  const int nU = Q->nU, nC = Q->nC;
+  memset(R, 0, sizeof(*R));
+  int rc = -1;
+  /* held inputs at their bound values */
+  double* u = (double*)calloc(nU, sizeof(double));
+  uint8_t* held = (uint8_t*)calloc(nU, 1);
+  R->free_idx = (int*)malloc(sizeof(int) * (nU + 1));
+  R->rows = (int*)malloc(sizeof(int) * (nC + 1));
+  R->basis = (int*)malloc(sizeof(int) * (nC + 1));
+  if (!u || !held || !R->free_idx || !R->rows || !R->basis) goto fail0;
+  for (int k = 0; k < nU; ++k) {
+    if (Wset[2 * k]) { held[k] = 1; u[k] = Q->bc[2 * k]; }
+    else if (Wset[2 * k + 1]) { held[k] = 1; u[k] = -Q->bc[2 * k + 1]; }
+    else R->free_idx[R->nF++] = k;
+  }
+  for (int k = 2 * nU; k < nC; ++k)
+    if (Wset[k]) R->rows[R->m++] = k;
+  {
+    const int nF = R->nF, m = R->m;
+    double* G = (double*)calloc((size_t)m * nF + 1, sizeof(double));
+    double* d = (double*)calloc((size_t)m + 1, sizeof(double));
+    double* V = (double*)calloc((size_t)m * nF + 1, sizeof(double));   /* rows being orthogonalized */
+    uint8_t* taken = (uint8_t*)calloc((size_t)m + 1, 1);
+    if (!G || !d || !V || !taken) { free(G); free(d); free(V); free(taken); goto fail0; }
+    for (int h = 0; h < m; ++h) {
+      const double* nr = Q->Nc + (size_t)R->rows[h] * nU;
+      double rhs = Q->bc[R->rows[h]];
+      for (int j = 0; j < nU; ++j)
+        if (held[j]) rhs -= nr[j] * u[j];
+      d[h] = rhs;
+      for (int f = 0; f < nF; ++f) G[IDX2(h, f, nF)] = nr[R->free_idx[f]];
+    }
+    memcpy(V, G, sizeof(double) * (size_t)m * nF);
+    double maxn = 0.0;
+    for (int h = 0; h < m; ++h) {
+      double s2 = 0.0;
+      for (int f = 0; f < nF; ++f) s2 += G[IDX2(h, f, nF)] * G[IDX2(h, f, nF)];
+      if (sqrt(s2) > maxn) maxn = sqrt(s2);
+    }
+    /* row-pivoted modified Gram-Schmidt */
+    for (;;) {
+      int best = -1;
+      double bn = 0.0;
+      for (int h = 0; h < m; ++h) {
+        if (taken[h]) continue;
+        double s2 = 0.0;
+        for (int f = 0; f < nF; ++f) s2 += V[IDX2(h, f, nF)] * V[IDX2(h, f, nF)];
+        if (sqrt(s2) > bn) { bn = sqrt(s2); best = h; }
+      }
+      if (best < 0 || !(bn > ORC_RANK_TOL * maxn)) break;
+      taken[best] = 1;
+      R->basis[R->r++] = best;
+      double* q = V + (size_t)best * nF;
+      for (int f = 0; f < nF; ++f) q[f] /= bn;
+      for (int h = 0; h < m; ++h) {
+        if (taken[h]) continue;
+        double dot = 0.0;
+        for (int f = 0; f < nF; ++f) dot += V[IDX2(h, f, nF)] * q[f];
+        for (int f = 0; f < nF; ++f) V[IDX2(h, f, nF)] -= dot * q[f];
+      }
+    }
+    const int r = R->r, nD = m - r;
+    /* consistent right-hand side y of the independent rows */
+    double* y = (double*)calloc((size_t)r + 1, sizeof(double));
+    for (int b = 0; b < r; ++b) y[b] = d[R->basis[b]];
+    if (nD > 0 && r > 0) {
+      int* dep = (int*)malloc(sizeof(int) * nD);
+      int nd = 0;
+      for (int h = 0; h < m; ++h)
+        if (!taken[h]) dep[nd++] = h;
+      /* Gram matrix M = G_B G_B' and X = M^-1 G_B G_D' (column by column), C = X' */
+      double* M = (double*)malloc(sizeof(double) * (size_t)r * r);
+      double* Mc = (double*)malloc(sizeof(double) * (size_t)r * r);
+      double* Ct = (double*)calloc((size_t)r * nD, sizeof(double));   /* C' [r][nD] */
+      double* col = (double*)malloc(sizeof(double) * r);
+      for (int a = 0; a < r; ++a)
+        for (int b = 0; b < r; ++b) {
+          double acc = 0.0;
+          for (int f = 0; f < nF; ++f) acc += G[IDX2(R->basis[a], f, nF)] * G[IDX2(R->basis[b], f, nF)];
+          M[IDX2(a, b, r)] = acc;
+        }
+      int ok = 1;
+      for (int e = 0; e < nD && ok; ++e) {
+        for (int a = 0; a < r; ++a) {
+          double acc = 0.0;
+          for (int f = 0; f < nF; ++f) acc += G[IDX2(R->basis[a], f, nF)] * G[IDX2(dep[e], f, nF)];
+          col[a] = acc;
+        }
+        memcpy(Mc, M, sizeof(double) * (size_t)r * r);
+        if (lu_solve(r, Mc, col) != 0) ok = 0;
+        for (int a = 0; a < r; ++a) Ct[IDX2(a, e, nD)] = col[a];
+      }
+      /* (I + C'C) y = d_B + C' d_D */
+      if (ok) {
+        for (int a = 0; a < r; ++a)
+          for (int b = 0; b < r; ++b) {
+            double acc = (a == b) ? 1.0 : 0.0;
+            for (int e = 0; e < nD; ++e) acc += Ct[IDX2(a, e, nD)] * Ct[IDX2(b, e, nD)];
+            Mc[IDX2(a, b, r)] = acc;
+          }
+        for (int a = 0; a < r; ++a) {
+          double acc = d[R->basis[a]];
+          for (int e = 0; e < nD; ++e) acc += Ct[IDX2(a, e, nD)] * d[dep[e]];
+          y[a] = acc;
+        }
+        if (lu_solve(r, Mc, y) != 0) ok = 0;
+      }
+      free(dep); free(M); free(Mc); free(Ct); free(col);
+      if (!ok) { free(G); free(d); free(V); free(taken); free(y); goto fail0; }
+    }
+    /* reduced EQP */
+    const int nk = nF + r;
+    R->K = (double*)calloc((size_t)nk * nk + 1, sizeof(double));
+    double* K = (double*)malloc(sizeof(double) * ((size_t)nk * nk + 1));
+    double* rhs = (double*)calloc((size_t)nk + 1, sizeof(double));
+    for (int a = 0; a < nF; ++a) {
+      const int ia = R->free_idx[a];
+      double gv = Q->g[ia];
+      for (int j = 0; j < nU; ++j)
+        if (held[j]) gv += Q->H[IDX2(ia, j, nU)] * u[j];
+      rhs[a] = -gv;
+      for (int b = 0; b < nF; ++b) R->K[IDX2(a, b, nk)] = Q->H[IDX2(ia, R->free_idx[b], nU)];
+    }
+    for (int b = 0; b < r; ++b) {
+      for (int f = 0; f < nF; ++f) {
+        R->K[IDX2(nF + b, f, nk)] = G[IDX2(R->basis[b], f, nF)];
+        R->K[IDX2(f, nF + b, nk)] = G[IDX2(R->basis[b], f, nF)];
+      }
+      rhs[nF + b] = y[b];
+    }
+    memcpy(K, R->K, sizeof(double) * (size_t)nk * nk);
+    const int lr = lu_solve(nk, K, rhs);
+    if (lr == 0) {
+      memcpy(Uout, u, sizeof(double) * nU);
+      for (int a = 0; a < nF; ++a) Uout[R->free_idx[a]] = rhs[a];
+      for (int k = 0; k < nC; ++k) mu_all[k] = 0.0;
+      for (int b = 0; b < r; ++b) mu_all[R->rows[R->basis[b]]] = -rhs[nF + b];
+      /* bound multipliers from stationarity H U + g - Nc' mu = 0 on the held inputs */
+      for (int j = 0; j < nU; ++j) {
+        if (!held[j]) continue;
+        double st = Q->g[j];
+        for (int l = 0; l < nU; ++l) st += Q->H[IDX2(j, l, nU)] * Uout[l];
+        for (int h = 0; h < m; ++h) st -= Q->Nc[IDX2(R->rows[h], j, nU)] * mu_all[R->rows[h]];
+        if (Wset[2 * j]) mu_all[2 * j] = st;
+        else mu_all[2 * j + 1] = -st;
+      }
+      rc = 0;
+    }
+    free(K); free(rhs); free(G); free(d); free(V); free(taken); free(y);
+  }
+fail0:
+  free(u); free(held);
+  return rc;
+}
+
 int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_t* W,
                         const double* targets, double qf_tie, double* X, double* U, double* loss,
-                        double* gQ, double* gR, double* gGoal) {
+                        double* gQ, double* gR, double* gGoal, double* mu_h, double* mu_u, int* n_dependent) {
   global_qp Q;
   memset(&Q, 0, sizeof(Q));
   if (global_build(s, &Q) != 0) { global_free(&Q); return -1; }
@@ -1023,6 +1214,8 @@ int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_
   double* wv = (double*)calloc(nU + nC, sizeof(double));
   double* dH = (double*)malloc(sizeof(double) * (size_t)m * m);
   double* dg = (double*)malloc(sizeof(double) * m);
+  reduced_eqp R;
+  memset(&R, 0, sizeof(R));
   int rc = 0;
   for (int k = 0; k < nU; ++k) {
     if (W[k] == 1) Wset[2 * k] = 1;
@@ -1030,8 +1223,13 @@ int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_
   }
   for (int k = 0; k < Q.P * T; ++k) Wset[2 * nU + k] = act_h[k] ? 1 : 0;
   /* polished primal solution at this active set */
-  if (global_eqp(&Q, Wset, U, mu) != 0) { rc = -2; goto out; }
+  if (global_eqp_polished(&Q, Wset, U, mu, &R) != 0) { rc = -2; goto out; }
   global_outputs(s, &Q, U, X);
+  if (mu_h)
+    for (int k = 0; k < Q.P * T; ++k) mu_h[k] = mu[2 * nU + k];
+  if (mu_u)
+    for (int k = 0; k < nU; ++k) mu_u[k] = Wset[2 * k] ? mu[2 * k] : (Wset[2 * k + 1] ? mu[2 * k + 1] : 0.0);
+  if (n_dependent) *n_dependent = R.m - R.r;
   /* loss and its gradient with respect to U */
   double L = 0.0;
   for (int i = 0; i < N; ++i)
@@ -1045,28 +1243,18 @@ int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_
                 2.0 * e * GM((&Q), i, t, s1)[IDX2(c, c1, nu)];
       }
   *loss = L;
-  /* adjoint: K w = [dl/dU; 0] with the (symmetric) KKT matrix of the active set */
+  /* adjoint: [H_FF G_B'; G_B 0] [w_F; nu] = [dl/dU_F; 0] (held inputs: w = 0);
+   * the right-hand side of the constraint rows is zero, so any independent
+   * subset of the active rows gives the same w */
   {
-    int nW = 0;
-    for (int k = 0; k < nC; ++k) nW += Wset[k] != 0;
-    const int nk = nU + nW;
-    double* K = (double*)calloc((size_t)nk * nk, sizeof(double));
-    double* b = (double*)calloc((size_t)nk, sizeof(double));
-    for (int i = 0; i < nU; ++i) {
-      for (int j = 0; j < nU; ++j) K[IDX2(i, j, nk)] = Q.H[IDX2(i, j, nU)];
-      b[i] = dl[i];
-    }
-    int w = 0;
-    for (int k = 0; k < nC; ++k) {
-      if (!Wset[k]) continue;
-      for (int j = 0; j < nU; ++j) {
-        K[IDX2(nU + w, j, nk)] = Q.Nc[IDX2(k, j, nU)];
-        K[IDX2(j, nU + w, nk)] = Q.Nc[IDX2(k, j, nU)];
-      }
-      ++w;
-    }
+    const int nk = R.nF + R.r;
+    double* K = (double*)malloc(sizeof(double) * ((size_t)nk * nk + 1));
+    double* b = (double*)calloc((size_t)nk + 1, sizeof(double));
+    memcpy(K, R.K, sizeof(double) * (size_t)nk * nk);
+    for (int a = 0; a < R.nF; ++a) b[a] = dl[R.free_idx[a]];
     int lr = lu_solve(nk, K, b);
-    if (lr == 0) memcpy(wv, b, sizeof(double) * nU);
+    if (lr == 0)
+      for (int a = 0; a < R.nF; ++a) wv[R.free_idx[a]] = b[a];
     free(K);
     free(b);
     if (lr != 0) { rc = -3; goto out; }
@@ -1128,6 +1316,7 @@ int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_
   }
 out:
   free(Wset); free(mu); free(dl); free(wv); free(dH); free(dg);
+  reduced_free(&R);
   global_free(&Q);
   return rc;
 }

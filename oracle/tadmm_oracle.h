@@ -24,7 +24,8 @@
  *     inputs and solved by the same active-set method (the ADMM fixed point).
  *   - orc_agent_bruteforce: exhaustive active-set enumeration for tiny QPs.
  *   - orc_global_gradient: implicit differentiation of the global QP's KKT
- *     system at a given active set (dense LU).
+ *     system at a given active set (held inputs substituted, independent
+ *     halfspace rows by pivoted Gram-Schmidt, dense LU).
  *
  * Parity pins: every function here is pinned by tests against closed forms,
  * library routines (bounded least squares), brute force and KKT invariants;
@@ -163,12 +164,20 @@ int orc_global_qp(const orc_scenario* s, int as_max, double eps_rel, orc_global_
 /* Solution of the global QP with the given active set held as equalities
  * (halfspaces with act_h=1 and bounds W), i.e. the polished KKT point, and the
  * gradient of loss = sum_{i,t=1..T} ||C x_{i,t} - target_{i,t}||^2 with respect
- * to diag(Q_i) (with Qf_i = qf_tie * Q_i), diag(R_i) and the goal x_ref_i. */
+ * to diag(Q_i) (with Qf_i = qf_tie * Q_i), diag(R_i) and the goal x_ref_i.
+ * Active halfspace rows that are linearly dependent (on the inputs not held at
+ * a bound) are allowed: the polished point is the minimizer subject to the
+ * active rows with their right-hand side projected (Euclidean, least squares)
+ * onto the range of those rows, which equals the plain EQP solution when the
+ * rows are consistent; the gradient is that of this solution map.  Optional
+ * outputs (NULL to skip): mu_h [P][T] halfspace and mu_u [N][T][nu] bound
+ * multipliers of the polished point (0 for rows found dependent and for
+ * inactive ones) and the number of dependent active halfspace rows. */
 int orc_global_gradient(const orc_scenario* s, const uint8_t* act_h, const int8_t* W,
                         const double* targets /* [N][T][dp] */, double qf_tie,
                         double* X, double* U, double* loss,
                         double* gQ /* [N][nx] */, double* gR /* [N][nu] */,
-                        double* gGoal /* [N][nx] */);
+                        double* gGoal /* [N][nx] */, double* mu_h, double* mu_u, int* n_dependent);
 
 #ifdef __cplusplus
 }

@@ -649,3 +649,136 @@ def test_heterogeneous_agents_generator_recipe():
     sub = h1.subset([1, 3])
     ao = b.agent_off
     assert np.array_equal(sub.A_agent, np.concatenate([h1.A_agent[ao[1]:ao[2]], h1.A_agent[ao[3]:ao[4]]]))
+
+
+# ----------------------------------------------------------------------------
+# Polished point and gradient at an active set with linearly dependent rows
+# ----------------------------------------------------------------------------
+def _dependent_rows_instance(consistent: bool, seed: int = 3):
+    """Five agents, T = 2: all ten pairs are held active at t = 1.  The relative
+    positions of five agents span eight dimensions, so at most eight of the ten
+    halfspace rows are independent.  The normals at t = 1 are unit vectors with
+    a_ij'(pbar_i - pbar_j) = d_min for a reachable configuration pbar, so the
+    rows are consistent; with consistent=False one normal is rotated so that
+    they are not."""
+    rng = np.random.default_rng(seed)
+    N, T, dp, dt, d = 5, 2, 2, 0.1, 0.4
+    starts = np.array([[0.0, 0.0], [1.2, 0.1], [0.3, 1.1], [-1.0, 0.4], [0.2, -1.3]])
+    goals = -starts + 0.1 * rng.standard_normal(starts.shape)
+    x_init, x_ref, a, w0, _ = build_scenario(starts, goals, T, dt, d)
+    pbar = starts + 0.5 * dt * dt * rng.uniform(-0.8, 0.8, size=starts.shape)
+    pl = pair_list(N)
+    a = a.reshape(len(pl), T, dp).copy()
+    for k, (i, j) in enumerate(pl):
+        delta = pbar[i] - pbar[j]
+        nd = np.linalg.norm(delta)
+        phi = np.arccos(d / nd) * (1 if k % 2 == 0 else -1)
+        c, s = np.cos(phi), np.sin(phi)
+        a[k, 0] = np.array([[c, -s], [s, c]]) @ (delta / nd)
+    if not consistent:
+        c, s = np.cos(0.3), np.sin(0.3)
+        a[4, 0] = np.array([[c, -s], [s, c]]) @ a[4, 0]
+    b = make_batch([dict(N=N, T=T, x_init=x_init, x_ref=x_ref, a=a.reshape(-1, dp), w0=w0, d=d, rho=1.0,
+                         umax=1.0, c=None)], dp=dp, dt=dt, umax=1.0)
+    act = np.zeros((len(pl), T), dtype=np.uint8)
+    act[:, 0] = 1
+    W = np.zeros((N, T, 2), dtype=np.int8)
+    targets = rng.uniform(-2, 2, size=(N * T, dp))
+    return b, act, W, targets
+
+
+def _numpy_constrained_point(b, act, project: bool):
+    """Independent restatement: the global objective of Eq. (1) condensed per
+    agent with numpy (tests/helpers), the active halfspace rows G U = d, and the
+    minimizer over the affine set by the null-space method (SVD).  With
+    project=True d is first replaced by its Euclidean projection onto range(G)."""
+    N, T, nx, nu, dp = int(b.N[0]), int(b.T[0]), b.nx, b.nu, b.dp
+    pl = pair_list(N)
+    Hs, gs, Fs, Gs = [], [], [], []
+    for i in range(N):
+        Hx = np.array([2 * (b.Qd[i] if t < T else b.Qfd[i]) for t in range(1, T + 1)])
+        gx = np.array([-2 * (b.Qd[i] if t < T else b.Qfd[i]) * b.x_ref[i] for t in range(1, T + 1)])
+        H, g, F, G = agent_condensed_qp(b.A, b.B, Hx, gx, 2 * b.Rd[i], b.x_init[i])
+        Hs.append(H); gs.append(g); Fs.append(F); Gs.append(G)
+    n = N * T * nu
+    H = np.zeros((n, n)); g = np.zeros(n)
+    for i in range(N):
+        sl = slice(i * T * nu, (i + 1) * T * nu)
+        H[sl, sl] = Hs[i]; g[sl] = gs[i]
+    a = b.a.reshape(len(pl), T, dp)
+    rows, rhs = [], []
+    for k, t in zip(*np.nonzero(act)):
+        i, j = pl[k]
+        r = np.zeros(n)
+        r[i * T * nu:(i + 1) * T * nu] += a[k, t] @ Gs[i][t + 1][:dp]
+        r[j * T * nu:(j + 1) * T * nu] -= a[k, t] @ Gs[j][t + 1][:dp]
+        rows.append(r)
+        rhs.append(b.d_min[0] - a[k, t] @ (Fs[i][t + 1][:dp] - Fs[j][t + 1][:dp]))
+    G = np.array(rows); d = np.array(rhs)
+    Uu, sv, Vt = np.linalg.svd(G)
+    rank = int((sv > 1e-10 * sv[0]).sum())
+    if project:
+        d = Uu[:, :rank] @ (Uu[:, :rank].T @ d)
+    zp = np.linalg.lstsq(G, d, rcond=None)[0]
+    Z = Vt[rank:].T
+    zu = zp + Z @ np.linalg.solve(Z.T @ H @ Z, -Z.T @ (g + H @ zp))
+    X = np.zeros((N, T + 1, nx))
+    for i in range(N):
+        ui = zu[i * T * nu:(i + 1) * T * nu]
+        for t in range(T + 1):
+            X[i, t] = Fs[i][t] + Gs[i][t] @ ui
+    return X, G, d, rank
+
+
+@pytest.mark.parametrize("consistent", [True, False])
+def test_polished_point_with_dependent_active_rows(consistent):
+    b, act, W, targets = _dependent_rows_instance(consistent)
+    gr = oracle.global_gradient(b, 0, act, W, targets)
+    X, G, d, rank = _numpy_constrained_point(b, act, project=True)
+    assert rank == 8 and gr["n_dependent"] == 2
+    assert np.abs(gr["X"] - X).max() <= 1e-9 * max(1.0, np.abs(X).max())
+    pl = pair_list(5)
+    a = b.a.reshape(len(pl), 2, 2)
+    viol = np.array([a[k, 0] @ (gr["X"][i, 1, :2] - gr["X"][j, 1, :2]) - b.d_min[0] for k, (i, j) in enumerate(pl)])
+    if consistent:
+        assert np.abs(viol).max() <= 1e-10          # every active row holds, dependent ones included
+    else:
+        assert np.abs(viol).max() > 1e-3             # no point satisfies all ten rows
+        # the residual of the rows is the least-squares one: orthogonal to their range
+        assert np.abs(G.T @ viol).max() <= 1e-10 * max(1.0, np.abs(G).max())
+
+
+@pytest.mark.parametrize("consistent", [True, False])
+def test_gradient_with_dependent_active_rows_matches_central_differences(consistent):
+    """Central differences (h = 1e-6) of the loss at the polished point, at the
+    same (dependent) active set, against the implicit gradient: diag Q (tied
+    Qf), diag R and the goal state of every agent."""
+    b, act, W, targets = _dependent_rows_instance(consistent)
+    gr = oracle.global_gradient(b, 0, act, W, targets)
+    h = 1e-6
+
+    def loss(mod):
+        bb = b.subset([0])
+        mod(bb)
+        return oracle.global_gradient(bb, 0, act, W, targets)["loss"]
+
+    checked = 0
+    for i in range(5):
+        for r in range(4):
+            def mq(bb, s):
+                bb.Qd = bb.Qd.copy(); bb.Qfd = bb.Qfd.copy()
+                bb.Qd[i, r] += s; bb.Qfd[i, r] += 10 * s
+
+            def mg(bb, s):
+                bb.x_ref = bb.x_ref.copy(); bb.x_ref[i, r] += s
+            for mod, an in ((mq, gr["gQ"][i, r]), (mg, gr["gGoal"][i, r])):
+                fd = (loss(lambda bb: mod(bb, h)) - loss(lambda bb: mod(bb, -h))) / (2 * h)
+                assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (i, r, fd, an)
+                checked += 1
+        for c in range(2):
+            def mr(bb, s):
+                bb.Rd = bb.Rd.copy(); bb.Rd[i, c] += s
+            fd = (loss(lambda bb: mr(bb, h)) - loss(lambda bb: mr(bb, -h))) / (2 * h)
+            assert abs(fd - gr["gR"][i, c]) <= 1e-5 * max(1.0, abs(fd)), (i, c, fd, gr["gR"][i, c])
+            checked += 1
+    assert checked == 50
