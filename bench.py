@@ -13,9 +13,18 @@ e2e        the same metric through the C ABI from pinned host buffers: upload of
            residuals, all inside the timed region.
 roofline   FP64 pipe (ALU-bound): algorithmic flops of the step from the kernel's
            own event counters (pair-steps, EQP stages, factorized stages) over the
-           device time; peak 1.259 TFLOP/s = 152 SMs x 4 FP64 flop/clk x 2.07 GHz.
+           device time, against the FP64 FMA throughput measured in the same run
+           by the library's probe kernel (tadmm_fma_probe); the derived figure
+           152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.259 TFLOP/s is reported beside
+           it.  DRAM traffic and executed FP64 instruction counts come from the
+           committed ncu summary of this kernel, used only while the kernel
+           sources hash to the value recorded there.
 plain_gpu  the same kernels, one scenario at a time, one launch per phase and a
-           host read of the residuals every iteration, on a seeded sample.
+           host read of the residuals every iteration, on a seeded sample; the
+           work-matched speedup is the ratio of scenario-iterations per second.
+extras     the other synthetic workloads (2-agent crossing, 14-agent ring,
+           512-agent 3D swarm, 64 x 16-agent differentiation batch), float32 and
+           double-float arithmetic and the extensions, each device-timed.
 cpu_baseline  the FP64 oracle on the host cores on a bounded seeded sample
            (one scenario per core, 20 ADMM iterations each), scaled to solves/s
            with the GPU run's solves per scenario-iteration.
@@ -42,19 +51,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "multi-agent QP solves/sec at residual 1e-4 (batched vs plain GPU); ms/solve"
 UNIT = "solves/s"
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_batched launch of the 4096-scenario
-# mixed batch (FP64, 500 iterations, 32 threads per CTA, register variant 0), one ncu pass
-K_BATCHED_TRAFFIC_BYTES = 893.11e9 + 321.97e9
-PEAK_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 1.259
+PEAK_FP64_DERIVED_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 1.259
 # Solves per scenario-iteration of the 4096-scenario mixed batch at tol 1e-4,
 # max_iter 500: 194 solves in 1 955 163 scenario-iterations.  A property of the
 # ADMM iterates on these instances (the GPU and the oracle produce the same
-# iterates and iteration counts); the reference arm uses it to express the
-# oracle's measured scenario-iteration throughput in solves/s, so the ratio of
-# the two arms is the ratio of their scenario-iteration throughputs.
-WORKLOAD_SOLVES_PER_SCEN_ITER = 194.0 / 1955163.0
-# algorithmic flops per unit (2D double integrator, nx=4, nu=2)
-FLOPS_PAIRSTEP, FLOPS_EQP_STAGE, FLOPS_FACT_STAGE = 30.0, 190.0, 580.0
+# iterates and iteration counts; a GPU test checks these two numbers against a
+# fresh solve, so a change of the kernels or the generator cannot leave them
+# stale); the reference arm uses it to express the oracle's measured
+# scenario-iteration throughput in solves/s, so the ratio of the two arms is
+# the ratio of their scenario-iteration throughputs.
+WORKLOAD_SOLVES, WORKLOAD_SCEN_ITERS = 194, 1955163
+WORKLOAD_SOLVES_PER_SCEN_ITER = WORKLOAD_SOLVES / WORKLOAD_SCEN_ITERS
+# algorithmic flops per unit: pair-step, EQP stage, factorized stage
+FLOPS_2D = (30.0, 190.0, 580.0)     # nx = 4, nu = 2
+FLOPS_3D = (41.0, 420.0, 1950.0)    # nx = 6, nu = 3
+FLOPS_PAIRSTEP, FLOPS_EQP_STAGE, FLOPS_FACT_STAGE = FLOPS_2D
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "k_batched_mixed4096_counters.txt")
 
 
 def parse():
@@ -67,7 +79,7 @@ def parse():
     p.add_argument("--n-scen", type=int, default=4096)
     p.add_argument("--tol", type=float, default=1e-4)
     p.add_argument("--max-iter", type=int, default=500)
-    p.add_argument("--plain-sample", type=int, default=16)
+    p.add_argument("--plain-sample", type=int, default=64)
     p.add_argument("--cpu-iters", type=int, default=20)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-plain", action="store_true")
@@ -135,6 +147,64 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
+def source_hash() -> str:
+    """Hash of the CUDA sources and the C ABI header (what a kernel profile was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_15838_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    with open(os.path.join(ROOT, "include", "tadmm.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_counters(tpc: int, variant: int):
+    """Figures of the committed ncu summary of k_batched (key = value lines),
+    or (None, reason) when the kernel sources or the launch shape differ."""
+    try:
+        with open(COUNTERS_FILE) as f:
+            kv = dict(ln.split("=", 1) for ln in f if "=" in ln and not ln.lstrip().startswith("#"))
+    except OSError:
+        return None, "no profile summary"
+    kv = {k.strip(): v.strip() for k, v in kv.items()}
+    if kv.get("source_hash") != source_hash():
+        return None, "kernel sources changed since the profile (hash %s, now %s)" % (kv.get("source_hash"),
+                                                                                    source_hash())
+    if (int(kv.get("threads_per_cta", -1)), int(kv.get("kernel_variant", -1))) != (tpc, variant):
+        return None, "launch shape differs from the profiled one"
+    return kv, None
+
+
+def measure_fma_peaks(tg, torch, target_ms=40.0):
+    """FP64 and FP32 FMA throughput of this GPU (TFLOP/s) from the library's
+    probe kernel, timed with CUDA events; best of 3 after a calibration run."""
+    import ctypes as C
+    L = tg.lib()
+    L.tadmm_fma_probe.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_void_p]
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    out = {}
+    for prec in (64, 32):
+        fl = C.c_double(0.0)
+
+        def timed(iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tg._check(L.tadmm_fma_probe(prec, int(iters), 8, C.byref(fl), sp), "tadmm_fma_probe")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), fl.value
+        iters = 2000 if prec == 64 else 50000
+        ms, _ = timed(iters)
+        iters = max(1, int(iters * target_ms / max(ms, 1e-3)))
+        best = min(timed(iters)[0] for _ in range(3))
+        out[prec] = fl.value / (best / 1e3) / 1e12
+    return out
+
+
 def workload_batch(n_scen: int, rank: int):
     """Rank r's shard of the weak-scaling job: scenario ids r*n_scen .. (r+1)*n_scen-1."""
     from instances import make_workload
@@ -156,12 +226,13 @@ def aggregate(t_local: float, solves_local: float, dist, device):
 
 def algorithmic_flops(batch, cnt, sol):
     """Flops of one step from the kernel's counters (per-unit figures above)."""
+    fp, fe, ff = FLOPS_2D if batch.nx == 4 else FLOPS_3D
     T = batch.T.astype(np.float64)
     lqr = np.where(sol["iters"] > 0, batch.N, 0) * T   # warm-start LQR solve of the first iteration
     eqp_stages = float((cnt["eqp"] * T).sum() + lqr.sum())
     fact_stages = float(cnt["fact"].sum())
     pairsteps = float(cnt["pairsteps"].sum())
-    flops = FLOPS_PAIRSTEP * pairsteps + FLOPS_EQP_STAGE * eqp_stages + FLOPS_FACT_STAGE * fact_stages
+    flops = fp * pairsteps + fe * eqp_stages + ff * fact_stages
     return flops, dict(pairsteps=pairsteps, eqp_stages=eqp_stages, fact_stages=fact_stages)
 
 
@@ -242,6 +313,9 @@ def run_ours(args, rank, world):
                        threads_per_cta=args.tpc, kernel_variant=args.variant)
     tpc, cps, var = (args.tpc, 0, args.variant) if args.no_autotune else solver.autotune(probe_iter=100)
     stream = torch.cuda.current_stream()
+    peak_clocks = ClockSampler(dev)
+    with peak_clocks:
+        peaks = measure_fma_peaks(tg, torch)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
@@ -331,21 +405,31 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             bdt = time.perf_counter() - t0
             bs.close()
+            scen_iter_rate = scen_iters * args.steps / t_local
             plain = {"value": pconv / pdt, "unit": UNIT, "scenarios": len(idx), "solves": pconv,
                      "seconds": pdt, "scenario_iterations_per_s": pscen_iters / pdt,
+                     "speedup_scenario_iterations": scen_iter_rate / (pscen_iters / pdt),
                      "batched_same_sample_seconds": bdt,
                      "speedup_batched_full_vs_plain": (value / (pconv / pdt)) if pconv else None,
-                     "speedup_same_sample_wall": pdt / bdt}
+                     "speedup_same_sample_wall": pdt / bdt,
+                     "note": "work-matched speedup = batched scenario-iterations/s over plain; the solves/s "
+                             "ratio also reflects which sampled scenarios converge within the cap"}
         cpu = None
         if not args.no_cpu:
             cpu = cpu_baseline(batch, args, solves_local / max(1, scen_iters))
-        ext = None if args.no_extras else extras(tg, torch, batch, args)
+        ext = None if args.no_extras else extras(tg, torch, batch, args, peaks)
         clk = clocks.summary()
         launches = args.steps * solver_launches(solver)
-        # DRAM bytes of one launch of this exact workload and launch shape, from the
-        # committed ncu capture (profiles/k_batched_mixed4096_traffic.md); null otherwise
-        traffic = (K_BATCHED_TRAFFIC_BYTES if (args.n_scen, args.max_iter, args.precision, tpc, var) ==
-                   (4096, 500, 64, 32, 0) else None)
+        prof, prof_why = profile_counters(tpc, var)
+        traffic = executed = None
+        if prof is not None and (args.n_scen, args.max_iter, args.precision) == (4096, 500, 64):
+            traffic = float(prof["dram_bytes_per_launch"])
+            # executed FP64 thread-flops per algorithmic flop (small capture) scaled to this step
+            ratio = float(prof["executed_per_algorithmic_flop"])
+            ex = achieved * ratio
+            executed = {"tflops": ex, "frac": ex / peaks[64], "executed_per_algorithmic_flop": ratio,
+                        "source": "ncu thread-level DFMA (x2), DADD, DMUL counts of k_batched on "
+                                  + prof.get("small_case", "a small case")}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -363,9 +447,20 @@ def run_ours(args, rank, world):
             "scenario_iterations_per_s": scen_iters * args.steps / t_local,
             "clocks": clk,
             "roofline": {"bound": "alu", "kernel": "k_batched (FP64 pipe)", "achieved": achieved,
-                         "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
-                         "traffic": traffic, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                         "peak": peaks[64], "unit": "TFLOP/s", "frac": achieved / peaks[64],
+                         "traffic": traffic, "traffic_note": prof_why,
+                         "peak_source": "measured in this run: FP64 FMA probe kernel (tadmm_fma_probe), 8 CTAs "
+                                        "of 256 threads per SM, CUDA events, best of 3",
+                         "peak_clocks": peak_clocks.summary(),
+                         "peak_fp32_measured": peaks[32],
+                         "peak_derived": PEAK_FP64_DERIVED_TFLOPS, "frac_of_derived": achieved / PEAK_FP64_DERIVED_TFLOPS,
+                         "peak_derived_source": "152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                         "executed": executed,
                          "algorithmic_units": units, "algorithmic_flops_per_step": flops},
+            "workload_check": {"solves": solves_local, "scenario_iterations": scen_iters,
+                               "matches_reference_arm_constant": (solves_local, scen_iters) ==
+                               (WORKLOAD_SOLVES, WORKLOAD_SCEN_ITERS) if args.n_scen == 4096 and rank == 0 and
+                               (args.tol, args.max_iter, args.precision) == (1e-4, 500, 64) else None},
             "plain_gpu": plain,
             "cpu_baseline": cpu,
             "extras": ext,
@@ -400,7 +495,112 @@ def timed_solves(tg, torch, batch, args, reps=2, **kw):
     return dict(value=conv / (m / 1e3), unit=UNIT, ms_per_step=m, solves_per_step=conv, launch=tuned)
 
 
-def extras(tg, torch, batch, args):
+def _event_ms(torch, fn, reps=5):
+    """Median device time (CUDA events on the current stream) of fn() after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def _loss_grad(b, X):
+    """Loss sum ||p_it - target_it||^2 (t = 1..T) of the differentiation workload and dl/dX."""
+    g = np.zeros_like(X)
+    xo = to = 0
+    for k in range(b.n_scen):
+        N, T = int(b.N[k]), int(b.T[k])
+        Xk = X[xo:xo + N * (T + 1) * b.nx].reshape(N, T + 1, b.nx)
+        e = Xk[:, 1:, :b.dp] - b.targets[to:to + N * T].reshape(N, T, b.dp)
+        gk = np.zeros_like(Xk)
+        gk[:, 1:, :b.dp] = 2 * e
+        g[xo:xo + gk.size] = gk.ravel()
+        xo += gk.size
+        to += N * T
+    return g
+
+
+def other_workloads(tg, torch, args, peaks):
+    """The remaining synthetic workloads, device-timed with CUDA events."""
+    from instances import make_workload
+    out = {}
+    # 2 agents, T = 20: latency of one solve to tol 1e-4 in each execution mode
+    b = make_workload("pair")
+    row = {}
+    for mode in ("batched", "graph", "plain"):
+        s = tg.Solver(b, precision=64, mode=mode)
+        row[f"ms_per_solve_{mode}"] = _event_ms(torch, lambda: s.solve(args.tol, args.max_iter), reps=10)
+        sol = s.split(s.solution())[0]
+        s.close()
+        row["iterations"], row["status"] = sol["iters"], sol["status"]
+    s = tg.Solver(b, precision=32)
+    row["ms_per_solve_batched_fp32"] = _event_ms(torch, lambda: s.solve(args.tol, args.max_iter), reps=10)
+    s.close()
+    row["note"] = "one scenario: latency-bound (a roofline fraction is not meaningful at 20 pair-steps)"
+    out["pair_2_agents"] = row
+    # 14 agents, T = 20: ms per iteration over 500 iterations; iterations to tol 1e-4 with balancing
+    b = make_workload("ring14")
+    row = {}
+    for mode, prec in (("batched", 64), ("graph", 64), ("plain", 64), ("batched", 32)):
+        s = tg.Solver(b, precision=prec, mode=mode)
+        row[f"ms_per_iteration_{mode}_fp{prec}"] = _event_ms(torch, lambda: s.solve(0.0, 500), reps=3) / 500
+        s.close()
+    s = tg.Solver(b, precision=64)
+    s.solve(args.tol, args.max_iter)
+    sol = s.split(s.solution())[0]
+    s.close()
+    row["status_at_500"], row["residual_r_at_500"] = sol["status"], sol["r"]
+    s = tg.Solver(b, precision=64, adapt=(10, 10.0, 2.0))
+    row["ms_to_tol_with_residual_balancing"] = _event_ms(torch, lambda: s.solve(args.tol, 20000), reps=2)
+    sol = s.split(s.solution())[0]
+    s.close()
+    row["iterations_to_tol_with_residual_balancing"], row["status_with_residual_balancing"] = sol["iters"], sol["status"]
+    row["note"] = ("rho = 1 as the workload states does not reach 1e-4 within 500 iterations (the oracle agrees); "
+                   "residual balancing (every 10 iterations, mu 10, tau 2) is an extension, labelled as such")
+    out["ring_14_agents"] = row
+    # 512 agents, 3D, T = 40: graph mode, ms per iteration over 100 iterations, FP64 roofline
+    b = make_workload("swarm3d")
+    row = {}
+    s = tg.Solver(b, precision=64, mode="graph")
+    ms = _event_ms(torch, lambda: s.solve(0.0, 100), reps=2)
+    cnt, sol = s.counters(), s.solution()
+    s.close()
+    fl, units = algorithmic_flops(b, cnt, sol)
+    row.update(ms_per_iteration_graph=ms / 100, iterations=100, algorithmic_units_per_100=units,
+               tflops=fl / (ms / 1e3) / 1e12, frac_of_measured_fp64=fl / (ms / 1e3) / 1e12 / peaks[64])
+    s = tg.Solver(b, precision=64, mode="plain")
+    row["ms_per_iteration_plain"] = _event_ms(torch, lambda: s.solve(0.0, 20), reps=2) / 20
+    s.close()
+    row["note"] = ("one scenario of 130816 pairs x 40 steps; the FP64 fraction counts algorithmic flops "
+                   "(41 per pair-step, 420 per EQP stage, 1950 per factorized stage) over the measured FP64 peak")
+    out["swarm3d_512_agents"] = row
+    # 64 scenarios x 16 agents, T = 30: solve, active-set polish and implicit-KKT backward
+    b = make_workload("diff", n_scen=64)
+    for prec, tol, iters in ((64, 1e-6, 2000), (32, 1e-5, 5000)):
+        row = {}
+        s = tg.Solver(b, precision=prec, adapt=(10, 10.0, 2.0))
+        row["ms_solve"] = _event_ms(torch, lambda: s.solve(tol, iters), reps=2)
+        t0 = time.perf_counter()
+        pol = s.polish(1e-9, 100)
+        row["ms_polish"] = 1e3 * (time.perf_counter() - t0)
+        row["polish_rounds"], row["polished_to_kkt"] = pol["rounds"], int((pol["status"] == 0).sum())
+        gX = _loss_grad(b, s.backward(None)["X_polished"])
+        row["ms_backward"] = _event_ms(torch, lambda: s.backward(gX), reps=3)
+        s.close()
+        row["note"] = (f"ADMM with residual balancing to tol {tol} or {iters} iterations, then active-set "
+                       "polishing (host-synchronized rounds, wall time) and the adjoint (host wall time "
+                       "includes the copies of the gradients)")
+        out[f"differentiation_64x16_fp{prec}"] = row
+    return out
+
+
+def extras(tg, torch, batch, args, peaks):
     out = {}
     out["fp32"] = timed_solves(tg, torch, batch, args, precision=32)
     out["fp32"]["note"] = "float32 arithmetic, same workload; parity 1e-4 against the float64 oracle"
@@ -424,31 +624,11 @@ def extras(tg, torch, batch, args):
     # one outer linearize-and-solve step: the device-side re-linearization of every halfspace
     s = tg.Solver(batch, precision=64)
     s.solve(args.tol, 20)
-    s.relinearize()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    s.relinearize()
-    e1.record()
-    torch.cuda.synchronize()
+    ms = _event_ms(torch, s.relinearize, reps=3)
     s.close()
-    out["relinearize"] = {"ms": e0.elapsed_time(e1), "pair_steps": int((batch.P * batch.T).sum()),
+    out["relinearize"] = {"ms": ms, "pair_steps": int((batch.P * batch.T).sum()),
                           "note": "normals and guesses re-formed at the last iterate, whole batch, one call"}
-    # one 512-agent 3D scenario (130816 pairs x 40 steps): graph mode vs plain mode per iteration
-    from instances import make_workload
-    sw = make_workload("swarm3d")
-    rows = {}
-    for mode in ("graph", "plain"):
-        s = tg.Solver(sw, precision=64, mode=mode)
-        s.solve(0.0, 2)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s.solve(0.0, 20)
-        torch.cuda.synchronize()
-        rows[mode] = 1e3 * (time.perf_counter() - t0) / 20
-        s.close()
-    out["swarm3d_512_agents"] = {"ms_per_iteration_graph": rows["graph"], "ms_per_iteration_plain": rows["plain"],
-                                 "pair_steps_per_iteration": 130816 * 40, "precision": 64}
+    out.update(other_workloads(tg, torch, args, peaks))
     return out
 
 

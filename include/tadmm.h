@@ -45,6 +45,8 @@ extern "C" {
 #define TADMM_NOT_CONVERGED 1 /* max_iter reached */
 #define TADMM_QP_FAIL 2       /* an agent QP hit the active-set iteration cap */
 #define TADMM_NUMERIC 3       /* non-finite residual or non-positive pivot */
+#define TADMM_INVALID_INPUT 4 /* tadmm_solve_noalloc: an input value breaks the rules that
+                                 tadmm_create checks on the host; nothing was solved */
 
 /* start modes of the per-agent QP (the paper's ablation variants, Sec. V.B) */
 #define TADMM_START_COLD 0  /* BaseADMM: u = clip(0), empty working set, every iteration */
@@ -209,20 +211,56 @@ int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* t
  * equality-constrained QP; its KKT system is solved exactly (the polished
  * solution) and differentiated implicitly: per-agent Riccati solves of the
  * block-tridiagonal LQ problems (Sec. IV.B) coupled through a dense Schur
- * complement over the active halfspaces.
+ * complement over the active halfspaces.  Active rows may be linearly
+ * dependent: the Schur complement is factored with diagonal pivoting up to its
+ * numerical rank (pivots above 1e-12 (float64) or 1e-6 (float32) times its
+ * largest diagonal entry), and the polished solution satisfies the active rows
+ * with their right-hand side projected, in the least-squares sense, onto the
+ * range of the rows (the rows themselves when they are consistent); the
+ * gradient is that of this solution map.
  *   grad_X      dl/dX in the layout of X (host or device), entries at t = 0 are
- *               ignored (x_0 is data)
+ *               ignored (x_0 is data); NULL: only the polished solution, status
+ *               and n_dependent are formed (the gradient outputs are not written)
  *   gQ, gQf     [sum N][nx] dl/d diag(Q_i) (stages t < T) and dl/d diag(Qf_i);
  *               for a tie Qf_i = c Q_i the total is gQ + c gQf
  *   gR          [sum N][nu] dl/d diag(R_i)
  *   gGoal       [sum N][nx] dl/d x_ref_i
  *   X_polished  polished states in the layout of X
- *   status      [n_scen] TADMM_CONVERGED, or TADMM_NUMERIC when the Schur
- *               complement is not positive definite (dependent active rows)
+ *   status      [n_scen] TADMM_CONVERGED, or TADMM_NUMERIC when a value is not
+ *               finite
+ *   n_dependent [n_scen] active halfspace rows found linearly dependent
  * Outputs may be host or device pointers, any may be NULL.  Horizons T <= 64.
  * Allocates its scratch on first use; synchronizes `stream`. */
 int tadmm_backward(tadmm_handle* h, const double* grad_X, double theta_eps, double* gQ, double* gQf,
-                   double* gR, double* gGoal, double* X_polished, int32_t* status, void* stream);
+                   double* gR, double* gGoal, double* X_polished, int32_t* status, int32_t* n_dependent,
+                   void* stream);
+
+/* Active-set polishing of the last solve's result on the centralized QP (an
+ * addition beyond the paper).  ADMM stopped at a tolerance leaves halfspaces
+ * whose scaled dual theta has not yet decayed to zero, so the active set read
+ * off its final iterate (inputs held at a bound by the last x-update,
+ * halfspaces with theta > theta_eps) need not be the optimal one.  Each round
+ * forms the polished point of the current set (as tadmm_backward does) and
+ * checks the KKT conditions of Eq. (1) with the linearized halfspaces there:
+ * active rows with a multiplier below -kkt_tol * max(1, largest multiplier)
+ * leave the set, and inactive halfspaces violated by more than
+ * kkt_tol * max(1, d_min), or inputs outside the box by more than
+ * kkt_tol * max(1, |bound|), enter it (held at the violated bound).  Rounds
+ * stop when no scenario's set changes or after max_rounds.  The refined set is
+ * kept in the handle: tadmm_backward uses it (and ignores its theta_eps) until
+ * the next tadmm_solve.
+ *   kkt_tol     0 = 1e-9 (float64) / 1e-5 (float32)
+ *   act         [sum P T] uint8 halfspace flags in the pair-step order of `a`
+ *   W           [sum N][T][nu] int8 held inputs (0 free, 1 lower, 2 upper)
+ *   status      [n_scen] TADMM_CONVERGED when the last round found the KKT
+ *               conditions satisfied, TADMM_NOT_CONVERGED when max_rounds was
+ *               reached first, TADMM_NUMERIC on a non-finite value
+ *   rounds      rounds taken
+ * act and W may be host or device pointers; status and rounds are host
+ * pointers; any may be NULL.  Horizons T <= 64.  Allocates its scratch on
+ * first use; synchronizes `stream` after every round. */
+int tadmm_polish(tadmm_handle* h, double theta_eps, int32_t max_rounds, double kkt_tol, uint8_t* act, int8_t* W,
+                 int32_t* status, int32_t* rounds, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free single-scenario solve.
@@ -242,13 +280,22 @@ int tadmm_backward(tadmm_handle* h, const double* grad_X, double theta_eps, doub
  *  - a scenario whose state does not fit (about 32 bytes per pair-step plus
  *    ~400 bytes per agent-step in 2D) is rejected with TADMM_EINVAL naming the
  *    required size; nothing is launched;
- *  - the first call on each device looks up the array's device address on that
- *    device (it must be current); make that first call before any stream
- *    capture;
+ *  - the array's device address is looked up with the device current, on
+ *    every call made outside stream capture (a call during a capture reuses the
+ *    last lookup on that device); with lazy module loading (the CUDA default)
+ *    the first call on each device also loads the library's module there,
+ *    which the driver allocates for: make one warm-up call per device (and per
+ *    (nx, nu, dp), whose kernels load on first use) at start-up, before any
+ *    stream capture; later calls allocate nothing;
  *  - every call shares the array and re-initializes all state it reads; calls
  *    whose GPU work overlaps (other streams or host threads on the same device)
  *    race on it and must be serialized by the caller;
- *  - input values are not checked on the host (they are on the device);
+ *  - input values are checked on the device by the rules tadmm_create applies
+ *    on the host (finite data, umin <= umax, Q, Qf >= 0, R > 0); a scenario
+ *    that breaks one gets status TADMM_INVALID_INPUT with iterations 0 and
+ *    residuals NaN, is not solved, and its X, U, theta are left unspecified;
+ *    pointers, sizes, rho, d_min, tol and max_iter are checked on the host
+ *    (TADMM_EINVAL);
  *  - asynchronous on `stream`; outputs: X [N][T+1][nx], U [N][T][nu],
  *    theta [P*T] (may be NULL), status_iters [2] = {status, iterations},
  *    res [2] = {r, s}; any output pointer may be NULL.                        */
@@ -266,6 +313,15 @@ typedef struct {
 
 int tadmm_solve_noalloc(const tadmm_scenario_dev* scenario, int32_t start_mode, double tol, int32_t max_iter,
                         double* X, double* U, double* theta, int32_t* status_iters, double* res, void* stream);
+
+/* Arithmetic roof probe (measurement helper; the paper has no counterpart).
+ * Enqueues on `stream` one kernel that fills every SM with blocks_per_sm CTAs
+ * of 256 threads, each running 8 independent fused multiply-add chains of
+ * `iters` steps in float64 (precision 64) or float32 (32), and writes the
+ * floating-point operations it performs (2 per FMA) to *flops (host pointer).
+ * Timing it with events on the same stream gives the measured FP64 / FP32
+ * throughput of the device.  Asynchronous; allocates nothing. */
+int tadmm_fma_probe(int32_t precision, int32_t iters, int32_t blocks_per_sm, double* flops, void* stream);
 
 /* Frees all device memory of the handle (synchronizes the device first). */
 void tadmm_destroy(tadmm_handle* h);

@@ -68,7 +68,9 @@ def lib():
         L.tadmm_relinearize.argtypes = [C.c_void_p, C.c_void_p]
         L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p, _i32p]
         L.tadmm_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
-                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.tadmm_polish.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_double, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_destroy.argtypes = [C.c_void_p]
         L.tadmm_destroy.restype = None
         L.tadmm_last_error.restype = C.c_char_p
@@ -208,14 +210,20 @@ class Solver:
         return dict(X=X, U=U, theta=th[:self.sizes["theta"]], W=W, status=st, iters=it, res=res)
 
     def backward(self, grad_X, theta_eps: float = 1e-9, polished: bool = True, stream=None):
-        """Implicit-KKT gradients of a loss at the final active set of the last solve.
+        """Implicit-KKT gradients of a loss at the final active set of the last solve
+        (or the set refined by polish()).
 
-        grad_X: dl/dX in the packed layout of X (numpy array or CUDA tensor).
-        Returns numpy arrays gQ, gQf, gR, gGoal (per agent), the polished
-        states X_polished and the per-scenario status."""
+        grad_X: dl/dX in the packed layout of X (numpy array or CUDA tensor), or
+        None for the polished states alone.  Returns numpy arrays gQ, gQf, gR,
+        gGoal (per agent), the polished states X_polished, the per-scenario
+        status and the number of active halfspace rows found linearly dependent
+        (n_dependent)."""
         b = self.batch
         na = int(b.N.sum())
-        if hasattr(grad_X, "data_ptr"):
+        if grad_X is None:
+            keep = None
+            gptr = None
+        elif hasattr(grad_X, "data_ptr"):
             g = grad_X.detach().to(dtype=__import__("torch").float64).contiguous()
             gptr = C.c_void_p(g.data_ptr())
             keep = g
@@ -226,11 +234,27 @@ class Solver:
         gQ = np.zeros((na, b.nx)); gQf = np.zeros((na, b.nx)); gR = np.zeros((na, b.nu)); gG = np.zeros((na, b.nx))
         Xp = np.zeros(self.sizes["X"]) if polished else None
         st = np.zeros(self.n_scen, dtype=np.int32)
+        nd = np.zeros(self.n_scen, dtype=np.int32)
         p = lambda a: C.c_void_p(a.ctypes.data) if a is not None else None
         _check(lib().tadmm_backward(self.h, gptr, float(theta_eps), p(gQ), p(gQf), p(gR), p(gG), p(Xp),
-                                    p(st), C.c_void_p(_stream_ptr(stream))), "tadmm_backward")
+                                    p(st), p(nd), C.c_void_p(_stream_ptr(stream))), "tadmm_backward")
         del keep
-        return dict(gQ=gQ, gQf=gQf, gR=gR, gGoal=gG, X_polished=Xp, status=st)
+        return dict(gQ=gQ, gQf=gQf, gR=gR, gGoal=gG, X_polished=Xp, status=st, n_dependent=nd)
+
+    def polish(self, theta_eps: float = 1e-9, max_rounds: int = 20, kkt_tol: float = 0.0, stream=None):
+        """Refines the active set of the last solve on the centralized QP until
+        the KKT conditions hold (tadmm_polish); backward() then uses it.
+        Returns the halfspace flags act [sum P T] (pair-step order of `a`), the
+        held inputs W [sum N T nu], the per-scenario status and the rounds."""
+        act = np.zeros(max(self.sizes["theta"], 1), dtype=np.uint8)
+        W = np.zeros(self.sizes["U"], dtype=np.int8)
+        st = np.zeros(self.n_scen, dtype=np.int32)
+        nr = C.c_int32(0)
+        _check(lib().tadmm_polish(self.h, float(theta_eps), int(max_rounds), float(kkt_tol),
+                                  C.c_void_p(act.ctypes.data), C.c_void_p(W.ctypes.data),
+                                  C.c_void_p(st.ctypes.data), C.byref(nr), C.c_void_p(_stream_ptr(stream))),
+               "tadmm_polish")
+        return dict(act=act[:self.sizes["theta"]], W=W, status=st, rounds=nr.value)
 
     def counters(self):
         eqp = np.zeros(self.n_scen, dtype=np.int64)
@@ -307,7 +331,7 @@ class TADMMFunction:
                 b.x_ref = np.ascontiguousarray(goal.detach().cpu().numpy(), dtype=np.float64)
                 solver.update(b)
                 solver.solve(tol, max_iter)
-                out = solver.backward(np.zeros(solver.sizes["X"]), theta_eps=theta_eps)
+                out = solver.backward(None, theta_eps=theta_eps)
                 ctx.solver, ctx.qf_tie, ctx.theta_eps = solver, qf_tie, theta_eps
                 ctx.status = out["status"]
                 return torch.from_numpy(out["X_polished"]).to(Qd.device)

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libtadmm.so")
 SOURCES = ["tadmm_api.cu", "tadmm_f64_2d.cu", "tadmm_f64_3d.cu", "tadmm_f32_2d.cu", "tadmm_f32_3d.cu",
-           "tadmm_noalloc.cu", "tadmm_df64_2d.cu"]
+           "tadmm_noalloc.cu", "tadmm_df64_2d.cu", "tadmm_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

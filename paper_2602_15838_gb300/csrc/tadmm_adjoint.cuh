@@ -11,13 +11,24 @@
 // responses Psi.  The polished primal solution and the adjoint of a loss
 // gradient dl/dX follow from two block solves each; the parameter gradients
 // are closed forms in the polished solution and the adjoint.
+//
+// Active rows may be linearly dependent (several halfspaces through the same
+// agents and step, or rows whose positions are fixed by inputs held at a
+// bound); S is then singular and the multipliers are not unique.  S is
+// factored with diagonal pivoting up to its numerical rank, and the
+// multipliers are the least-squares solution of S mu = b in the factor's
+// range: the polished point then satisfies the active rows with their
+// right-hand side projected onto the range of the rows (exactly the rows
+// when they are consistent), and the gradient is that of this solution map.
 #pragma once
+
+#include <climits>
 
 namespace tadmm {
 
 struct BwdScen {
   int64_t psi_off;   // per-agent responses [N][T][DP][T][DP]
-  int64_t s_off;     // Schur complement [m][m]
+  int64_t s_off;     // Schur complement [m][m], then the normal matrix [m][m]
   int64_t v_off;     // vectors [3][m]
   int32_t m;         // active halfspaces
   int32_t pad;
@@ -27,6 +38,7 @@ template <typename F>
 struct BwdDev {
   const BwdScen* bs;
   int32_t* act;              // per scenario at ps_off: active pair-step indices q (t-major)
+  int32_t* piv;              // per scenario at ps_off: pivot order of the Schur factorization
   int32_t* act_cnt;          // [n_scen]
   unsigned long long* amask; // [agents] bit t-1 set when the agent has an active halfspace at t
   F* psi;
@@ -45,9 +57,29 @@ struct BwdDev {
   double* gR;                // [agents][NU]
   double* gGoal;             // [agents][NX]
   int32_t* bstatus;          // [n_scen]
+  int32_t* ndep;             // [n_scen] active rows found dependent (m - rank)
+  uint8_t* hmask;            // [pair-steps] active halfspaces (scenario layout [T][P] at ps_off)
+  uint16_t* Wb;              // [agent-steps] inputs held at a bound (layout of Wm)
+  int32_t* pchg;             // [n_scen] polishing: the active set changed in this round
+  int32_t adjoint;           // 0: stop after the polished primal point (polishing rounds)
+  double kkt_tol;            // polishing: relative tolerance of the KKT conditions
   double theta_eps;
+  double rank_tol;           // relative pivot size below which a row counts as dependent
   int64_t kk_stride;         // Tmax * NU
 };
+
+// Active set of the last solve's final iterate: halfspaces whose projection
+// step theta exceeds theta_eps and the inputs the last x-update held at a
+// bound (one CTA per scenario).
+template <typename F, int NX, int NU, int DP>
+__global__ void k_bwd_init(Dev<F> D, BwdDev<F> B) {
+  const int sc = blockIdx.x;
+  const ScenMeta s = D.meta[sc];
+  const F* th = D.theta + (size_t)(D.cur_lvl[sc] >> 1) * D.tot_ps + s.ps_off;
+  const int64_t PT = (int64_t)s.P * s.T, NT = (int64_t)s.N * s.T;
+  for (int64_t q = threadIdx.x; q < PT; q += blockDim.x) B.hmask[s.ps_off + q] = double(th[q]) > B.theta_eps ? 1 : 0;
+  for (int64_t e = threadIdx.x; e < NT; e += blockDim.x) B.Wb[s.as_off + e] = D.Wm[s.as_off + e];
+}
 
 // Ordered compaction of the active halfspaces of one scenario (one warp).
 template <typename F, int NX, int NU, int DP>
@@ -55,14 +87,14 @@ __global__ void k_bwd_count(Dev<F> D, BwdDev<F> B) {
   const int sc = blockIdx.x;
   const ScenMeta s = D.meta[sc];
   const int lane = threadIdx.x;
-  const F* th = D.theta + (size_t)(D.cur_lvl[sc] >> 1) * D.tot_ps + s.ps_off;
+  const uint8_t* hm = B.hmask + s.ps_off;
   for (int i = lane; i < s.N; i += 32) B.amask[s.agent_off + i] = 0ull;
   __syncwarp();
   const int64_t PT = (int64_t)s.P * s.T;
   int count = 0;
   for (int64_t base = 0; base < PT; base += 32) {
     const int64_t q = base + lane;
-    const bool on = q < PT && double(th[q]) > B.theta_eps;
+    const bool on = q < PT && hm[q] != 0;
     const unsigned ball = __ballot_sync(0xffffffffu, on);
     if (on) {
       const int pos = count + __popc(ball & ((1u << lane) - 1u));
@@ -224,6 +256,124 @@ __device__ void chol_solve_serial(const F* L, int m, F* x) {
   }
 }
 
+// Rank-revealing Cholesky of the positive semidefinite m x m matrix S (full
+// symmetric storage) by one CTA, with diagonal pivoting: step k takes the
+// largest remaining diagonal entry (ties to the lowest position) and stops
+// when it is not above rank_tol times the largest diagonal entry of S.  The
+// pivot order goes to piv; afterwards L[r][c] = S[piv[r] m + piv[c]] for
+// r >= c, c < rank is the factor of the permuted matrix restricted to its
+// first `rank` columns ([L11; L21]).  Returns the rank (same in every thread).
+template <typename F>
+__device__ int cta_pivoted_cholesky(F* S, int m, int* piv, F rank_tol) {
+  __shared__ F red_v[128];
+  __shared__ int red_i[128];
+  __shared__ F s_dref;
+  __shared__ int s_stop;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int r = tid; r < m; r += nt) piv[r] = r;
+  int rank = m;
+  for (int k = 0; k < m; ++k) {
+    __syncthreads();
+    F bv = F(-1);
+    int bi = m;
+    for (int j = k + tid; j < m; j += nt) {
+      const F v = S[(size_t)piv[j] * m + piv[j]];
+      if (v > bv) { bv = v; bi = j; }
+    }
+    red_v[tid] = bv;
+    red_i[tid] = bi;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+      if (tid < w) {
+        const F v2 = red_v[tid + w];
+        const int i2 = red_i[tid + w];
+        if (v2 > red_v[tid] || (v2 == red_v[tid] && i2 < red_i[tid])) {
+          red_v[tid] = v2;
+          red_i[tid] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const F v = red_v[0];
+      const int j = red_i[0];
+      if (k == 0) s_dref = v;
+      if (j >= m || !(v > rank_tol * s_dref)) {
+        s_stop = 1;
+      } else {
+        s_stop = 0;
+        const int t = piv[k];
+        piv[k] = piv[j];
+        piv[j] = t;
+        S[(size_t)piv[k] * m + piv[k]] = sqrt_(v);
+      }
+    }
+    __syncthreads();
+    if (s_stop) {
+      rank = k;
+      break;
+    }
+    const int pk = piv[k];
+    const F lkk = S[(size_t)pk * m + pk];
+    for (int r = k + 1 + tid; r < m; r += nt) S[(size_t)piv[r] * m + pk] /= lkk;
+    __syncthreads();
+    const int rem = m - k - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int pr = piv[k + 1 + e / rem], pc = piv[k + 1 + e % rem];
+      S[(size_t)pr * m + pc] = fma(-S[(size_t)pr * m + pk], S[(size_t)pc * m + pk], S[(size_t)pr * m + pc]);
+    }
+  }
+  __syncthreads();
+  return rank;
+}
+
+// Normal matrix M = L'L (rank x rank) of the rank-deficient factor and its
+// Cholesky factor, by one CTA (nothing to do when rank = m).  Sets *s_bad if
+// M is not positive definite.
+template <typename F>
+__device__ void cta_ls_prepare(const F* S, int m, const int* piv, int rank, F* M, int* s_bad) {
+  if (rank == m || rank == 0) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < rank * rank; e += nt) {
+    const int a = e / rank, b = e % rank;
+    if (b > a) continue;
+    F acc = 0;
+    for (int i = a; i < m; ++i) acc = fma(S[(size_t)piv[i] * m + piv[a]], S[(size_t)piv[i] * m + piv[b]], acc);
+    M[(size_t)a * rank + b] = acc;
+    M[(size_t)b * rank + a] = acc;
+  }
+  cta_cholesky(M, rank, s_bad);
+}
+
+// Least-squares solution of S lambda = b within the range of the pivoted
+// factor (one thread; b is overwritten by lambda, tmp has m entries):
+// v minimizes |L v - b_p| (b_p = b in pivot order), lambda_p = [L11^{-T} v; 0].
+// For rank = m this is the plain solve L11^{-T} L11^{-1} b_p.
+template <typename F>
+__device__ void ls_apply_serial(const F* S, int m, const int* piv, int rank, const F* M, F* b, F* tmp) {
+  auto L = [&](int r, int c) -> F { return S[(size_t)piv[r] * m + piv[c]]; };
+  if (rank == m) {
+    for (int r = 0; r < m; ++r) {
+      F v = b[piv[r]];
+      for (int k = 0; k < r; ++k) v = fma(-L(r, k), tmp[k], v);
+      tmp[r] = v / L(r, r);
+    }
+  } else {
+    for (int a = 0; a < rank; ++a) {
+      F acc = 0;
+      for (int i = a; i < m; ++i) acc = fma(L(i, a), b[piv[i]], acc);
+      tmp[a] = acc;
+    }
+    if (rank > 0) chol_solve_serial(M, rank, tmp);
+  }
+  for (int r = rank - 1; r >= 0; --r) {
+    F v = tmp[r];
+    for (int k = r + 1; k < rank; ++k) v = fma(-L(k, r), tmp[k], v);
+    tmp[r] = v / L(r, r);
+  }
+  for (int r = 0; r < m; ++r) b[piv[r]] = r < rank ? tmp[r] : F(0);
+}
+
 template <typename F, int NX, int NU, int DP, bool DI>
 __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
   using CL = CacheLayout<NX, NU>;
@@ -237,13 +387,16 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
   if (tid == 0) s_bad = 0;
   __syncthreads();
   F* cache = D.cache + s.xs_off * CL::E;
-  const uint16_t* Wm = D.Wm + s.as_off;
+  const uint16_t* Wm = B.Wb + s.as_off;
   const int32_t* act = B.act + s.ps_off;
   const F* a = D.a + s.ps_off * DP;
   const int32_t* pr = D.pairs + s.pair_off;
   F* psi = B.psi + bs.psi_off;
   F* Sm = B.S + bs.s_off;
+  F* Mn = Sm + (size_t)m * m;
+  int* piv = B.piv + s.ps_off;
   F* rhs = B.vec + bs.v_off;
+  F* tmp = rhs + 2 * m;
   F* pos0 = B.pos0 + s.as_off * DP;
   F* force = B.force + s.as_off * DP;
   auto Q = [&](int i, int r) { return D.Qd[(s.agent_off + i) * NX + r]; };
@@ -386,9 +539,12 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
               pos0[((size_t)i * T + tm1) * DP + c] - pos0[((size_t)j * T + tm1) * DP + c], v);
     rhs[h] = v;
   }
-  // 5. factor S and solve for the halfspace multipliers mu
-  if (m > 0) cta_cholesky(Sm, m, &s_bad);
-  if (tid == 0 && m > 0) chol_solve_serial(Sm, m, rhs);
+  // 5. rank-revealing factorization of S; least-squares multipliers mu
+  __syncthreads();
+  const int rank = m > 0 ? cta_pivoted_cholesky(Sm, m, piv, F(B.rank_tol)) : 0;
+  if (m > 0) cta_ls_prepare(Sm, m, piv, rank, Mn, &s_bad);
+  __syncthreads();
+  if (tid == 0 && m > 0) ls_apply_serial(Sm, m, piv, rank, Mn, rhs, tmp);
   __syncthreads();
 
   // 6. coupling forces G' mu, polished primal solve
@@ -434,8 +590,17 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
   }
   __syncthreads();
 
-  // 7. adjoint: w0 = H^{-1} dl/dz (homogeneous), S lam = -G w0, w = w0 + Psi G' lam
   F* lamw = rhs + m;
+  if (!B.adjoint) {
+    if (tid == 0) {
+      bool fin = true;
+      for (int h = 0; h < m; ++h) fin = fin && finite_(rhs[h]);
+      B.bstatus[sc] = (s_bad || !fin) ? ST_NUMERIC : ST_CONVERGED;
+      B.ndep[sc] = m - rank;
+    }
+    return;
+  }
+  // 7. adjoint: w0 = H^{-1} dl/dz (homogeneous), S lam = -G w0, w = w0 + Psi G' lam
   for (int i = tid; i < N; i += nt) {
     const double* g = B.gX + (s.xs_off + (int64_t)i * (T + 1)) * NX;
     F* kk = B.kks + ((s.agent_off + i) * DP) * (size_t)B.kk_stride;
@@ -461,7 +626,7 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
     lamw[h] = v;
   }
   __syncthreads();
-  if (tid == 0 && m > 0) chol_solve_serial(Sm, m, lamw);
+  if (tid == 0 && m > 0) ls_apply_serial(Sm, m, piv, rank, Mn, lamw, tmp);
   __syncthreads();
   forces(lamw);
   for (int i = tid; i < N; i += nt) {
@@ -518,7 +683,207 @@ __global__ void __launch_bounds__(128) k_bwd_main(Dev<F> D, BwdDev<F> B) {
       if (B.gR) B.gR[ag * NU + c] = double(gr);
     }
   }
-  if (tid == 0) B.bstatus[sc] = s_bad ? ST_NUMERIC : ST_CONVERGED;
+  if (tid == 0) {
+    bool fin = true;
+    for (int h = 0; h < m; ++h) fin = fin && finite_(rhs[h]) && finite_(lamw[h]);
+    B.bstatus[sc] = (s_bad || !fin) ? ST_NUMERIC : ST_CONVERGED;
+    B.ndep[sc] = m - rank;
+  }
+}
+
+// One round of active-set polishing on the centralized QP (one CTA per
+// scenario), after k_bwd_main (adjoint = 0) has formed the polished point of
+// the current active set, its halfspace multipliers mu (in the order of the
+// active list) and the coupling forces G' mu.  KKT check at that point:
+//   - halfspace rows: active ones need mu >= 0, inactive ones a'(p_i - p_j) >= d;
+//   - inputs: held ones need a non-negative bound multiplier, from
+//     stationarity mu_lower = 2 R u_t + B' lambda_{t+1} (mu_upper its negative)
+//     with the costates lambda_t = 2 Q_t (x_t - x_ref) - C' f_t + A' lambda_{t+1}
+//     of the global problem (f_t the coupling force), free ones lie in the box.
+// One change per round, as in a primal active-set method: the row with the
+// most negative multiplier below -kkt_tol * max(1, largest |multiplier|)
+// leaves the set; if there is none, the most violated row (halfspace
+// violation relative to max(1, d), box violation relative to max(1, |bound|))
+// beyond kkt_tol enters it (an input held at the violated bound).  Ties go to
+// the lowest index (halfspace rows in active-list or pair-step order first,
+// then inputs by agent, step, component).  pchg[sc] = 1 when the set changed.
+template <typename F, int NX, int NU, int DP, bool DI>
+__global__ void __launch_bounds__(128) k_bwd_polish(Dev<F> D, BwdDev<F> B) {
+  __shared__ Model<F, NX, NU> Mo;
+  __shared__ unsigned long long s_scale, s_key;
+  __shared__ long long s_idx;
+  load_model<F, NX, NU>(Mo, D.model);
+  const int sc = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const ScenMeta s = D.meta[sc];
+  const BwdScen bs = B.bs[sc];
+  const int N = s.N, T = s.T, P = s.P, m = bs.m;
+  const int32_t* act = B.act + s.ps_off;
+  const F* mu = B.vec + bs.v_off;
+  const F* a = D.a + s.ps_off * DP;
+  const int32_t* pr = D.pairs + s.pair_off;
+  const F* force = B.force + s.as_off * DP;
+  uint16_t* Wb = B.Wb + s.as_off;
+  uint8_t* hm = B.hmask + s.ps_off;
+  const int64_t PT = (int64_t)P * T;
+  if (tid == 0) {
+    s_scale = ord_bits(F(1));
+    s_key = ~0ull;
+    s_idx = LLONG_MAX;
+  }
+  __syncthreads();
+  // Costates of agent i backwards from lambda_{T+1} = 0; for every input u_{t-1}
+  // visit(t-1, c, working-set mask, u, g) with g = 2 R u_{t-1} + B' lambda_t.
+  auto sweep = [&](int i, auto&& visit) {
+    const Model<F, NX, NU>& Ma = agent_model<F, NX, NU>(D, Mo, s, i);
+    const F* Xp = B.Xp + (s.xs_off + (int64_t)i * (T + 1)) * NX;
+    const F* Up = B.Up + (s.as_off + (int64_t)i * T) * NU;
+    F lam[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) lam[r] = F(0);
+    for (int t = T; t >= 1; --t) {
+      F ln[NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        const F q = t < T ? D.Qd[(s.agent_off + i) * NX + r] : D.Qfd[(s.agent_off + i) * NX + r];
+        F acc = (F(2) * q) * (Xp[(size_t)t * NX + r] - D.x_ref[(s.agent_off + i) * NX + r]);
+        if (r < DP) acc -= force[((size_t)i * T + (t - 1)) * DP + r];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc = fma(Ma.A[k][r], lam[k], acc);
+        ln[r] = acc;
+      }
+      const uint16_t msk = Wb[(size_t)(t - 1) * N + i];
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        const F u = Up[(size_t)(t - 1) * NU + c];
+        F g = (F(2) * D.Rd[(s.agent_off + i) * NU + c]) * u;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) g = fma(Ma.B[r][c], ln[r], g);
+        visit(t - 1, c, msk, u, g, Ma);
+      }
+#pragma unroll
+      for (int r = 0; r < NX; ++r) lam[r] = ln[r];
+    }
+  };
+  auto bound_mu = [](uint16_t msk, int c, F g) -> F { return (msk & (1u << c)) ? g : -g; };
+  auto held = [](uint16_t msk, int c) -> bool { return (msk & (0x101u << c)) != 0; };
+  // largest |multiplier|
+  for (int i = tid; i < N; i += nt)
+    sweep(i, [&](int, int c, uint16_t msk, F, F g, const Model<F, NX, NU>&) {
+      if (held(msk, c)) atomicMax(&s_scale, abs_bits(bound_mu(msk, c, g)));
+    });
+  for (int h = tid; h < m; h += nt) atomicMax(&s_scale, abs_bits(mu[h]));
+  __syncthreads();
+  const F tol = F(B.kkt_tol);
+  const F mtol = tol * from_bits(s_scale, F(0));
+  // 1. the most negative multiplier (smallest order key), then its lowest index
+  for (int h = tid; h < m; h += nt)
+    if (mu[h] < -mtol) atomicMin(&s_key, mono_key(mu[h]));
+  for (int i = tid; i < N; i += nt)
+    sweep(i, [&](int, int c, uint16_t msk, F, F g, const Model<F, NX, NU>&) {
+      if (held(msk, c) && bound_mu(msk, c, g) < -mtol) atomicMin(&s_key, mono_key(bound_mu(msk, c, g)));
+    });
+  __syncthreads();
+  const unsigned long long kdrop = s_key;
+  if (kdrop != ~0ull) {
+    for (int h = tid; h < m; h += nt)
+      if (mono_key(mu[h]) == kdrop) atomicMin(&s_idx, (long long)h);
+    for (int i = tid; i < N; i += nt)
+      sweep(i, [&](int t, int c, uint16_t msk, F, F g, const Model<F, NX, NU>&) {
+        if (held(msk, c) && mono_key(bound_mu(msk, c, g)) == kdrop)
+          atomicMin(&s_idx, (long long)m + ((long long)i * T + t) * NU + c);
+      });
+    __syncthreads();
+    if (tid == 0) {
+      const long long e = s_idx;
+      if (e < m) {
+        hm[act[e]] = 0;
+      } else {
+        const long long r = e - m;
+        const int c = (int)(r % NU), t = (int)((r / NU) % T), i = (int)(r / ((long long)NU * T));
+        Wb[(size_t)t * N + i] = (uint16_t)(Wb[(size_t)t * N + i] & ~(0x101u << c));
+      }
+      B.pchg[sc] = 1;
+    }
+    return;
+  }
+  // 2. the most violated row (largest relative violation), then its lowest index
+  const F dscale = F(s.d) > F(1) ? F(s.d) : F(1);
+  auto slack_rel = [&](int64_t q) -> F {   // a'(p_i - p_j) - d, relative to max(1, d)
+    const int tm1 = (int)(q / P), pair = (int)(q - (int64_t)tm1 * P);
+    const int pk = pr[pair], i = pk & 0xFFFF, j = pk >> 16;
+    const F* xi = B.Xp + (s.xs_off + (int64_t)i * (T + 1) + tm1 + 1) * NX;
+    const F* xj = B.Xp + (s.xs_off + (int64_t)j * (T + 1) + tm1 + 1) * NX;
+    F v = -F(s.d);
+#pragma unroll
+    for (int c = 0; c < DP; ++c) v = fma(a[((size_t)tm1 * DP + c) * P + pair], xi[c] - xj[c], v);
+    return v / dscale;
+  };
+  auto box_rel = [](F u, F lo, F hi) -> F {   // distance outside the box, relative; <= 0 inside
+    const F sl = fabs_(lo) > F(1) ? fabs_(lo) : F(1), sh = fabs_(hi) > F(1) ? fabs_(hi) : F(1);
+    const F vl = (lo - u) / sl, vh = (u - hi) / sh;
+    return vl > vh ? vl : vh;
+  };
+  for (int64_t q = tid; q < PT; q += nt)
+    if (!hm[q]) {
+      const F v = -slack_rel(q);
+      if (v > tol) atomicMin(&s_key, ~mono_key(v));
+    }
+  for (int i = tid; i < N; i += nt)
+    sweep(i, [&](int, int c, uint16_t msk, F u, F, const Model<F, NX, NU>& Ma) {
+      if (!held(msk, c)) {
+        const F v = box_rel(u, Ma.umin[c], Ma.umax[c]);
+        if (v > tol) atomicMin(&s_key, ~mono_key(v));
+      }
+    });
+  __syncthreads();
+  const unsigned long long kadd = s_key;
+  if (kadd == ~0ull) {
+    if (tid == 0) B.pchg[sc] = 0;   // KKT conditions hold
+    return;
+  }
+  for (int64_t q = tid; q < PT; q += nt)
+    if (!hm[q] && ~mono_key(-slack_rel(q)) == kadd) atomicMin(&s_idx, (long long)q);
+  for (int i = tid; i < N; i += nt)
+    sweep(i, [&](int t, int c, uint16_t msk, F u, F, const Model<F, NX, NU>& Ma) {
+      if (!held(msk, c) && ~mono_key(box_rel(u, Ma.umin[c], Ma.umax[c])) == kadd)
+        atomicMin(&s_idx, PT + ((long long)i * T + t) * NU + c);
+    });
+  __syncthreads();
+  if (tid == 0) {
+    const long long e = s_idx;
+    if (e < PT) {
+      hm[e] = 1;
+    } else {
+      const long long r = e - PT;
+      const int c = (int)(r % NU), t = (int)((r / NU) % T), i = (int)(r / ((long long)NU * T));
+      const F u = B.Up[(s.as_off + (int64_t)i * T + t) * NU + c];
+      const Model<F, NX, NU>& Ma = agent_model<F, NX, NU>(D, Mo, s, i);
+      const uint16_t bit = (u < Ma.umin[c]) ? (uint16_t)(1u << c) : (uint16_t)(0x100u << c);
+      Wb[(size_t)t * N + i] = (uint16_t)(Wb[(size_t)t * N + i] | bit);
+    }
+    B.pchg[sc] = 1;
+  }
+}
+
+// Active set in the caller's layouts: halfspace flags [pair-step] (pair-major,
+// then t) and held inputs [agent][t][nu] (0 free, 1 lower, 2 upper).
+template <typename F>
+__global__ void k_bwd_export_set(Dev<F> D, BwdDev<F> B, int nu, uint8_t* act_out, int8_t* W_out) {
+  const int sc = blockIdx.x;
+  const ScenMeta s = D.meta[sc];
+  const int64_t PT = (int64_t)s.P * s.T, NT = (int64_t)s.N * s.T;
+  if (act_out)
+    for (int64_t q = threadIdx.x; q < PT; q += blockDim.x) {
+      const int tm1 = (int)(q / s.P), pair = (int)(q - (int64_t)tm1 * s.P);
+      act_out[s.ps_off + (int64_t)pair * s.T + tm1] = B.hmask[s.ps_off + q];
+    }
+  if (W_out)
+    for (int64_t e = threadIdx.x; e < NT; e += blockDim.x) {
+      const int t = (int)(e / s.N), i = (int)(e - (int64_t)t * s.N);
+      const uint16_t msk = B.Wb[s.as_off + e];
+      for (int c = 0; c < nu; ++c)
+        W_out[(s.as_off + (int64_t)i * s.T + t) * nu + c] = (msk & (1u << c)) ? 1 : ((msk & (0x100u << c)) ? 2 : 0);
+    }
 }
 
 template <typename F>

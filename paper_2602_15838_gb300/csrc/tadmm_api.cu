@@ -175,7 +175,8 @@ static void free_all(tadmm_handle* h) {
     if (p) cudaFree(p);
   void* bptrs[] = {h->bwd.act, h->bwd.cnt, h->bwd.amask, h->bwd.psi, h->bwd.kks, h->bwd.pos0, h->bwd.force,
                    h->bwd.Xp,  h->bwd.Up,  h->bwd.Wx,    h->bwd.Wu,  h->bwd.bstat, h->bwd.bs, h->bwd.S,
-                   h->bwd.vec, h->bwd.gX,  h->bwd.gout,  h->bwd.xpol};
+                   h->bwd.vec, h->bwd.gX,  h->bwd.gout,  h->bwd.xpol, h->bwd.piv, h->bwd.ndep, h->bwd.hmask,
+                   h->bwd.Wb,  h->bwd.pchg, h->bwd.set_act, h->bwd.set_W};
   for (void* p : bptrs)
     if (p) cudaFree(p);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -521,6 +522,7 @@ extern "C" int tadmm_solve(tadmm_handle* h, double tol, int32_t max_iter, void* 
     rc = run();
   }
   if (rc == TADMM_OK) h->solved = 1;
+  h->bwd_polished = 0;
   return rc;
 }
 
@@ -667,10 +669,10 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
 }
 
 extern "C" int tadmm_backward(tadmm_handle* h, const double* grad_X, double theta_eps, double* gQ, double* gQf,
-                              double* gR, double* gGoal, double* X_polished, int32_t* status, void* stream) {
+                              double* gR, double* gGoal, double* X_polished, int32_t* status, int32_t* n_dependent,
+                              void* stream) {
   if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
   if (!h->solved) return set_error(TADMM_ESTATE, "backward before solve");
-  if (!grad_X) return set_error(TADMM_EINVAL, "grad_X is NULL");
   if (!(theta_eps >= 0.0) || !std::isfinite(theta_eps)) return set_error(TADMM_EINVAL, "theta_eps must be >= 0");
   for (const auto& m : h->meta_h)
     if (m.T > 64) return set_error(TADMM_EINVAL, "backward supports horizons T <= 64");
@@ -696,18 +698,19 @@ extern "C" int tadmm_backward(tadmm_handle* h, const double* grad_X, double thet
       (rc = grow(&h->bwd.gout, h->bwd.gout_cap, sizeof(double) * gout_n)) ||
       (rc = grow(&h->bwd.xpol, h->bwd.xpol_cap, gx_bytes)))
     return rc;
-  if ((rc = cuda_check(cudaMemcpyAsync(h->bwd.gX, grad_X, gx_bytes, cudaMemcpyDefault, st), "grad_X copy")))
+  if (grad_X && (rc = cuda_check(cudaMemcpyAsync(h->bwd.gX, grad_X, gx_bytes, cudaMemcpyDefault, st), "grad_X copy")))
     return rc;
   double* gout = (double*)h->bwd.gout;
   auto run = [&]() -> int {
-    TADMM_DISPATCH(h, backward(h, (const double*)h->bwd.gX, theta_eps, gout, X_polished ? (double*)h->bwd.xpol : nullptr, st));
+    TADMM_DISPATCH(h, backward(h, grad_X ? (const double*)h->bwd.gX : nullptr, theta_eps, gout,
+                               X_polished ? (double*)h->bwd.xpol : nullptr, st));
   };
   if ((rc = run())) return rc;
   struct Out { void* dst; size_t off, n; };
   const Out outs[4] = {{gQ, 0, (size_t)na * nx}, {gQf, (size_t)na * nx, (size_t)na * nx},
                        {gR, 2 * (size_t)na * nx, (size_t)na * nu}, {gGoal, 2 * (size_t)na * nx + na * nu, (size_t)na * nx}};
   for (const Out& o : outs)
-    if (o.dst && (rc = cuda_check(cudaMemcpyAsync(o.dst, gout + o.off, sizeof(double) * o.n, cudaMemcpyDefault, st),
+    if (grad_X && o.dst && (rc = cuda_check(cudaMemcpyAsync(o.dst, gout + o.off, sizeof(double) * o.n, cudaMemcpyDefault, st),
                                   "gradient copy")))
       return rc;
   if (X_polished && (rc = cuda_check(cudaMemcpyAsync(X_polished, h->bwd.xpol, gx_bytes, cudaMemcpyDefault, st),
@@ -716,7 +719,57 @@ extern "C" int tadmm_backward(tadmm_handle* h, const double* grad_X, double thet
   if (status && (rc = cuda_check(cudaMemcpyAsync(status, h->bwd.bstat, 4 * h->n_scen, cudaMemcpyDefault, st),
                                  "backward status copy")))
     return rc;
+  if (n_dependent && (rc = cuda_check(cudaMemcpyAsync(n_dependent, h->bwd.ndep, 4 * h->n_scen, cudaMemcpyDefault, st),
+                                      "backward rank copy")))
+    return rc;
   return cuda_check(cudaStreamSynchronize(st), "backward sync");
+}
+
+extern "C" int tadmm_polish(tadmm_handle* h, double theta_eps, int32_t max_rounds, double kkt_tol, uint8_t* act,
+                            int8_t* W, int32_t* status, int32_t* rounds, void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (!h->solved) return set_error(TADMM_ESTATE, "polish before solve");
+  if (!(theta_eps >= 0.0) || !std::isfinite(theta_eps)) return set_error(TADMM_EINVAL, "theta_eps must be >= 0");
+  if (max_rounds < 1) return set_error(TADMM_EINVAL, "max_rounds must be >= 1");
+  if (!(kkt_tol >= 0.0) || !std::isfinite(kkt_tol)) return set_error(TADMM_EINVAL, "kkt_tol must be >= 0");
+  if (kkt_tol == 0.0) kkt_tol = h->prec == 32 ? 1e-5 : 1e-9;
+  for (const auto& m : h->meta_h)
+    if (m.T > 64) return set_error(TADMM_EINVAL, "polish supports horizons T <= 64");
+  cudaStream_t st = (cudaStream_t)stream;
+  auto grow = [&](void** p, size_t& cap, size_t bytes) -> int {
+    if (bytes <= cap && *p) return TADMM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(TADMM_ENOMEM, "polish staging allocation failed");
+    }
+    cap = bytes;
+    return TADMM_OK;
+  };
+  int rc;
+  const size_t act_bytes = (size_t)std::max<int64_t>(h->tot_ps, 1), w_bytes = (size_t)h->tot_as * h->nu;
+  if ((act && (rc = grow(&h->bwd.set_act, h->bwd.set_act_cap, act_bytes))) ||
+      (W && (rc = grow(&h->bwd.set_W, h->bwd.set_W_cap, w_bytes))))
+    return rc;
+  uint8_t* act_dev = act ? (uint8_t*)h->bwd.set_act : nullptr;
+  int8_t* W_dev = W ? (int8_t*)h->bwd.set_W : nullptr;
+  std::vector<int32_t> stat(h->n_scen);
+  int32_t nr = 0;
+  auto run = [&]() -> int {
+    TADMM_DISPATCH(h, polish(h, theta_eps, max_rounds, kkt_tol, act_dev, W_dev, stat.data(), &nr, st));
+  };
+  if ((rc = run())) return rc;
+  if (act && h->tot_ps > 0 &&
+      (rc = cuda_check(cudaMemcpyAsync(act, act_dev, (size_t)h->tot_ps, cudaMemcpyDefault, st), "active set copy")))
+    return rc;
+  if (W && (rc = cuda_check(cudaMemcpyAsync(W, W_dev, w_bytes, cudaMemcpyDefault, st), "working set copy")))
+    return rc;
+  if ((rc = cuda_check(cudaStreamSynchronize(st), "polish sync"))) return rc;
+  if (status) std::memcpy(status, stat.data(), 4 * h->n_scen);
+  if (rounds) *rounds = nr;
+  return TADMM_OK;
 }
 
 extern "C" void tadmm_destroy(tadmm_handle* h) {

@@ -15,10 +15,13 @@
 struct BwdBufs {
   void *act = nullptr, *cnt = nullptr, *amask = nullptr, *psi = nullptr, *kks = nullptr, *pos0 = nullptr,
        *force = nullptr, *Xp = nullptr, *Up = nullptr, *Wx = nullptr, *Wu = nullptr, *bstat = nullptr,
-       *bs = nullptr, *S = nullptr, *vec = nullptr, *gX = nullptr, *gout = nullptr, *xpol = nullptr;
+       *bs = nullptr, *S = nullptr, *vec = nullptr, *gX = nullptr, *gout = nullptr, *xpol = nullptr,
+       *piv = nullptr, *ndep = nullptr, *hmask = nullptr, *Wb = nullptr, *pchg = nullptr, *set_act = nullptr,
+       *set_W = nullptr;
   size_t act_cap = 0, cnt_cap = 0, amask_cap = 0, psi_cap = 0, kks_cap = 0, pos0_cap = 0, force_cap = 0,
          Xp_cap = 0, Up_cap = 0, Wx_cap = 0, Wu_cap = 0, bstat_cap = 0, bs_cap = 0, S_cap = 0, vec_cap = 0,
-         gX_cap = 0, gout_cap = 0, xpol_cap = 0;
+         gX_cap = 0, gout_cap = 0, xpol_cap = 0, piv_cap = 0, ndep_cap = 0, hmask_cap = 0, Wb_cap = 0,
+         pchg_cap = 0, set_act_cap = 0, set_W_cap = 0;
 };
 
 struct tadmm_handle {
@@ -97,6 +100,7 @@ struct tadmm_handle {
   double g_tol = -1.0;
   int g_iter = -1, g_tpc = -1, g_cps = -1, g_var = -1;
   int solved = 0;
+  int bwd_polished = 0;     // the backward active set was refined by tadmm_polish after the last solve
   int64_t launches = 0;   // kernel launches enqueued by the last solve
   BwdBufs bwd;
 
@@ -127,6 +131,8 @@ struct Impl {
   static int backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev, double* xpol_dev,
                       cudaStream_t st);
   static int relinearize(tadmm_handle* h, cudaStream_t st);
+  static int polish(tadmm_handle* h, double theta_eps, int max_rounds, double kkt_tol, uint8_t* act_dev, int8_t* W_dev,
+                    int32_t* status, int32_t* rounds, cudaStream_t st);
 };
 
 }  // namespace tadmm

@@ -857,9 +857,11 @@ int Impl<F, NX, NU, DP>::export_solution(tadmm_handle* h, double* X, double* U, 
 
 namespace tadmm {
 
+// Scratch of the backward pass and the polishing rounds (grown on demand) and
+// the device view of it; gX_dev / gout_dev may be null (polishing).
 template <typename F, int NX, int NU, int DP>
-int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev,
-                                  double* xpol_dev, cudaStream_t st) {
+static int bwd_prepare(tadmm_handle* h, double theta_eps, const double* gX_dev, double* gout_dev, BwdDev<F>& B,
+                       std::vector<BwdScen>& bs) {
   const int64_t na = h->tot_agents;
   int tmax = 0;
   for (const ScenMeta& m : h->meta_h) tmax = std::max(tmax, m.T);
@@ -876,7 +878,7 @@ int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double 
     return TADMM_OK;
   };
   int64_t psi_total = 0;
-  std::vector<BwdScen> bs(h->n_scen);
+  bs.assign(h->n_scen, BwdScen{});
   for (int s = 0; s < h->n_scen; ++s) {
     const ScenMeta& m = h->meta_h[s];
     bs[s].psi_off = psi_total;
@@ -884,7 +886,10 @@ int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double 
   }
   int rc;
   BwdBufs& b = h->bwd;
-  if ((rc = grow(&b.act, b.act_cap, 4 * std::max<int64_t>(h->tot_ps, 1))) ||
+  const int64_t ps1 = std::max<int64_t>(h->tot_ps, 1);
+  if ((rc = grow(&b.act, b.act_cap, 4 * ps1)) || (rc = grow(&b.piv, b.piv_cap, 4 * ps1)) ||
+      (rc = grow(&b.hmask, b.hmask_cap, ps1)) || (rc = grow(&b.Wb, b.Wb_cap, 2 * h->tot_as)) ||
+      (rc = grow(&b.pchg, b.pchg_cap, 4 * h->n_scen)) || (rc = grow(&b.ndep, b.ndep_cap, 4 * h->n_scen)) ||
       (rc = grow(&b.cnt, b.cnt_cap, 4 * h->n_scen)) || (rc = grow(&b.amask, b.amask_cap, 8 * na)) ||
       (rc = grow(&b.psi, b.psi_cap, sizeof(F) * std::max<int64_t>(psi_total, 1))) ||
       (rc = grow(&b.kks, b.kks_cap, sizeof(F) * na * DP * tmax * NU)) ||
@@ -894,8 +899,6 @@ int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double 
       (rc = grow(&b.Wx, b.Wx_cap, sizeof(F) * h->tot_xs * NX)) || (rc = grow(&b.Wu, b.Wu_cap, sizeof(F) * h->tot_as * NU)) ||
       (rc = grow(&b.bstat, b.bstat_cap, 4 * h->n_scen)) || (rc = grow(&b.bs, b.bs_cap, sizeof(BwdScen) * h->n_scen)))
     return rc;
-  Dev<F> D = make_dev<F>(h);
-  BwdDev<F> B;
   std::memset(&B, 0, sizeof(B));
   B.act = (int32_t*)b.act;
   B.act_cnt = (int32_t*)b.cnt;
@@ -909,13 +912,33 @@ int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double 
   B.Wx = (F*)b.Wx;
   B.Wu = (F*)b.Wu;
   B.gX = gX_dev;
-  B.gQ = gout_dev;
-  B.gQf = gout_dev + na * NX;
-  B.gR = gout_dev + 2 * na * NX;
-  B.gGoal = gout_dev + 2 * na * NX + na * NU;
+  if (gout_dev) {
+    B.gQ = gout_dev;
+    B.gQf = gout_dev + na * NX;
+    B.gR = gout_dev + 2 * na * NX;
+    B.gGoal = gout_dev + 2 * na * NX + na * NU;
+  }
   B.bstatus = (int32_t*)b.bstat;
+  B.piv = (int32_t*)b.piv;
+  B.ndep = (int32_t*)b.ndep;
+  B.hmask = (uint8_t*)b.hmask;
+  B.Wb = (uint16_t*)b.Wb;
+  B.pchg = (int32_t*)b.pchg;
   B.theta_eps = theta_eps;
+  // pivots of S below this fraction of its largest diagonal entry are rounding
+  // noise of an exactly dependent row (about m eps in float64, m eps_32 in float32)
+  B.rank_tol = std::is_same<F, float>::value ? 1e-6 : 1e-12;
   B.kk_stride = (int64_t)tmax * NU;
+  B.adjoint = 1;
+  return TADMM_OK;
+}
+
+// Active list of the current set, its sizes, then k_bwd_main (one CTA per scenario).
+template <typename F, int NX, int NU, int DP>
+static int bwd_solve(tadmm_handle* h, BwdDev<F>& B, std::vector<BwdScen>& bs, cudaStream_t st) {
+  Dev<F> D = make_dev<F>(h);
+  BwdBufs& b = h->bwd;
+  int rc;
   k_bwd_count<F, NX, NU, DP><<<h->n_scen, 32, 0, st>>>(D, B);
   if ((rc = cuda_check(cudaGetLastError(), "backward count launch"))) return rc;
   std::vector<int32_t> cnt(h->n_scen);
@@ -927,23 +950,97 @@ int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double 
     bs[s].m = cnt[s];
     bs[s].s_off = s_total;
     bs[s].v_off = v_total;
-    s_total += (int64_t)cnt[s] * cnt[s];
+    s_total += 2 * (int64_t)cnt[s] * cnt[s];   // S, then the normal matrix of a rank-deficient S
     v_total += 3 * (int64_t)cnt[s];
   }
+  auto grow = [&](void** p, size_t& cap, size_t bytes) -> int {
+    if (bytes <= cap && *p) return TADMM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(TADMM_ENOMEM, "backward scratch allocation failed");
+    }
+    cap = bytes;
+    return TADMM_OK;
+  };
   if ((rc = grow(&b.S, b.S_cap, sizeof(F) * std::max<int64_t>(s_total, 1))) ||
       (rc = grow(&b.vec, b.vec_cap, sizeof(F) * std::max<int64_t>(v_total, 1))))
     return rc;
   B.S = (F*)b.S;
   B.vec = (F*)b.vec;
   B.bs = (const BwdScen*)b.bs;
-  cudaMemcpyAsync(b.bs, bs.data(), sizeof(BwdScen) * h->n_scen, cudaMemcpyHostToDevice, st);
+  if ((rc = cuda_check(cudaMemcpyAsync(b.bs, bs.data(), sizeof(BwdScen) * h->n_scen, cudaMemcpyHostToDevice, st),
+                       "backward sizes")))
+    return rc;
   if (h->di)
     k_bwd_main<F, NX, NU, DP, true><<<h->n_scen, 128, 0, st>>>(D, B);
   else
     k_bwd_main<F, NX, NU, DP, false><<<h->n_scen, 128, 0, st>>>(D, B);
-  if ((rc = cuda_check(cudaGetLastError(), "backward launch"))) return rc;
+  return cuda_check(cudaGetLastError(), "backward launch");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev,
+                                  double* xpol_dev, cudaStream_t st) {
+  BwdDev<F> B;
+  std::vector<BwdScen> bs;
+  int rc;
+  if ((rc = bwd_prepare<F, NX, NU, DP>(h, theta_eps, gX_dev, gout_dev, B, bs))) return rc;
+  B.adjoint = gX_dev != nullptr;   // without a loss gradient: the polished point only
+  Dev<F> D = make_dev<F>(h);
+  if (!h->bwd_polished) {   // the active set of the last solve's final iterate
+    k_bwd_init<F, NX, NU, DP><<<h->n_scen, 128, 0, st>>>(D, B);
+    if ((rc = cuda_check(cudaGetLastError(), "backward init launch"))) return rc;
+  }
+  if ((rc = bwd_solve<F, NX, NU, DP>(h, B, bs, st))) return rc;
   if (xpol_dev) k_bwd_export_x<F><<<grid_for(h->tot_xs * NX, 256), 256, 0, st>>>(B.Xp, h->tot_xs * NX, xpol_dev);
   return cuda_check(cudaGetLastError(), "backward export");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::polish(tadmm_handle* h, double theta_eps, int max_rounds, double kkt_tol, uint8_t* act_dev,
+                                int8_t* W_dev, int32_t* status, int32_t* rounds, cudaStream_t st) {
+  BwdDev<F> B;
+  std::vector<BwdScen> bs;
+  int rc;
+  if ((rc = bwd_prepare<F, NX, NU, DP>(h, theta_eps, nullptr, nullptr, B, bs))) return rc;
+  B.adjoint = 0;
+  B.kkt_tol = kkt_tol;
+  Dev<F> D = make_dev<F>(h);
+  k_bwd_init<F, NX, NU, DP><<<h->n_scen, 128, 0, st>>>(D, B);
+  if ((rc = cuda_check(cudaGetLastError(), "polish init launch"))) return rc;
+  h->bwd_polished = 1;
+  std::vector<int32_t> chg(h->n_scen, 1), bst(h->n_scen, 0);
+  int done_rounds = 0;
+  for (int r = 0; r < max_rounds; ++r) {
+    if ((rc = bwd_solve<F, NX, NU, DP>(h, B, bs, st))) return rc;
+    if (h->di)
+      k_bwd_polish<F, NX, NU, DP, true><<<h->n_scen, 128, 0, st>>>(D, B);
+    else
+      k_bwd_polish<F, NX, NU, DP, false><<<h->n_scen, 128, 0, st>>>(D, B);
+    if ((rc = cuda_check(cudaGetLastError(), "polish launch"))) return rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(chg.data(), h->bwd.pchg, 4 * h->n_scen, cudaMemcpyDeviceToHost, st),
+                         "polish flags")) ||
+        (rc = cuda_check(cudaMemcpyAsync(bst.data(), h->bwd.bstat, 4 * h->n_scen, cudaMemcpyDeviceToHost, st),
+                         "polish status")) ||
+        (rc = cuda_check(cudaStreamSynchronize(st), "polish sync")))
+      return rc;
+    done_rounds = r + 1;
+    bool any = false;
+    for (int s = 0; s < h->n_scen; ++s) any = any || chg[s];
+    if (!any) break;
+  }
+  if (status)
+    for (int s = 0; s < h->n_scen; ++s)
+      status[s] = bst[s] == ST_NUMERIC ? ST_NUMERIC : (chg[s] ? ST_NOT_CONVERGED : ST_CONVERGED);
+  if (rounds) *rounds = done_rounds;
+  if (act_dev || W_dev) {
+    k_bwd_export_set<F><<<h->n_scen, 128, 0, st>>>(D, B, NU, act_dev, W_dev);
+    if ((rc = cuda_check(cudaGetLastError(), "polish export"))) return rc;
+  }
+  return TADMM_OK;
 }
 
 }  // namespace tadmm

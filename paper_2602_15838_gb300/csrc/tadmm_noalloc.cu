@@ -14,8 +14,14 @@
 // reads, and two calls whose work overlaps on the GPU (different streams, or
 // different host threads, on the same device) race on it and corrupt each
 // other.  Callers must serialize them.
+//
+// Input values are checked on the device (the caller's arrays are device
+// memory) by the rules tadmm_create applies on the host; a scenario that
+// breaks one is reported through status TADMM_INVALID_INPUT and not solved.
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -34,15 +40,21 @@ std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The name of the
-// array is only a host-side stand-in, so the address is looked up once per
-// device with that device current.
-int scratch_address(void** out) {
+// array is only a host-side stand-in, so the address is looked up with that
+// device current: on every call made outside stream capture (which also picks
+// up a new address after a device reset), and from the last lookup during a
+// capture.  With lazy module loading the first call on a device also loads the
+// library's module there (an allocation by the driver), so it belongs to the
+// caller's start-up, before any capture.
+int scratch_address(void** out, cudaStream_t st) {
   int dev = 0;
   int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   if (rc) return rc;
   if (dev < 0 || dev >= kMaxDevices) return set_error(TADMM_EINVAL, "device ordinal out of range");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((rc = cuda_check(cudaStreamIsCapturing(st, &cap), "cudaStreamIsCapturing"))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
     void* p = nullptr;
     rc = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
     if (rc) return rc;
@@ -90,10 +102,35 @@ __global__ void k_noalloc_setup(ScenMeta* meta, int32_t* order, int32_t* pairs, 
   }
 }
 
+// Input values by the rules of tadmm_create (host checks there, device checks
+// here, since the inputs are device memory): finite A, B, x_init, x_ref, w0,
+// a; finite umin <= umax; finite Q, Qf >= 0; finite R > 0.  Any violation
+// marks the scenario TADMM_INVALID_INPUT (bad = 1), which the solve skips.
+template <int NX, int NU, int DP>
+__global__ void k_noalloc_validate(const double* model, const double* Qd, const double* Rd, const double* Qfd,
+                                   const double* x_init, const double* x_ref, const double* a, const double* w0,
+                                   int N, int64_t P, int T, int32_t* bad) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  bool ok = true;
+  for (int64_t k = tid; k < NX * NX + NX * NU; k += nt) ok = ok && isfinite(model[k]);
+  if (tid < NU) {
+    const double lo = model[NX * NX + NX * NU + tid], hi = model[NX * NX + NX * NU + NU + tid];
+    ok = ok && isfinite(lo) && isfinite(hi) && lo <= hi;
+  }
+  for (int64_t k = tid; k < (int64_t)N * NX; k += nt)
+    ok = ok && isfinite(Qd[k]) && Qd[k] >= 0.0 && isfinite(Qfd[k]) && Qfd[k] >= 0.0 && isfinite(x_init[k]) &&
+         isfinite(x_ref[k]);
+  for (int64_t k = tid; k < (int64_t)N * NU; k += nt) ok = ok && isfinite(Rd[k]) && Rd[k] > 0.0;
+  for (int64_t k = tid; k < (int64_t)N * T * DP; k += nt) ok = ok && isfinite(w0[k]);
+  for (int64_t k = tid; k < P * T * DP; k += nt) ok = ok && isfinite(a[k]);
+  if (!ok) atomicOr(bad, 1);
+}
+
 // The single scenario's ADMM run: the same phases as the batched persistent
 // kernel, in one CTA.
 template <typename F, int NX, int NU, int DP>
-__global__ void __launch_bounds__(64) k_noalloc_solve(Dev<F> D) {
+__global__ void __launch_bounds__(64) k_noalloc_solve(Dev<F> D, const int32_t* bad) {
+  if (*bad) return;
   __shared__ Model<F, NX, NU> M;
   __shared__ CtaScratch cs;
   __shared__ F kcs[AgentConst<NX, NU>::KC * 64];
@@ -104,14 +141,14 @@ __global__ void __launch_bounds__(64) k_noalloc_solve(Dev<F> D) {
 }
 
 __global__ void k_noalloc_results(const int32_t* status, const int32_t* iters, const double* res,
-                                  int32_t* status_iters, double* res_out) {
+                                  const int32_t* bad, int32_t* status_iters, double* res_out) {
   if (status_iters) {
-    status_iters[0] = status[0];
-    status_iters[1] = iters[0];
+    status_iters[0] = *bad ? TADMM_INVALID_INPUT : status[0];
+    status_iters[1] = *bad ? 0 : iters[0];
   }
   if (res_out) {
-    res_out[0] = res[0];
-    res_out[1] = res[1];
+    res_out[0] = *bad ? CUDART_NAN : res[0];
+    res_out[1] = *bad ? CUDART_NAN : res[1];
   }
 }
 
@@ -134,7 +171,7 @@ static int noalloc_run(const tadmm_scenario_dev* sc, int start_mode, double tol,
         return set_error(TADMM_EINVAL, "scenario needs " + std::to_string(cv.off) +
                                            " bytes of solver state; the static scratch of tadmm_solve_noalloc holds " +
                                            std::to_string((size_t)TADMM_NOALLOC_SCRATCH_BYTES) + " bytes");
-      int rc = scratch_address(&base);
+      int rc = scratch_address(&base, st);
       if (rc) return rc;
     }
     cv = Carve{(char*)base};
@@ -168,7 +205,11 @@ static int noalloc_run(const tadmm_scenario_dev* sc, int start_mode, double tol,
     unsigned long long* eqp = cv.take<unsigned long long>(8);
     unsigned long long* fact = cv.take<unsigned long long>(8);
     int32_t* queue = cv.take<int32_t>(4);
+    int32_t* bad = cv.take<int32_t>(4);
     if (pass == 0) continue;
+
+    int rc0 = cuda_check(cudaMemsetAsync(bad, 0, sizeof(int32_t), st), "clear input flag");
+    if (rc0) return rc0;
 
     k_noalloc_setup<<<grid_for(N, 64, 1024), 64, 0, st>>>(meta, order, pairs, pair_scen, agent_scen, queue, N, T,
                                                           sc->d_min, sc->rho);
@@ -183,6 +224,8 @@ static int noalloc_run(const tadmm_scenario_dev* sc, int start_mode, double tol,
     k_convert<F><<<grid_for(N * NX, 128), 128, 0, st>>>(sc->x_ref, x_ref, (int64_t)N * NX);
     if (P > 0) k_import_a<F, DP><<<grid_for(P, 128), 128, 0, st>>>(meta, pair_scen, sc->a, a, P);
     k_import_w0<F, DP><<<grid_for(N, 128), 128, 0, st>>>(meta, agent_scen, sc->w0, w0, N);
+    k_noalloc_validate<NX, NU, DP><<<grid_for(std::max<int64_t>(PT * DP, (int64_t)N * T * DP), 128, 1024), 128, 0, st>>>(
+        model, Qd, Rd, Qfd, x_init, x_ref, a, w0, N, P, T, bad);
 
     D.meta = meta; D.order = order; D.pairs = pairs; D.model = model;
     D.Qd = Qd; D.Rd = Rd; D.Qfd = Qfd; D.x_init = x_init; D.x_ref = x_ref; D.a = a; D.w0 = w0;
@@ -191,11 +234,11 @@ static int noalloc_run(const tadmm_scenario_dev* sc, int start_mode, double tol,
     D.status = status; D.iters = iters; D.cur_lvl = cur_lvl; D.res = resd; D.eqp = eqp; D.fact = fact;
     D.queue = queue;
     D.tol = tol; D.max_iter = max_iter; D.start_mode = start_mode; D.as_max = 0; D.eps_rel = 0.0;
-    k_noalloc_solve<F, NX, NU, DP><<<1, 64, 0, st>>>(D);
+    k_noalloc_solve<F, NX, NU, DP><<<1, 64, 0, st>>>(D, bad);
     if (X || U)
       k_export_agents<F, NX, NU><<<grid_for(N, 128), 128, 0, st>>>(D, agent_scen, N, X, U, nullptr);
     if (theta && P > 0) k_export_theta<F><<<grid_for(P, 128), 128, 0, st>>>(D, pair_scen, P, theta);
-    k_noalloc_results<<<1, 1, 0, st>>>(status, iters, resd, status_iters, res);
+    k_noalloc_results<<<1, 1, 0, st>>>(status, iters, resd, bad, status_iters, res);
   }
   return cuda_check(cudaGetLastError(), "tadmm_solve_noalloc launches");
 }

@@ -4,8 +4,8 @@ Tolerances (FP64): every ADMM iterate within 1e-9 relative
 (|gpu - oracle|_inf / max(1, |oracle|_inf)) on X, U and theta at equal
 iteration count; final working sets equal except degenerate entries (a bound
 multiplier within 1e-7 of zero, or a free input within 1e-9 of its bound).
-FP32 runs are stated against the FP64 oracle with 1e-4 relative on positions
-and inputs after a fixed number of iterations.
+FP32 runs are stated against the FP64 oracle with 1e-4 relative on every state
+(positions and velocities) and input after the same number of iterations.
 """
 import numpy as np
 import pytest
@@ -163,12 +163,19 @@ def test_swarm3d_reduced_fp64(tg):
     assert rel(g[0]["U"], o["U"]) <= 1e-9
 
 
-def test_ring14_fp32_against_fp64_oracle(tg):
+@pytest.mark.parametrize("k", [2, 10, 100])
+def test_ring14_fp32_against_fp64_oracle(tg, k):
+    """Float32 iterates of the 14-agent ring after k iterations against the
+    float64 oracle: every state and input within 1e-4 relative.  (Measured on a
+    GB300: states <= 2.5e-6, inputs <= 7.4e-5 up to 1000 iterations; after the
+    first iteration a degenerate working-set entry can flip in float32, which
+    moves one input by 3.3e-4, so k starts at 2.)"""
     b = make_workload("ring14")
-    g, _ = gpu_run(tg, b, 0.0, 10, precision=32)
-    o = oracle.admm(b, 0, tol=0.0, max_iter=10, nthreads=8)
-    assert rel(g[0]["X"], o["X"]) <= 1e-4
-    assert rel(g[0]["U"], o["U"]) <= 1e-3
+    g, _ = gpu_run(tg, b, 0.0, k, precision=32)
+    o = oracle.admm(b, 0, tol=0.0, max_iter=k, nthreads=8)
+    assert rel(g[0]["X"][:, :, :2], o["X"][:, :, :2]) <= 1e-4
+    assert rel(g[0]["X"][:, :, 2:], o["X"][:, :, 2:]) <= 1e-4
+    assert rel(g[0]["U"], o["U"]) <= 1e-4
 
 
 def test_literal_infeasible_not_converged(tg):
@@ -336,17 +343,21 @@ def test_double_float_mixed_batch_sampled(tg):
 
 
 def test_fp32_converged_solutions_against_fp64_oracle(tg):
-    """Float32 runs that reach tol 1e-4: converged positions and inputs within
-    1e-4 relative of the float64 oracle after the same number of iterations."""
+    """Float32 runs that reach tol 1e-4 on 512 mixed scenarios: every converged
+    scenario with N <= 12 (plus the 478-iteration one) against the float64
+    oracle run to the same iteration: positions, velocities and inputs each
+    within 1e-4 relative.  (Measured on a GB300 over all 20 scenarios that
+    converge in both precisions: positions <= 1.3e-6, velocities <= 2.4e-6,
+    inputs <= 2.3e-5.)"""
     b = make_workload("mixed", n_scen=512)
-    g, _ = gpu_run(tg, b, 1e-4, 200, precision=32)
-    done = [k for k in range(b.n_scen) if g[k]["status"] == tg.CONVERGED and g[k]["iters"] > 1]
-    done = sorted(done, key=lambda k: int(b.N[k]) * g[k]["iters"])[:4]
-    assert len(done) >= 2
+    g, _ = gpu_run(tg, b, 1e-4, 500, precision=32)
+    done = [k for k in range(b.n_scen) if g[k]["status"] == tg.CONVERGED and (int(b.N[k]) <= 12 or k == 107)]
+    assert len(done) >= 8 and 107 in done
     for k in done:
-        o = oracle.admm(b, k, tol=0.0, max_iter=g[k]["iters"])
+        o = oracle.admm(b, k, tol=0.0, max_iter=g[k]["iters"], nthreads=8)
         assert rel(g[k]["X"][:, :, :2], o["X"][:, :, :2]) <= 1e-4, k
-        assert rel(g[k]["U"], o["U"]) <= 1e-3, k
+        assert rel(g[k]["X"][:, :, 2:], o["X"][:, :, 2:]) <= 1e-4, k
+        assert rel(g[k]["U"], o["U"]) <= 1e-4, k
 
 
 def test_largest_mixed_batch_scenarios_fp64(tg):
@@ -581,3 +592,63 @@ def test_sparse_coupling_matches_oracle(tg):
             assert g0[k]["iters"] == g1[k]["iters"] and g0[k]["status"] == g1[k]["status"], (mode, k)
             assert np.array_equal(g0[k]["X"], g1[k]["X"]), (mode, k)
             assert np.array_equal(g0[k]["theta"], g1[k]["theta"]), (mode, k)
+
+
+def test_autotune_shape_and_candidate_shapes_bitwise_equal(tg):
+    """tadmm_autotune on a ragged batch that mixes grouped small scenarios with a
+    lone 40-agent scenario returns a shape from its candidate set (threads per
+    CTA 32/64/128 with register variant 0, 32 with variant 1, 64 with variant 2;
+    resident CTAs per SM >= 1), and every candidate shape, at the occupancy
+    limit and at 2 CTAs per SM, gives bitwise the same iterates, working sets,
+    statuses, residuals and work counters."""
+    small = make_workload("mixed", n_scen=40, first=300)
+    big = random_scenario(seed=91, N=40, T=24, box=5.0)
+    parts = []
+    for bb in (small, big):
+        for k in range(bb.n_scen):
+            s = bb.scenario(k)
+            parts.append(dict(N=int(s.N[0]), T=int(s.T[0]), x_init=s.x_init, x_ref=s.x_ref, a=s.a, w0=s.w0,
+                              d=float(s.d_min[0]), rho=float(s.rho[0]), umax=1.0, c=None))
+    b = make_batch(parts, dp=2, dt=0.1, umax=1.0)
+    cands = [(32, 0), (64, 0), (128, 0), (32, 1), (64, 2)]
+    s = tg.Solver(b)
+    t, c, v = s.autotune(probe_iter=5)
+    s.close()
+    assert (t, v) in cands and c >= 1
+
+    def run(tpc, var, cps):
+        sv = tg.Solver(b, threads_per_cta=tpc, kernel_variant=var, ctas_per_sm=cps)
+        sv.solve(1e-4, 60)
+        out = sv.split(sv.solution())
+        cnt = sv.counters()
+        sv.close()
+        return out, cnt
+
+    ref, cref = run(32, 0, 0)
+    assert max(int(n) for n in b.N) == 40
+    for tpc, var in cands:
+        for cps in (0, 2):
+            g, cg = run(tpc, var, cps)
+            for k in range(b.n_scen):
+                assert g[k]["status"] == ref[k]["status"] and g[k]["iters"] == ref[k]["iters"], (tpc, var, cps, k)
+                assert np.array_equal(g[k]["X"], ref[k]["X"]), (tpc, var, cps, k)
+                assert np.array_equal(g[k]["theta"], ref[k]["theta"]), (tpc, var, cps, k)
+                assert np.array_equal(g[k]["W"], ref[k]["W"]), (tpc, var, cps, k)
+                assert g[k]["r"] == ref[k]["r"] and g[k]["s"] == ref[k]["s"], (tpc, var, cps, k)
+            for key in ("eqp", "fact", "pairsteps"):
+                assert np.array_equal(cg[key], cref[key]), (tpc, var, cps, key)
+
+
+def test_bench_workload_statistics(tg):
+    """The 4096-scenario mixed batch at tol 1e-4, 500 iterations: the number of
+    converged scenarios and of scenario-iterations that bench.py's reference arm
+    uses to express the oracle's throughput in solves/s (the GPU and the oracle
+    take the same iterates, so these are properties of the instances)."""
+    import bench
+    b = make_workload("mixed")
+    s = tg.Solver(b)
+    s.solve(1e-4, 500)
+    sol = s.solution()
+    s.close()
+    assert int((sol["status"] == tg.CONVERGED).sum()) == bench.WORKLOAD_SOLVES
+    assert int(sol["iters"].sum()) == bench.WORKLOAD_SCEN_ITERS
