@@ -668,13 +668,16 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
 }
 
 // Agents per warp of the per-phase x-update kernels: 32 (one per lane) when
-// there are enough agents to give every SM a few warps; otherwise fewer, down
-// to one per lane group of the cooperative refactorization, so that a small
-// agent count is spread over more SMs and every owner can have a lane group.
+// there are enough agents to give every SM at least four warps, otherwise
+// fewer, down to one.  Each of an SM's four sub-partitions issues FP64
+// instructions at its own fixed rate whatever the number of active lanes, so a
+// small agent count (one large scenario) is spread over four warps per SM, one
+// per sub-partition, rather than packed into fewer warps; an agent alone in
+// its warp still takes its EQP passes and refactorizations on a lane group.
 template <int NX>
 static int agents_per_warp(int64_t agents, int sm_count) {
   int apw = 32;
-  while (apw > CoopShape<NX>::NG && (int64_t)apw * sm_count * 2 > agents) apw /= 2;
+  while (apw > 1 && (int64_t)apw * sm_count * 4 > agents) apw /= 2;
   return apw;
 }
 
