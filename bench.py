@@ -629,7 +629,26 @@ def extras(tg, torch, batch, args, peaks):
     out["relinearize"] = {"ms": ms, "pair_steps": int((batch.P * batch.T).sum()),
                           "note": "normals and guesses re-formed at the last iterate, whole batch, one call"}
     out.update(other_workloads(tg, torch, args, peaks))
+    out["homotopy_hot_start"] = homotopy_vs_primal(tg, torch, batch)
     return out
+
+
+def homotopy_vs_primal(tg, torch, batch, iters=100):
+    """The parametric (homotopy) hot start against the primal hot start on the
+    same batch, both in graph mode (per-phase kernels; the homotopy runs only
+    there), the first `iters` ADMM iterations: device time and EQP solves."""
+    row = {}
+    for start in ("turbo", "homotopy"):
+        s = tg.Solver(batch, precision=64, start=start, mode="graph")
+        ms = _event_ms(torch, lambda: s.solve(0.0, iters), reps=2)
+        cnt = s.counters()
+        s.close()
+        row[start] = {"ms": ms, "eqp_solves": int(cnt["eqp"].sum()), "factorized_stages": int(cnt["fact"].sum())}
+    row["iterations"] = iters
+    row["homotopy_over_primal_time"] = row["homotopy"]["ms"] / row["turbo"]["ms"]
+    row["note"] = ("graph mode, float64, tol 0; eqp_solves counts the homotopy's direction solves with the "
+                   "confirming passes; same iterates either way (the per-agent QP solution is unique)")
+    return row
 
 
 def solver_launches(solver) -> int:

@@ -52,6 +52,11 @@ extern "C" {
 #define TADMM_START_COLD 0  /* BaseADMM: u = clip(0), empty working set, every iteration */
 #define TADMM_START_HOT 1   /* HotstartADMM: cold first iteration, then previous (u, W, factors) */
 #define TADMM_START_TURBO 2 /* TurboADMM: clipped affine-LQR warm start, then hot start */
+#define TADMM_START_HOMOTOPY 3 /* turbo warm start, then a parametric (homotopy) hot start in the manner of
+                                  qpOASES, which the paper's hot start names: the optimum is followed from
+                                  the previous x-update's linear term to the new one, one direction solve
+                                  per working-set change, then confirmed by the primal active set; plain
+                                  and graph modes only (EINVAL in the batched mode) */
 
 /* execution modes */
 #define TADMM_MODE_BATCHED 0 /* all scenarios, all iterations in one persistent, graph-captured launch */
@@ -105,7 +110,7 @@ typedef struct {
 
 typedef struct {
   int32_t precision;       /* 64 (float64 arithmetic) or 32 (float32) */
-  int32_t start_mode;      /* TADMM_START_* */
+  int32_t start_mode;      /* TADMM_START_* (TADMM_START_HOMOTOPY: plain and graph modes) */
   int32_t as_max;          /* cap on active-set EQP solves per agent QP; 0 = 10*T*nu + 10 */
   double eps_rel;          /* multiplier drop tolerance scale; 0 = 1e-12 (fp64) / 1e-5 (fp32) */
   int32_t mode;            /* TADMM_MODE_* */

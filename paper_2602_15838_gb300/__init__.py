@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtadmm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4
 CONVERGED, NOT_CONVERGED, QP_FAIL, NUMERIC = 0, 1, 2, 3
-START = {"cold": 0, "hot": 1, "turbo": 2}
+START = {"cold": 0, "hot": 1, "turbo": 2, "homotopy": 3}
 FLAG_NO_FUSED_PAIR_GATHER, FLAG_NO_STRUCTURE, FLAG_NO_GROUPING, FLAG_DOUBLE_FLOAT = 1, 2, 4, 8
 FLAG_NO_LANE_GROUPS = FLAG_NO_COOP_REFACTOR = 16
 MODE = {"batched": 0, "plain": 1, "graph": 2}
@@ -133,8 +133,8 @@ class _HostBatch:
 class Solver:
     """A batch of scenarios resident on the current GPU (tadmm_create).
 
-    precision: 64 or 32; start: 'turbo' | 'hot' | 'cold'; mode: 'batched' |
-    'plain'.  Results are float64 regardless of the arithmetic precision.
+    precision: 64 or 32; start: 'turbo' | 'hot' | 'cold' | 'homotopy' (plain and
+    graph modes); mode: 'batched' | 'plain' | 'graph'.  Results are float64 regardless of the arithmetic precision.
     """
 
     def __init__(self, batch, precision: int = 64, start: str = "turbo", mode: str = "batched",

@@ -170,7 +170,7 @@ static void free_all(tadmm_handle* h) {
                   h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->phi, h->sx, h->models, h->st_models, h->X, h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
                   h->res,    h->eqp,   h->fact,  h->rho_out, h->rho_chg, h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
-                  h->ex_buf, h->flag,  h->red2};
+                  h->ex_buf, h->flag,  h->red2, h->hprev, h->hmu, h->hdmu};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* bptrs[] = {h->bwd.act, h->bwd.cnt, h->bwd.amask, h->bwd.psi, h->bwd.kks, h->bwd.pos0, h->bwd.force,
@@ -251,7 +251,11 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
   o.mode = TADMM_MODE_BATCHED;
   if (opt) o = *opt;
   if (o.precision != 64 && o.precision != 32) return set_error(TADMM_EINVAL, "precision must be 64 or 32");
-  if (o.start_mode < 0 || o.start_mode > 2) return set_error(TADMM_EINVAL, "start_mode must be 0, 1 or 2");
+  if (o.start_mode < 0 || o.start_mode > 3) return set_error(TADMM_EINVAL, "start_mode must be 0, 1, 2 or 3");
+  if (o.start_mode == TADMM_START_HOMOTOPY && o.mode == TADMM_MODE_BATCHED)
+    return set_error(TADMM_EINVAL, "the homotopy hot start runs in the plain and graph modes");
+  if (o.start_mode == TADMM_START_HOMOTOPY && (o.flags & TADMM_FLAG_DOUBLE_FLOAT))
+    return set_error(TADMM_EINVAL, "the homotopy hot start does not take TADMM_FLAG_DOUBLE_FLOAT");
   if (o.mode != TADMM_MODE_BATCHED && o.mode != TADMM_MODE_PLAIN && o.mode != TADMM_MODE_GRAPH)
     return set_error(TADMM_EINVAL, "bad mode");
   if (o.as_max < 0 || o.eps_rel < 0 || !std::isfinite(o.eps_rel)) return set_error(TADMM_EINVAL, "bad as_max / eps_rel");
@@ -456,6 +460,9 @@ extern "C" int tadmm_create(const tadmm_batch* b, const tadmm_options* opt, tadm
       (rc = dmalloc(&h->st_w0, 8 * h->tot_as * dp)) || (rc = dmalloc(&h->ex_buf, h->ex_bytes + h->tot_as * nu + 16)) ||
       (rc = dmalloc(&h->flag, 16)) || (rc = dmalloc(&h->red2, 16)) ||
       (o.relax_alpha != 1.0 && ((rc = dmalloc(&h->phi, fs * h->tot_ps)) || (rc = dmalloc(&h->sx, fs * h->tot_as * dp)))) ||
+      (o.start_mode == TADMM_START_HOMOTOPY &&
+       ((rc = dmalloc(&h->hprev, fs * h->tot_as * dp)) || (rc = dmalloc(&h->hmu, fs * h->tot_as * nu)) ||
+        (rc = dmalloc(&h->hdmu, fs * h->tot_as * nu)))) ||
       (h->hetero && ((rc = dmalloc(&h->models, fs * na * (nx * nx + nx * nu + 2 * nu))) ||
                      (rc = dmalloc(&h->st_models, 8 * na * (nx * nx + nx * nu + 2 * nu)))))) {
     free_all(h);

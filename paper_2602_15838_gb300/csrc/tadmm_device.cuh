@@ -36,7 +36,7 @@
 namespace tadmm {
 
 enum { ST_CONVERGED = 0, ST_NOT_CONVERGED = 1, ST_QP_FAIL = 2, ST_NUMERIC = 3 };
-enum { START_COLD = 0, START_HOT = 1, START_TURBO = 2 };
+enum { START_COLD = 0, START_HOT = 1, START_TURBO = 2, START_HOMOTOPY = 3 };
 enum { QP_COLD = 0, QP_LQR = 1, QP_GIVEN = 2 };
 
 struct ScenMeta {
@@ -103,6 +103,10 @@ struct Dev {
   const int32_t* deg;        // [agents] consensus copies n_c of each agent (its pairs)
   const int32_t* adj_ptr;    // [agents + 1] listed-pair adjacency of sparse scenarios
   const int32_t* adj;        // scenario-local pair index, bit 31 set when the agent is second
+  // homotopy hot start (per-phase kernels): per scenario at as_off
+  F* hprev;                  // [T][DP][N] coupling term of the agent's previous x-update
+  F* mu;                     // [T][NU][N] bound multipliers of the previous x-update's optimum
+  F* dmu;                    // [T][NU][N] their direction along the homotopy segment
 };
 
 // Per-stage factor cache of one agent (stage t):
@@ -1482,14 +1486,274 @@ __device__ __forceinline__ AgentCtx<F, NX, NU, DP> idle_agent(const Model<F, NX,
 template <typename F>
 __device__ __forceinline__ int start_kind_of(const Dev<F>& D, int k) {
   if (D.start_mode == START_COLD) return QP_COLD;
-  if (k == 0) return D.start_mode == START_TURBO ? QP_LQR : QP_COLD;
+  if (k == 0) return (D.start_mode == START_TURBO || D.start_mode == START_HOMOTOPY) ? QP_LQR : QP_COLD;
   return QP_GIVEN;
+}
+
+// ---------------------------------------------------------------------------
+// Parametric (homotopy) hot start of the per-agent QP, in the manner of
+// qpOASES's hot start (Sec. IV.C names qpOASES's hotstart as the source of the
+// paper's hot start): the optimum is followed from the previous x-update's
+// linear term q_old to the new one along q(tau) = q_old + tau (q - q_old),
+// tau: 0 -> 1.  On each segment the working set W is fixed and the optimum
+// moves linearly, u(tau) = u + tau du, mu(tau) = mu + tau dmu, where (du, dmu)
+// solve the equality-constrained problem with linear term q - q_old, x_0 = 0
+// and the held inputs at 0 (the direction solve).  The segment ends where a
+// free input meets a bound or a held input's multiplier meets zero (smallest
+// step, ties to the lowest (t, c) index; steps clamped at 0); the working set
+// changes there and the next segment starts.  The primal active set then
+// confirms the end point (one EQP solve when the homotopy reached tau = 1).
+// ---------------------------------------------------------------------------
+
+// u + s v with a separate product and sum (no contraction), the order in which
+// the plain definition of the segment step is written.
+__device__ __forceinline__ double step_rn(double u, double s, double v) { return __dadd_rn(u, __dmul_rn(s, v)); }
+__device__ __forceinline__ float step_rn(float u, float s, float v) { return __fadd_rn(u, __fmul_rn(s, v)); }
+__device__ __forceinline__ df64 step_rn(df64 u, df64 s, df64 v) { return u + s * v; }
+
+// Direction solve of one agent with the cached stage factors (one lane per
+// agent): linear term q_t - q_old,t (t = 1..T), x_0 = 0, held inputs at 0.
+// Writes du to Us and the held inputs' multiplier directions
+// dmu = +-(B' dlambda_{t+1}) (no Rbar term: a held input's direction is 0) to
+// dmu; returns 1 on a non-finite value.
+template <typename F, int NX, int NU, int DP, bool DI>
+__device__ int eqp_direction(const AgentCtx<F, NX, NU, DP>& A, const F* hprev, F* dmu) {
+  constexpr int H = NX / 2;
+  using CL = CacheLayout<NX, NU>;
+  const Model<F, NX, NU>& Mo = *A.M;
+  const int T = A.T, N = A.N, i = A.i;
+  auto dq = [&](int t, int r) -> F {   // (q - q_old)_t row r
+    if (r >= DP) return F(0);
+    const F hp = hprev[((size_t)(t - 1) * DP + r) * N + i];
+    if (t < T) return A.q_h(r, A.hv(t, r)) - A.q_h(r, hp);
+    const F base = terminal_lin(A.qf[r], A.xr[r]);
+    return lin_term(base, A.k(AgentConst<NX, NU>::RHO), A.hv(t, r)) -
+           lin_term(base, A.k(AgentConst<NX, NU>::RHO), hp);
+  };
+  F pn[NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) pn[r] = dq(T, r);
+  for (int t = T - 1; t >= 0; --t) {
+    const uint16_t mask = A.W(t);
+    F K[NU][NX], L[NU][NU];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+#pragma unroll
+      for (int c = 0; c < NX; ++c) K[a][c] = A.C(t, CL::K + a * NX + c);
+#pragma unroll
+      for (int b = 0; b < NU; ++b) L[a][b] = A.C(t, CL::L + (b <= a ? a * NU + b : b * NU + a));
+    }
+    F bpn[NU], sv[NU], kk[NU];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      F acc = 0;
+      if constexpr (DI) {
+        acc = fma(Mo.B[0][0], pn[a], acc);
+        acc = fma(Mo.B[H][0], pn[H + a], acc);
+      } else {
+#pragma unroll
+        for (int r = 0; r < NX; ++r) acc = fma(Mo.B[r][a], pn[r], acc);
+      }
+      bpn[a] = acc;
+      sv[a] = (mask & (0x101u << a)) ? F(0) : acc;
+    }
+    if (mask) {
+#pragma unroll
+      for (int a = 0; a < NU; ++a) A.C(t, CL::bp + a) = bpn[a];
+    }
+    neg_sinv<F, NU>(L, sv, kk);
+#pragma unroll
+    for (int a = 0; a < NU; ++a) A.C(t, CL::k + a) = kk[a];
+    if (t >= 1) {
+      F np[NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        F acc = dq(t, r);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], pn[k], acc);
+#pragma unroll
+        for (int k = 0; k < NU; ++k) acc = fma(K[k][r], sv[k], acc);
+        np[r] = acc;
+      }
+#pragma unroll
+      for (int r = 0; r < NX; ++r) pn[r] = np[r];
+    }
+  }
+  F xv[NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) xv[r] = F(0);
+  int bad = 0;
+  for (int t = 0; t < T; ++t) {
+    const uint16_t mask = A.W(t);
+    F uv[NU];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      if (mask & (0x101u << a)) {
+        uv[a] = F(0);
+      } else {
+        F acc = A.C(t, CL::k + a);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) acc = fma(A.C(t, CL::K + a * NX + c), xv[c], acc);
+        uv[a] = acc;
+      }
+    }
+    F xn[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      F acc = 0;
+#pragma unroll
+      for (int c = 0; c < NX; ++c) acc = fma(Mo.A[r][c], xv[c], acc);
+#pragma unroll
+      for (int c = 0; c < NU; ++c) acc = fma(Mo.B[r][c], uv[c], acc);
+      xn[r] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      A.us(t, a) = uv[a];
+      F d = F(0);
+      if (mask & (0x101u << a)) {
+        // B' dlambda_{t+1} = (P_{t+1} B)' dx_{t+1} + B' dp_{t+1}
+        F g = A.C(t, CL::bp + a);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) g = fma(A.C(t, CL::PB + c * NU + a), xn[c], g);
+        d = (mask & (1u << a)) ? g : -g;
+      }
+      dmu[((size_t)t * NU + a) * N + i] = d;
+      if (!finite_(d) || !finite_(uv[a])) bad = 1;
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) xv[r] = xn[r];
+  }
+  return bad;
+}
+
+// Homotopy segments of the warp's agents from (u, W, mu) of the previous
+// x-update (all lanes call this together; lanes with has = false only help
+// the refactorizations).  Counts every direction solve in neqp.  Returns
+// ST_NUMERIC on a non-finite value, else ST_CONVERGED (the confirming primal
+// active-set solve follows in xupdate_agent).
+template <typename F, int NX, int NU, int DP, bool DI>
+__device__ int homotopy_agent(const AgentCtx<F, NX, NU, DP>& A, bool has, const F* hprev, F* mu, F* dmu,
+                              int as_max, unsigned long long& neqp, unsigned long long& nfact) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const Model<F, NX, NU>& Mo = *A.M;
+  const int T = has ? A.T : 0, N = A.N, i = A.i;
+  auto MU = [&](F* b, int t, int c) -> F& { return b[((size_t)t * NU + c) * N + i]; };
+  int dirty = -1;
+  for (int t = 0; t < T; ++t)
+    if (A.CM(t) != A.W(t)) dirty = t;
+  bool done = !has;
+  int status = ST_CONVERGED, steps = 0;
+  F tau = F(0);
+  for (;;) {
+    const bool go = !done && steps < as_max;
+    if (!__any_sync(FULL, go)) break;
+    int bad = 0;
+    refactor_sweep<F, NX, NU, DP, DI>(A, go, dirty, nfact, bad);
+    if (!go) continue;
+    ++steps;
+    ++neqp;
+    if (bad || eqp_direction<F, NX, NU, DP, DI>(A, hprev, dmu)) {
+      status = ST_NUMERIC;
+      done = true;
+      continue;
+    }
+    dirty = -1;
+    F best = F(1) - tau;
+    int bk = -1, side = 0;
+    for (int t = 0; t < T; ++t) {
+      const uint16_t w = A.W(t);
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        F r;
+        int sd;
+        if (!(w & (0x101u << c))) {
+          const F du = A.us(t, c), u = A.u(t, c);
+          if (du > F(0)) { r = (Mo.umax[c] - u) / du; sd = 2; }
+          else if (du < F(0)) { r = (Mo.umin[c] - u) / du; sd = 1; }
+          else continue;
+        } else {
+          const F dm = MU(dmu, t, c);
+          if (!(dm < F(0))) continue;
+          r = MU(mu, t, c) / -dm;
+          sd = 0;
+        }
+        if (r < F(0)) r = F(0);
+        if (r < best) { best = r; bk = t * NU + c; side = sd; }
+      }
+    }
+    for (int t = 0; t < T; ++t) {
+      const uint16_t w = A.W(t);
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        if (!(w & (0x101u << c))) A.u(t, c) = step_rn(A.u(t, c), best, A.us(t, c));
+        else MU(mu, t, c) = step_rn(MU(mu, t, c), best, MU(dmu, t, c));
+      }
+    }
+    tau = tau + best;
+    if (bk < 0) {
+      done = true;   // tau = 1: the segment reached the new problem
+      continue;
+    }
+    const int bt = bk / NU, ba = bk - bt * NU;
+    if (side) {
+      A.W(bt) = (uint16_t)(A.W(bt) | (side == 1 ? (1u << ba) : (0x100u << ba)));
+      A.u(bt, ba) = side == 1 ? Mo.umin[ba] : Mo.umax[ba];
+    } else {
+      A.W(bt) = (uint16_t)(A.W(bt) & ~(0x101u << ba));
+    }
+    MU(mu, bt, ba) = F(0);
+    dirty = bt;
+  }
+  return status;
+}
+
+// Bound multipliers of the agent's QP optimum (for the next homotopy) from the
+// costate recursion lambda_T = Qbar_T x_T + q_T, lambda_t = Qbar_t x_t + q_t +
+// A' lambda_{t+1} (Sec. IV.B dual recovery): mu = +-(Rbar u_t + B' lambda_{t+1})
+// on the held inputs (lower: +, upper: -), 0 on the free ones; and the coupling
+// term of this x-update becomes the agent's previous one.
+template <typename F, int NX, int NU, int DP>
+__device__ void homotopy_store(const AgentCtx<F, NX, NU, DP>& A, F* hprev, F* mu) {
+  using AC = AgentConst<NX, NU>;
+  const Model<F, NX, NU>& Mo = *A.M;
+  const int T = A.T, N = A.N, i = A.i;
+  F lam[NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) lam[r] = F(0);
+  for (int t = T; t >= 1; --t) {
+    F ln[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      const F qb = t < T ? A.k(AC::QB + r) : A.qbarT(r);
+      F acc = fma(qb, A.x(t, r), A.q(t, r));
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc = fma(Mo.A[k][r], lam[k], acc);
+      ln[r] = acc;
+    }
+    const uint16_t w = A.W(t - 1);
+#pragma unroll
+    for (int c = 0; c < NU; ++c) {
+      F m = F(0);
+      if (w & (0x101u << c)) {
+        F g = A.k(AC::RB + c) * A.u(t - 1, c);
+#pragma unroll
+        for (int r = 0; r < NX; ++r) g = fma(Mo.B[r][c], ln[r], g);
+        m = (w & (1u << c)) ? g : -g;
+      }
+      mu[((size_t)(t - 1) * NU + c) * N + i] = m;
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) lam[r] = ln[r];
+#pragma unroll
+    for (int r = 0; r < DP; ++r) hprev[((size_t)(t - 1) * DP + r) * N + i] = A.hv(t, r);
+  }
 }
 
 // x-update of agents i0, i0 + stride, ... of scenario s (none when in_scen is
 // false).  Every lane of the warp calls this; all lanes take the same number
 // of rounds, so that xupdate_agent always runs warp-wide.
-template <typename F, int NX, int NU, int DP, bool DI, bool COOP_EQP = false>
+template <typename F, int NX, int NU, int DP, bool DI, bool COOP_EQP = false, bool HOMO = false>
 __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const ScenMeta& s, bool in_scen, int k,
                              int lvl_out, int i0, int stride, unsigned long long& neqp,
                              unsigned long long& nfact, F* kcs) {
@@ -1504,7 +1768,21 @@ __device__ int xupdate_phase(const Dev<F>& D, const Model<F, NX, NU>& M, const S
     const AgentCtx<F, NX, NU, DP> A =
         has ? make_agent<F, NX, NU, DP, DI>(D, M, s, i0 + r * stride, lvl_out, kcs + threadIdx.x, blockDim.x, s.rho)
             : idle_agent<F, NX, NU, DP>(M, kcs + threadIdx.x, blockDim.x, D.coop);
-    const int res = xupdate_agent<F, NX, NU, DP, DI, COOP_EQP>(A, has, kind, as_max, eps, neqp, nfact);
+    int res = ST_CONVERGED;
+    if constexpr (HOMO) {
+      // warp-collective: every lane enters when any lane's agent takes a
+      // homotopy (lanes of other iterations or of stopped scenarios only help)
+      const bool hh = has && k > 0;
+      if (__any_sync(0xffffffffu, hh))
+        res = homotopy_agent<F, NX, NU, DP, DI>(A, hh, D.hprev + s.as_off * DP, D.mu + s.as_off * NU,
+                                               D.dmu + s.as_off * NU, as_max, neqp, nfact);
+    }
+    const int r2 = xupdate_agent<F, NX, NU, DP, DI, COOP_EQP>(A, has && res == ST_CONVERGED, kind, as_max, eps,
+                                                             neqp, nfact);
+    if (res == ST_CONVERGED) res = r2;
+    if constexpr (HOMO) {
+      if (has && res == ST_CONVERGED) homotopy_store<F, NX, NU, DP>(A, D.hprev + s.as_off * DP, D.mu + s.as_off * NU);
+    }
     if (has && res > st) st = res;
   }
   return st;

@@ -62,6 +62,9 @@ struct tadmm_handle {
   int hetero = 0;                // 1: per-agent dynamics
   void* phi = nullptr;           // over-relaxation: [tot_ps] pair part of the consensus copies
   void* sx = nullptr;            // over-relaxation: [tot_as][dp] agent part of the consensus copies
+  void* hprev = nullptr;         // homotopy hot start: [tot_as][dp] previous coupling terms
+  void* hmu = nullptr;           //   [tot_as][nu] bound multipliers of the previous optimum
+  void* hdmu = nullptr;          //   [tot_as][nu] their segment direction
   void* X = nullptr;
   void* h = nullptr;
   void* U = nullptr;

@@ -67,9 +67,9 @@ __global__ void k_init(Dev<F> D, int sc) {
   }
 }
 
-template <typename F, int NX, int NU, int DP, bool DI>
+template <typename F, int NX, int NU, int DP, bool DI, bool HOMO = false>
 // One warp per CTA; lanes 0..apw-1 own agents blockIdx.x * apw + lane, the
-// other lanes help with their refactorizations.
+// other lanes help with their refactorizations.  HOMO: homotopy hot start.
 __global__ void __launch_bounds__(32) k_xupdate(Dev<F> D, int sc, int k, int lvl_out, int32_t* flag, int apw) {
   __shared__ Model<F, NX, NU> M;
   __shared__ F kcs[AgentConst<NX, NU>::KC * 32];
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(32) k_xupdate(Dev<F> D, int sc, int k, int lvl
   const bool owns = (int)threadIdx.x < apw;
   const int i = blockIdx.x * apw + threadIdx.x;
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI, true>(D, M, s, owns, k, lvl_out, i, s.N, neqp, nfact, kcs);
+  const int st = xupdate_phase<F, NX, NU, DP, DI, true, HOMO>(D, M, s, owns, k, lvl_out, i, s.N, neqp, nfact, kcs);
   if (st && owns && i < s.N) atomicMax(flag, st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
   if (nfact) atomicAdd(&D.fact[sc], nfact);
@@ -174,7 +174,7 @@ __global__ void k_g_init(Dev<F> D, GState G) {
   }
 }
 
-template <typename F, int NX, int NU, int DP, bool DI>
+template <typename F, int NX, int NU, int DP, bool DI, bool HOMO = false>
 __global__ void __launch_bounds__(32) k_g_xupdate(Dev<F> D, GState G, const int32_t* __restrict__ agent_scen,
                                                    int64_t tot_agents, int apw) {
   __shared__ Model<F, NX, NU> M;
@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(32) k_g_xupdate(Dev<F> D, GState G, const int3
   const ScenMeta s = D.meta[sc];
   const int i = (int)(ga - s.agent_off), k = G.iter[sc];
   unsigned long long neqp = 0, nfact = 0;
-  const int st = xupdate_phase<F, NX, NU, DP, DI, true>(D, M, s, in_scen, k, (k + 1) & 1, i, s.N, neqp, nfact, kcs);
+  const int st =
+      xupdate_phase<F, NX, NU, DP, DI, true, HOMO>(D, M, s, in_scen, k, (k + 1) & 1, i, s.N, neqp, nfact, kcs);
   if (!in_scen) return;
   if (st) atomicMax(&G.fail[sc], st);
   if (neqp) atomicAdd(&D.eqp[sc], neqp);
@@ -493,6 +494,9 @@ static Dev<F> make_dev(tadmm_handle* h) {
   D.deg = h->deg;
   D.adj_ptr = h->adj_ptr;
   D.adj = h->adj;
+  D.hprev = (F*)h->hprev;
+  D.mu = (F*)h->hmu;
+  D.dmu = (F*)h->hdmu;
   return D;
 }
 
@@ -667,16 +671,17 @@ int Impl<F, NX, NU, DP>::solve_batched(tadmm_handle* h, double tol, int max_iter
   return cuda_check(cudaGraphLaunch(h->gexec, st), "graph launch");
 }
 
-// Agents per warp of the per-phase x-update kernels: 32 (one per lane) when
-// there are enough agents to give every SM at least four warps, otherwise
-// fewer, down to one.  Each of an SM's four sub-partitions issues FP64
-// instructions at its own fixed rate whatever the number of active lanes, so a
-// small agent count (one large scenario) is spread over four warps per SM, one
-// per sub-partition, rather than packed into fewer warps; an agent alone in
-// its warp still takes its EQP passes and refactorizations on a lane group.
+// Agents per warp of the per-phase x-update kernels: at most one per lane
+// group of the cooperative passes (CoopShape<NX>::NG: 8 in 2D, 4 in 3D), and
+// fewer, down to one, when there are not enough agents to give every SM four
+// warps.  Each of an SM's four sub-partitions issues FP64 instructions at its
+// own fixed rate whatever the number of active lanes, so a small agent count
+// (one large scenario) is spread over four warps per SM, one per
+// sub-partition, rather than packed into fewer warps; every owner can take its
+// EQP passes and refactorizations on a lane group.
 template <int NX>
 static int agents_per_warp(int64_t agents, int sm_count) {
-  int apw = 32;
+  int apw = CoopShape<NX>::NG;
   while (apw > 1 && (int64_t)apw * sm_count * 4 > agents) apw /= 2;
   return apw;
 }
@@ -688,6 +693,7 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
   D.max_iter = max_iter;
   unsigned long long* hb = (unsigned long long*)h->pinned;  // [0] flag, [1] r bits, [2] s bits
   int64_t launches = 0;
+  const bool homo = h->opt.start_mode == TADMM_START_HOMOTOPY;
   for (int sc = 0; sc < h->n_scen; ++sc) {
     const ScenMeta& s = h->meta_h[sc];
     const int64_t PT = (int64_t)s.P * s.T, NT = (int64_t)s.N * s.T;
@@ -704,9 +710,15 @@ int Impl<F, NX, NU, DP>::solve_plain(tadmm_handle* h, double tol, int max_iter, 
       cudaMemsetAsync(h->flag, 0, sizeof(int32_t), st);
       cudaMemsetAsync(h->red2, 0, 2 * sizeof(unsigned long long), st);
       if (h->di)
-        k_xupdate<F, NX, NU, DP, true><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
+        if (homo)
+          k_xupdate<F, NX, NU, DP, true, true><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
+        else
+          k_xupdate<F, NX, NU, DP, true><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
       else
-        k_xupdate<F, NX, NU, DP, false><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
+        if (homo)
+          k_xupdate<F, NX, NU, DP, false, true><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
+        else
+          k_xupdate<F, NX, NU, DP, false><<<(s.N + apw - 1) / apw, 32, 0, st>>>(D, sc, k, xl ^ 1, h->flag, apw);
       k_pair<F, NX, NU, DP><<<grid_for(PT, 256, h->sm_count * 8), 256, 0, st>>>(D, sc, xl, tk, tkp1, h->red2);
       launches += 2;
       cudaMemcpyAsync(hb, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
@@ -778,6 +790,7 @@ int Impl<F, NX, NU, DP>::solve_graph(tadmm_handle* h, double tol, int max_iter, 
   GState G{(int32_t*)h->gs_iter, (int32_t*)h->gs_active, (int32_t*)h->gs_need, (int32_t*)h->gs_fail,
            (unsigned long long*)h->gs_rb, (unsigned long long*)h->gs_sb};
   Dev<F> D = make_dev<F>(h);
+  const bool homo = h->opt.start_mode == TADMM_START_HOMOTOPY;
   D.tol = tol;
   D.max_iter = max_iter;
   int tmax = 0;
@@ -815,9 +828,15 @@ int Impl<F, NX, NU, DP>::solve_graph(tadmm_handle* h, double tol, int max_iter, 
     const dim3 gp(grid_for(h->tot_pairs, 128, 1 << 30), tmax);
     const dim3 gg(h->n_gblk, tmax);
     if (h->di)
-      k_g_xupdate<F, NX, NU, DP, true><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
+      if (homo)
+        k_g_xupdate<F, NX, NU, DP, true, true><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
+      else
+        k_g_xupdate<F, NX, NU, DP, true><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
     else
-      k_g_xupdate<F, NX, NU, DP, false><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
+      if (homo)
+        k_g_xupdate<F, NX, NU, DP, false, true><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
+      else
+        k_g_xupdate<F, NX, NU, DP, false><<<gx, 32, 0, h->cap_stream>>>(D, G, h->agent_scen, h->tot_agents, gapw);
     if (h->tot_pairs > 0) k_g_pair<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);
     k_g_check1<F><<<grid_for(h->n_scen, 128), 128, 0, h->cap_stream>>>(D, G);
     if (h->tot_pairs > 0) k_g_dual<F, NX, NU, DP><<<gp, 128, 0, h->cap_stream>>>(D, G, h->pair_scen, h->tot_pairs);

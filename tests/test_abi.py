@@ -57,7 +57,8 @@ def _create_rc(tg, batch, **opt):
 
 @pytest.mark.parametrize("fault", ["nan_q", "neg_r", "box", "rho", "dims", "N0", "prec", "adapt_mode", "adapt_mu",
                                    "pair_dup", "pair_order", "relax_range", "relax_mode", "relax_flags",
-                                   "hetero_half", "hetero_nan", "hetero_df64"])
+                                   "hetero_half", "hetero_nan", "hetero_df64", "homotopy_batched", "homotopy_df64",
+                                   "start_range"])
 def test_invalid_inputs_rejected_on_host(libtadmm, fault):
     tg, _ = libtadmm
     from instances import make_workload
@@ -91,6 +92,14 @@ def test_invalid_inputs_rejected_on_host(libtadmm, fault):
             b.A_agent[1, 0, 0] = np.nan
         else:
             opt["flags"] = 8
+    elif fault == "homotopy_batched":   # the homotopy hot start runs in the plain and graph modes
+        opt["start"] = 3
+    elif fault == "homotopy_df64":
+        opt["start"] = 3
+        opt["mode"] = 1
+        opt["flags"] = 8
+    elif fault == "start_range":
+        opt["start"] = 4
     elif fault == "relax_range":   # over-relaxation factor in (0, 2)
         opt["relax"] = 2.0
     elif fault == "relax_mode":    # over-relaxation runs in the batched mode only

@@ -652,3 +652,76 @@ def test_bench_workload_statistics(tg):
     s.close()
     assert int((sol["status"] == tg.CONVERGED).sum()) == bench.WORKLOAD_SOLVES
     assert int(sol["iters"].sum()) == bench.WORKLOAD_SCEN_ITERS
+
+
+@pytest.mark.parametrize("mode", ["plain", "graph"])
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_homotopy_hot_start_matches_oracle(tg, mode, k):
+    """Parametric (homotopy) hot start on the GPU against the oracle's
+    (ORC_START_HOMOTOPY) on the 2-agent crossing and the 14-agent ring: every
+    iterate within 1e-9, the same non-degenerate final working sets, and the
+    same count of EQP solves (direction solves plus confirming passes)."""
+    for name in ("pair", "ring14"):
+        b = make_workload(name)
+        g, cnt = gpu_run(tg, b, 0.0, k, start="homotopy", mode=mode)
+        o = oracle.admm(b, 0, start_mode=oracle.START_HOMOTOPY, tol=0.0, max_iter=k, nthreads=8)
+        g = g[0]
+        assert g["iters"] == k == o["iters"], name
+        assert rel(g["X"], o["X"]) <= 1e-9, name
+        assert rel(g["U"], o["U"]) <= 1e-9, name
+        assert rel(g["theta"], o["theta"]) <= 1e-9, name
+        ok, _ = nondegenerate_w_equal(g["W"], o, b)
+        assert ok, name
+        assert cnt["eqp"][0] == o["as_iters"], (name, int(cnt["eqp"][0]), o["as_iters"])
+
+
+def test_homotopy_hot_start_equals_primal_hot_start(tg):
+    """The per-agent QP solution is unique, so the homotopy and the primal hot
+    start give the same ADMM iterates (14-agent ring, 60 iterations, graph
+    mode), to rounding."""
+    b = make_workload("ring14")
+    gh, ch = gpu_run(tg, b, 0.0, 60, start="homotopy", mode="graph")
+    gp, cp = gpu_run(tg, b, 0.0, 60, start="turbo", mode="graph")
+    assert rel(gh[0]["X"], gp[0]["X"]) <= 1e-10
+    assert rel(gh[0]["U"], gp[0]["U"]) <= 1e-10
+    assert rel(gh[0]["theta"], gp[0]["theta"]) <= 1e-10
+    assert ch["eqp"][0] > 0 and cp["eqp"][0] > 0
+
+
+def test_homotopy_mixed_batch_graph_mode_sampled(tg):
+    """24 scenarios of the mixed batch in graph mode with the homotopy hot start:
+    every scenario's iterates after 8 iterations within 1e-9 of the oracle's
+    homotopy run, and its EQP count equal to the oracle's."""
+    b = make_workload("mixed", n_scen=24)
+    g, cnt = gpu_run(tg, b, 0.0, 8, start="homotopy", mode="graph")
+    same = 0
+    for k in range(b.n_scen):
+        o = oracle.admm(b, k, start_mode=oracle.START_HOMOTOPY, tol=0.0, max_iter=8, nthreads=8)
+        assert rel(g[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(g[k]["U"], o["U"]) <= 1e-9, k
+        assert rel(g[k]["theta"], o["theta"]) <= 1e-9, k
+        same += int(cnt["eqp"][k] == o["as_iters"])
+    assert same == b.n_scen, same
+
+
+def test_graph_mode_several_agents_per_warp(tg):
+    """300 mixed scenarios (about 5000 agents): the graph-mode x-update puts
+    eight agents on each warp.  The primal hot start equals the persistent
+    kernel (iterates to 1e-12, working sets and EQP counts exactly) and the
+    homotopy hot start matches the oracle's on sampled scenarios (1e-9, the
+    same EQP counts)."""
+    b = make_workload("mixed", n_scen=300)
+    assert int(b.N.sum()) >= 8 * 152 * 4
+    gb, cb = gpu_run(tg, b, 0.0, 4)
+    gg, cg = gpu_run(tg, b, 0.0, 4, mode="graph")
+    for k in range(b.n_scen):
+        assert rel(gg[k]["X"], gb[k]["X"]) <= 1e-12, k
+        assert rel(gg[k]["theta"], gb[k]["theta"]) <= 1e-12, k
+        assert np.array_equal(gg[k]["W"], gb[k]["W"]), k
+    assert np.array_equal(cb["eqp"], cg["eqp"])
+    gh, ch = gpu_run(tg, b, 0.0, 4, mode="graph", start="homotopy")
+    for k in (0, 57, 150, 299):
+        o = oracle.admm(b, k, start_mode=oracle.START_HOMOTOPY, tol=0.0, max_iter=4, nthreads=8)
+        assert rel(gh[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(gh[k]["theta"], o["theta"]) <= 1e-9, k
+        assert int(ch["eqp"][k]) == o["as_iters"], k
