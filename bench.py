@@ -162,8 +162,9 @@ def source_hash() -> str:
 
 
 def profile_counters(tpc: int, variant: int):
-    """Figures of the committed ncu summary of k_batched (key = value lines),
-    or (None, reason) when the kernel sources or the launch shape differ."""
+    """Figures of the committed ncu summary of k_batched (key = value lines) for
+    this launch shape, or (None, reason) when the kernel sources or the launch
+    shape differ from the profiled ones."""
     try:
         with open(COUNTERS_FILE) as f:
             kv = dict(ln.split("=", 1) for ln in f if "=" in ln and not ln.lstrip().startswith("#"))
@@ -173,8 +174,10 @@ def profile_counters(tpc: int, variant: int):
     if kv.get("source_hash") != source_hash():
         return None, "kernel sources changed since the profile (hash %s, now %s)" % (kv.get("source_hash"),
                                                                                     source_hash())
-    if (int(kv.get("threads_per_cta", -1)), int(kv.get("kernel_variant", -1))) != (tpc, variant):
-        return None, "launch shape differs from the profiled one"
+    variants = [int(v) for v in kv.get("variants", "").split(",") if v.strip()]
+    if int(kv.get("threads_per_cta", -1)) != tpc or variant not in variants:
+        return None, "launch shape differs from the profiled ones"
+    kv["dram_bytes_per_launch"] = kv["variant%d.dram_bytes_per_launch" % variant]
     return kv, None
 
 

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "tadmm_impl.h"
@@ -49,9 +50,42 @@ static int cache_words(int nx, int nu) {
   return nx * nx + nu * nx + nu * nu + nu + nx * nu + nu;
 }
 
+// True when no element is a NaN or an infinity (all exponent bits set).  The
+// check runs over chunks with no early exit inside a chunk, on the bit
+// patterns, so that the compiler vectorizes it; large arrays are split over a
+// few host threads.  It runs on every tadmm_create and tadmm_update (the
+// halfspace normals alone are tens of millions of values).
+static bool finite_range(const double* p, int64_t n) {
+  constexpr uint64_t kExp = 0x7FF0000000000000ull;
+  constexpr int64_t kChunk = 4096;
+  for (int64_t k0 = 0; k0 < n; k0 += kChunk) {
+    const int64_t k1 = std::min(n, k0 + kChunk);
+    uint64_t bad = 0;
+    for (int64_t k = k0; k < k1; ++k) {
+      uint64_t b;
+      std::memcpy(&b, p + k, sizeof(b));
+      bad |= (uint64_t)((b & kExp) == kExp);
+    }
+    if (bad) return false;
+  }
+  return true;
+}
+
 static bool finite_all(const double* p, int64_t n) {
-  for (int64_t k = 0; k < n; ++k)
-    if (!std::isfinite(p[k])) return false;
+  constexpr int64_t kPerThread = (int64_t)1 << 22;
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<int64_t>(std::min<unsigned>(hw, 8u), (n + kPerThread - 1) / kPerThread);
+  if (nt <= 1) return finite_range(p, n);
+  std::vector<std::thread> pool;
+  std::vector<uint8_t> ok((size_t)nt, 1);
+  const int64_t per = (n + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    const int64_t a = t * per, b = std::min(n, a + per);
+    pool.emplace_back([&, t, a, b]() { ok[(size_t)t] = b > a ? finite_range(p + a, b - a) : 1; });
+  }
+  for (auto& th : pool) th.join();
+  for (uint8_t v : ok)
+    if (!v) return false;
   return true;
 }
 
