@@ -534,25 +534,34 @@ def other_workloads(tg, torch, args, peaks):
     from instances import make_workload
     out = {}
     # 2 agents, T = 20: latency of one solve to tol 1e-4 in each execution mode
+    def frac(bb, s, ms):
+        fl, _ = algorithmic_flops(bb, s.counters(), s.solution())
+        return fl / (ms / 1e3) / 1e12 / peaks[64]
+
     b = make_workload("pair")
     row = {}
     for mode in ("batched", "graph", "plain"):
         s = tg.Solver(b, precision=64, mode=mode)
-        row[f"ms_per_solve_{mode}"] = _event_ms(torch, lambda: s.solve(args.tol, args.max_iter), reps=10)
+        row[f"ms_per_solve_{mode}"] = ms = _event_ms(torch, lambda: s.solve(args.tol, args.max_iter), reps=10)
+        row[f"frac_of_measured_fp64_{mode}"] = frac(b, s, ms)
         sol = s.split(s.solution())[0]
         s.close()
         row["iterations"], row["status"] = sol["iters"], sol["status"]
     s = tg.Solver(b, precision=32)
     row["ms_per_solve_batched_fp32"] = _event_ms(torch, lambda: s.solve(args.tol, args.max_iter), reps=10)
     s.close()
-    row["note"] = "one scenario: latency-bound (a roofline fraction is not meaningful at 20 pair-steps)"
+    row["note"] = ("one scenario: latency-bound; the FP64 fractions (algorithmic flops from the run's counters over "
+                   "the measured peak) show how little of the GPU a 2-agent problem occupies")
     out["pair_2_agents"] = row
     # 14 agents, T = 20: ms per iteration over 500 iterations; iterations to tol 1e-4 with balancing
     b = make_workload("ring14")
     row = {}
     for mode, prec in (("batched", 64), ("graph", 64), ("plain", 64), ("batched", 32)):
         s = tg.Solver(b, precision=prec, mode=mode)
-        row[f"ms_per_iteration_{mode}_fp{prec}"] = _event_ms(torch, lambda: s.solve(0.0, 500), reps=3) / 500
+        ms = _event_ms(torch, lambda: s.solve(0.0, 500), reps=3)
+        row[f"ms_per_iteration_{mode}_fp{prec}"] = ms / 500
+        if prec == 64:
+            row[f"frac_of_measured_fp64_{mode}"] = frac(b, s, ms)
         s.close()
     s = tg.Solver(b, precision=64)
     s.solve(args.tol, args.max_iter)
@@ -589,6 +598,8 @@ def other_workloads(tg, torch, args, peaks):
         row = {}
         s = tg.Solver(b, precision=prec, adapt=(10, 10.0, 2.0))
         row["ms_solve"] = _event_ms(torch, lambda: s.solve(tol, iters), reps=2)
+        if prec == 64:
+            row["solve_frac_of_measured_fp64"] = frac(b, s, row["ms_solve"])
         t0 = time.perf_counter()
         pol = s.polish(1e-9, 100)
         row["ms_polish"] = 1e3 * (time.perf_counter() - t0)

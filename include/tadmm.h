@@ -163,6 +163,18 @@ int tadmm_create(const tadmm_batch* batch, const tadmm_options* opt, tadmm_handl
  * repacks the models in a host buffer that an earlier copy may still read). */
 int tadmm_update(tadmm_handle* h, const tadmm_batch* batch, void* stream);
 
+/* Replaces the per-agent cost data of Eq. (1) — diag Q, diag R, diag Q_T and the
+ * goal state x_ref, each [sum N][nx] (R: [sum N][nu]) in the layouts of
+ * tadmm_batch — from host or device memory (any pointer may be NULL: that array
+ * is kept), e.g. the parameters of a differentiable layer that live on the GPU.
+ * The values are checked on the device by tadmm_create's rules (finite, Q,
+ * Q_T >= 0, R > 0); on a violation the call returns TADMM_EINVAL and the
+ * handle's data is unchanged.  The other inputs (dynamics, x_init, normals,
+ * guesses) and the last solve's results are kept.  Synchronizes `stream`
+ * (to read the check). */
+int tadmm_update_costs(tadmm_handle* h, const double* Qd, const double* Rd, const double* Qfd, const double* x_ref,
+                       void* stream);
+
 /* Runs ADMM from its initial point (consensus copies = w0, duals = 0) until
  * r <= tol and s <= tol or max_iter iterations, for every scenario.
  * r = max |p - w|_inf and s = rho * max |w^{k+1} - w^k|_inf over all pairs,

@@ -61,6 +61,7 @@ def lib():
         L.tadmm_create.argtypes = [C.POINTER(TadmmBatch), C.POINTER(TadmmOptions), C.POINTER(C.c_void_p)]
         L.tadmm_update.argtypes = [C.c_void_p, C.POINTER(TadmmBatch), C.c_void_p]
         L.tadmm_solve.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]
+        L.tadmm_update_costs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_get_solution.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.tadmm_get_counters.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
@@ -175,6 +176,40 @@ class Solver:
         hb = pinned_batch if pinned_batch is not None else _HostBatch(batch)
         self._upd = hb
         _check(lib().tadmm_update(self.h, C.byref(hb.s), C.c_void_p(_stream_ptr(stream))), "tadmm_update")
+
+    def update_costs(self, Qd=None, Rd=None, Qfd=None, x_ref=None, stream=None):
+        """Replaces diag Q, diag R, diag Qf and the goal states (tadmm_update_costs)
+        from numpy arrays or float64 torch tensors (host or CUDA); None keeps an
+        array.  The values are checked on the device."""
+        keep = []
+
+        def ptr(v, shape):
+            if v is None:
+                return None
+            if hasattr(v, "data_ptr"):
+                t = v.detach().to(dtype=__import__("torch").float64).contiguous()
+                assert tuple(t.shape) == shape, (tuple(t.shape), shape)
+                keep.append(t)
+                return C.c_void_p(t.data_ptr())
+            a = np.ascontiguousarray(v, dtype=np.float64).reshape(shape)
+            keep.append(a)
+            return C.c_void_p(a.ctypes.data)
+        na, b = int(self.batch.N.sum()), self.batch
+        _check(lib().tadmm_update_costs(self.h, ptr(Qd, (na, b.nx)), ptr(Rd, (na, b.nu)), ptr(Qfd, (na, b.nx)),
+                                        ptr(x_ref, (na, b.nx)), C.c_void_p(_stream_ptr(stream))),
+               "tadmm_update_costs")
+
+    def polished_states(self, theta_eps: float = 1e-9, stream=None):
+        """Polished states at the final (or polished) active set as a float64
+        CUDA tensor in the packed layout of X (tadmm_backward without a loss
+        gradient, writing straight to device memory)."""
+        import torch
+        X = torch.empty(self.sizes["X"], dtype=torch.float64, device="cuda")
+        st = np.zeros(self.n_scen, dtype=np.int32)
+        _check(lib().tadmm_backward(self.h, None, float(theta_eps), None, None, None, None, C.c_void_p(X.data_ptr()),
+                                    C.c_void_p(st.ctypes.data), None, C.c_void_p(_stream_ptr(stream))),
+               "tadmm_backward")
+        return X, st
 
     def solve(self, tol: float = 1e-4, max_iter: int = 500, stream=None):
         _check(lib().tadmm_solve(self.h, float(tol), int(max_iter), C.c_void_p(_stream_ptr(stream))), "tadmm_solve")
@@ -311,10 +346,12 @@ class TADMMFunction:
     """Differentiable solve: X = TADMMFunction.apply(Qd, Rd, goal, solver, ...).
 
     Qd [sum N, nx] (diag Q per agent, with Qf = qf_tie * Q), Rd [sum N, nu] and
-    goal [sum N, nx] (the goal state x_ref) are float64 torch tensors.  The
-    forward pass uploads them into `solver`'s batch, solves to `tol` and returns
-    the polished states at the final active set (packed layout of X, float64 on
-    the GPU).  The backward pass runs the implicit-KKT adjoint kernel.
+    goal [sum N, nx] (the goal state x_ref) are float64 torch tensors (CUDA or
+    host).  The forward pass writes them into `solver`'s device data
+    (tadmm_update_costs, no host round trip for CUDA tensors), solves to `tol`
+    and returns the polished states at the final active set (packed layout of
+    X, float64 on the GPU).  The backward pass runs the implicit-KKT adjoint
+    kernel.
     """
 
     @staticmethod
@@ -324,17 +361,12 @@ class TADMMFunction:
         class _F(torch.autograd.Function):
             @staticmethod
             def forward(ctx, Qd, Rd, goal, solver, tol, max_iter, qf_tie, theta_eps):
-                b = solver.batch
-                b.Qd = np.ascontiguousarray(Qd.detach().cpu().numpy(), dtype=np.float64)
-                b.Qfd = qf_tie * b.Qd
-                b.Rd = np.ascontiguousarray(Rd.detach().cpu().numpy(), dtype=np.float64)
-                b.x_ref = np.ascontiguousarray(goal.detach().cpu().numpy(), dtype=np.float64)
-                solver.update(b)
+                solver.update_costs(Qd=Qd, Rd=Rd, Qfd=qf_tie * Qd, x_ref=goal)
                 solver.solve(tol, max_iter)
-                out = solver.backward(None, theta_eps=theta_eps)
+                X, st = solver.polished_states(theta_eps=theta_eps)
                 ctx.solver, ctx.qf_tie, ctx.theta_eps = solver, qf_tie, theta_eps
-                ctx.status = out["status"]
-                return torch.from_numpy(out["X_polished"]).to(Qd.device)
+                ctx.status = st
+                return X if Qd.is_cuda else X.cpu()
 
             @staticmethod
             def backward(ctx, grad_X):

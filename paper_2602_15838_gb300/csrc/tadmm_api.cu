@@ -204,7 +204,7 @@ static void free_all(tadmm_handle* h) {
                   h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->phi, h->sx, h->models, h->st_models, h->X, h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
                   h->res,    h->eqp,   h->fact,  h->rho_out, h->rho_chg, h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
-                  h->ex_buf, h->flag,  h->red2, h->hprev, h->hmu, h->hdmu};
+                  h->ex_buf, h->flag,  h->red2, h->hprev, h->hmu, h->hdmu, h->st_costs, h->cost_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* bptrs[] = {h->bwd.act, h->bwd.cnt, h->bwd.amask, h->bwd.psi, h->bwd.kks, h->bwd.pos0, h->bwd.force,
@@ -544,6 +544,63 @@ extern "C" int tadmm_update(tadmm_handle* h, const tadmm_batch* b, void* stream)
   int rc = validate(b, h);
   if (rc) return rc;
   return upload_inputs(h, b, (cudaStream_t)stream);
+}
+
+// Device-side checks of new cost values (float64): finite Q, Qf >= 0, finite
+// x_ref, finite R > 0.  Any violation sets *bad.
+__global__ void k_check_costs(const double* Qd, const double* Rd, const double* Qfd, const double* xr, int64_t nq,
+                              int64_t nr, int32_t* bad) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  bool ok = true;
+  for (int64_t k = tid; k < nq; k += nt) {
+    if (Qd) ok = ok && isfinite(Qd[k]) && Qd[k] >= 0.0;
+    if (Qfd) ok = ok && isfinite(Qfd[k]) && Qfd[k] >= 0.0;
+    if (xr) ok = ok && isfinite(xr[k]);
+  }
+  if (Rd)
+    for (int64_t k = tid; k < nr; k += nt) ok = ok && isfinite(Rd[k]) && Rd[k] > 0.0;
+  if (!ok) atomicOr(bad, 1);
+}
+
+extern "C" int tadmm_update_costs(tadmm_handle* h, const double* Qd, const double* Rd, const double* Qfd,
+                                  const double* x_ref, void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t na = h->tot_agents, nq = na * h->nx, nr = na * h->nu;
+  int rc;
+  if (!h->st_costs) {
+    if ((rc = dmalloc(&h->st_costs, sizeof(double) * (size_t)(3 * nq + nr))) || (rc = dmalloc(&h->cost_flag, 16)))
+      return rc;
+  }
+  // scratch blocks Qd | Rd | Qfd | x_ref, then the staging blocks of the same arrays
+  double* sc[4] = {h->st_costs, h->st_costs + nq, h->st_costs + nq + nr, h->st_costs + 2 * nq + nr};
+  double* sg[4] = {h->st_agent, h->st_agent + nq, h->st_agent + nq + nr, h->st_agent + 3 * nq + nr};
+  const double* src[4] = {Qd, Rd, Qfd, x_ref};
+  const int64_t n[4] = {nq, nr, nq, nq};
+  int which = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (!src[k]) continue;
+    which |= 1 << k;
+    if ((rc = cuda_check(cudaMemcpyAsync(sc[k], src[k], sizeof(double) * n[k], cudaMemcpyDefault, st), "cost copy")))
+      return rc;
+  }
+  if (!which) return TADMM_OK;
+  if ((rc = cuda_check(cudaMemsetAsync(h->cost_flag, 0, sizeof(int32_t), st), "cost flag")))
+    return rc;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (std::max(nq, nr) + 255) / 256));
+  k_check_costs<<<grid, 256, 0, st>>>(
+      Qd ? sc[0] : nullptr, Rd ? sc[1] : nullptr, Qfd ? sc[2] : nullptr, x_ref ? sc[3] : nullptr, nq, nr, h->cost_flag);
+  int32_t* flag_h = (int32_t*)h->pinned;
+  if ((rc = cuda_check(cudaGetLastError(), "cost check")) ||
+      (rc = cuda_check(cudaMemcpyAsync(flag_h, h->cost_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "cost flag")) ||
+      (rc = cuda_check(cudaStreamSynchronize(st), "cost check sync")))
+    return rc;
+  if (*flag_h) return set_error(TADMM_EINVAL, "update_costs: Q and Qf diagonals must be finite and >= 0, R finite and > 0, x_ref finite");
+  for (int k = 0; k < 4; ++k)
+    if ((which >> k) & 1 &&
+        (rc = cuda_check(cudaMemcpyAsync(sg[k], sc[k], sizeof(double) * n[k], cudaMemcpyDeviceToDevice, st), "cost stage")))
+      return rc;
+  TADMM_DISPATCH(h, import_costs(h, which, st));
 }
 
 extern "C" int tadmm_solve(tadmm_handle* h, double tol, int32_t max_iter, void* stream) {

@@ -88,6 +88,8 @@ struct tadmm_handle {
   double* st_a = nullptr;       // [tot_ps][dp]
   double* st_w0 = nullptr;      // [tot_as][dp]
   double* ex_buf = nullptr;     // export scratch
+  double* st_costs = nullptr;   // tadmm_update_costs: float64 staging of Qd, Rd, Qfd, x_ref before validation
+  int32_t* cost_flag = nullptr; //   its device-side validation flag
   size_t ex_bytes = 0;
 
   // plain mode
@@ -134,6 +136,7 @@ struct Impl {
   static int backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev, double* xpol_dev,
                       cudaStream_t st);
   static int relinearize(tadmm_handle* h, cudaStream_t st);
+  static int import_costs(tadmm_handle* h, int which, cudaStream_t st);
   static int polish(tadmm_handle* h, double theta_eps, int max_rounds, double kkt_tol, uint8_t* act_dev, int8_t* W_dev,
                     int32_t* status, int32_t* rounds, cudaStream_t st);
 };

@@ -552,6 +552,20 @@ int Impl<F, NX, NU, DP>::import_inputs(tadmm_handle* h, cudaStream_t st) {
   return cuda_check(cudaGetLastError(), "import kernels");
 }
 
+// Conversion of the per-agent cost arrays alone (bit 0 Qd, 1 Rd, 2 Qfd, 3 x_ref)
+// from their float64 staging into the arithmetic type.
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::import_costs(tadmm_handle* h, int which, cudaStream_t st) {
+  const int64_t na = h->tot_agents;
+  if (which & 1) k_convert<F><<<grid_for(na * NX, 256), 256, 0, st>>>(h->st_agent, (F*)h->Qd, na * NX);
+  if (which & 2) k_convert<F><<<grid_for(na * NU, 256), 256, 0, st>>>(h->st_agent + na * NX, (F*)h->Rd, na * NU);
+  if (which & 4)
+    k_convert<F><<<grid_for(na * NX, 256), 256, 0, st>>>(h->st_agent + na * NX + na * NU, (F*)h->Qfd, na * NX);
+  if (which & 8)
+    k_convert<F><<<grid_for(na * NX, 256), 256, 0, st>>>(h->st_agent + 3 * na * NX + na * NU, (F*)h->x_ref, na * NX);
+  return cuda_check(cudaGetLastError(), "cost import kernels");
+}
+
 template <typename F, int NX, int NU, int DP>
 int Impl<F, NX, NU, DP>::relinearize(tadmm_handle* h, cudaStream_t st) {
   Dev<F> D = make_dev<F>(h);

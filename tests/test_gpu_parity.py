@@ -725,3 +725,37 @@ def test_graph_mode_several_agents_per_warp(tg):
         assert rel(gh[k]["X"], o["X"]) <= 1e-9, k
         assert rel(gh[k]["theta"], o["theta"]) <= 1e-9, k
         assert int(ch["eqp"][k]) == o["as_iters"], k
+
+
+def test_update_costs_from_device_tensors(tg):
+    """tadmm_update_costs with CUDA tensors (and with numpy arrays) gives
+    bitwise the results of tadmm_update with the same values; invalid values
+    (a negative R entry) are rejected with EINVAL and leave the handle's data
+    unchanged."""
+    import torch
+    b = make_workload("mixed", n_scen=12)
+    rng = np.random.default_rng(3)
+    Qd = b.Qd * (1.0 + 0.2 * rng.random(b.Qd.shape))
+    Rd = b.Rd * (1.0 + 0.2 * rng.random(b.Rd.shape))
+    xr = b.x_ref + 0.1 * rng.standard_normal(b.x_ref.shape)
+    bb = b.subset(list(range(b.n_scen)))
+    bb.Qd, bb.Qfd, bb.Rd, bb.x_ref = Qd, 10.0 * Qd, Rd, xr
+    ref, cref = gpu_run(tg, bb, 0.0, 6)
+    for dev in (True, False):
+        s = tg.Solver(b)
+        cv = (lambda a: torch.tensor(a, device="cuda")) if dev else (lambda a: a)
+        s.update_costs(Qd=cv(Qd), Rd=cv(Rd), Qfd=cv(10.0 * Qd), x_ref=cv(xr))
+        s.solve(0.0, 6)
+        g = s.split(s.solution())
+        for k in range(b.n_scen):
+            assert np.array_equal(g[k]["X"], ref[k]["X"]), (dev, k)
+            assert np.array_equal(g[k]["theta"], ref[k]["theta"]), (dev, k)
+        bad = Rd.copy()
+        bad[3, 1] = -1.0
+        with pytest.raises(tg.TadmmError):
+            s.update_costs(Rd=cv(bad))
+        s.solve(0.0, 6)
+        g2 = s.split(s.solution())
+        for k in range(b.n_scen):
+            assert np.array_equal(g2[k]["X"], ref[k]["X"]), (dev, k)
+        s.close()
