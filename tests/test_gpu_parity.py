@@ -759,3 +759,28 @@ def test_update_costs_from_device_tensors(tg):
         for k in range(b.n_scen):
             assert np.array_equal(g2[k]["X"], ref[k]["X"]), (dev, k)
         s.close()
+
+
+def test_mixed_batch_converged_scenarios_exact_active_sets_fp64(tg):
+    """The scenarios of a 512-scenario sample of the mixed batch that reach
+    r, s <= 1e-4 within 500 iterations after more than one iteration (those
+    converging at the first x-update have no active halfspace): the oracle run
+    to the same tolerance stops at the same iteration with the same status,
+    states within 1e-9, the same set of active halfspaces (theta > 0; on most
+    of these the collision rows end inactive, the 478-iteration one holds
+    active ones) and the same working sets except degenerate entries."""
+    b = make_workload("mixed", n_scen=512)
+    g, _ = gpu_run(tg, b, 1e-4, 500)
+    done = [k for k in range(b.n_scen) if g[k]["status"] == tg.CONVERGED and g[k]["iters"] > 1]
+    done = sorted(done, key=lambda k: int(b.N[k]) * g[k]["iters"])
+    assert len(done) >= 6
+    assert any(int((g[k]["theta"] > 0).sum()) > 0 for k in done)
+    assert all(int((g[k]["W"] != 0).sum()) > 0 for k in done)
+    for k in done:
+        o = oracle.admm(b, k, tol=1e-4, max_iter=500, nthreads=8)
+        assert o["status"] == oracle.CONVERGED and o["iters"] == g[k]["iters"], k
+        assert rel(g[k]["X"], o["X"]) <= 1e-9, k
+        assert rel(g[k]["theta"], o["theta"]) <= 1e-9, k
+        assert np.array_equal(g[k]["theta"] > 0, o["theta"] > 0), k
+        ok, _ = nondegenerate_w_equal(g[k]["W"], o, b, k)
+        assert ok, k
