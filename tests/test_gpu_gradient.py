@@ -358,3 +358,33 @@ def test_autograd_function(tg):
                 checked += 1
     assert checked >= 30
     s.close()
+
+
+def test_gradient_3d_model_matches_oracle(tg):
+    """The 3D double integrator (nx = 6, nu = 3) of the swarm workload with 5
+    agents, T = 8: the implicit-KKT gradient of a position-tracking loss at
+    the GPU's final active set (polished to KKT) against the oracle's
+    dense-KKT gradient at the same set (1e-6), and the polished states
+    (1e-9)."""
+    b = make_workload("swarm3d", N_override=5, T_override=8)
+    N, T = int(b.N[0]), int(b.T[0])
+    rng = np.random.default_rng(8)
+    targets = rng.uniform(-3.0, 3.0, size=(N * T, 3))
+    s = tg.Solver(b, precision=64)
+    s.solve(1e-6, 3000)
+    pol = s.polish(1e-9, 50)
+    assert pol["status"][0] == 0
+    X = s.backward(None)["X_polished"].reshape(N, T + 1, 6)
+    gX = np.zeros_like(X)
+    gX[:, 1:, :3] = 2 * (X[:, 1:, :3] - targets.reshape(N, T, 3))
+    g = s.backward(gX.ravel())
+    P = N * (N - 1) // 2
+    act = pol["act"].reshape(P, T)
+    W = pol["W"].reshape(N, T, 3)
+    ref = oracle.global_gradient(b, 0, act, W, targets, qf_tie=10.0)
+    assert act.sum() + (W != 0).sum() > 0
+    assert _rel(X, ref["X"]) <= 1e-9
+    assert _rel(g["gQ"] + 10.0 * g["gQf"], ref["gQ"]) <= 1e-6
+    assert _rel(g["gR"], ref["gR"]) <= 1e-6
+    assert _rel(g["gGoal"], ref["gGoal"]) <= 1e-6
+    s.close()
