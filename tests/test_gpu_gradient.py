@@ -388,3 +388,73 @@ def test_gradient_3d_model_matches_oracle(tg):
     assert _rel(g["gR"], ref["gR"]) <= 1e-6
     assert _rel(g["gGoal"], ref["gGoal"]) <= 1e-6
     s.close()
+
+
+def test_backward_after_graph_and_plain_mode_solves(tg):
+    """The adjoint reads the final iterate (its theta slot and working sets)
+    of whichever execution mode solved: after a graph-mode or a plain-mode
+    solve it gives bitwise the gradients and polished states of the
+    persistent kernel's solve."""
+    b = _case(6, 12, n_scen=3)
+    res = {}
+    for mode in ("batched", "graph", "plain"):
+        s = tg.Solver(b, precision=64, mode=mode)
+        s.solve(0.0, 30)
+        X = s.backward(None)["X_polished"]
+        _, gX = _loss_grad(b, X, b.targets)
+        res[mode] = (X, s.backward(gX))
+        s.close()
+    for mode in ("graph", "plain"):
+        assert np.array_equal(res[mode][0], res["batched"][0]), mode
+        for key in ("gQ", "gQf", "gR", "gGoal"):
+            assert np.array_equal(res[mode][1][key], res["batched"][1][key]), (mode, key)
+
+
+def test_polish_and_gradient_with_listed_pairs(tg):
+    """Listed (4-nearest-neighbour) coupling: the polished active set is
+    certified optimal by the oracle and the gradient matches its dense-KKT
+    gradient (1e-6) at that set."""
+    from instances import nearest_neighbour_pairs
+    b = nearest_neighbour_pairs(make_workload("diff", n_scen=4), 4)
+    s = tg.Solver(b, precision=64, adapt=(10, 10.0, 2.0))
+    s.solve(1e-6, 3000)
+    pol = s.polish(1e-9, 100)
+    X = s.backward(None)["X_polished"]
+    _, gX = _loss_grad(b, X, b.targets)
+    g = s.backward(gX)
+    to = uo = 0
+    certified = 0
+    for k in range(b.n_scen):
+        N, T, P = int(b.N[k]), int(b.T[k]), int(b.P[k])
+        act = pol["act"][to:to + P * T].reshape(P, T)
+        W = pol["W"][uo:uo + N * T * b.nu].reshape(N, T, b.nu)
+        tk = b.targets[int(b.agentstep_off[k]):int(b.agentstep_off[k + 1])]
+        ref = oracle.global_gradient(b, k, act, W, tk, qf_tie=10.0)
+        if pol["status"][k] == 0:
+            assert _certify_listed(b, k, ref, act, W), k
+            certified += 1
+        sl = slice(int(b.agent_off[k]), int(b.agent_off[k + 1]))
+        assert _rel(g["gQ"][sl] + 10.0 * g["gQf"][sl], ref["gQ"]) <= 1e-6, k
+        assert _rel(g["gR"][sl], ref["gR"]) <= 1e-6, k
+        assert _rel(g["gGoal"][sl], ref["gGoal"]) <= 1e-6, k
+        to += P * T
+        uo += N * T * b.nu
+    assert certified >= 3
+    s.close()
+
+
+def _certify_listed(b, k, ref, act, W, tol=1e-8):
+    """KKT conditions at the oracle's polished point with the scenario's listed pairs."""
+    N, T, P = int(b.N[k]), int(b.T[k]), int(b.P[k])
+    pl = np.asarray(b.pairs_of(k)).reshape(P, 2)
+    a = b.a[b.pairstep_off[k]:b.pairstep_off[k + 1]].reshape(P, T, b.dp)
+    X, U = ref["X"], ref["U"]
+    slack = (a * (X[pl[:, 0], 1:, :b.dp] - X[pl[:, 1], 1:, :b.dp])).sum(-1) - b.d_min[k]
+    scale = max(1.0, np.abs(ref["mu_h"]).max(), np.abs(ref["mu_u"]).max())
+    ok = slack.min() >= -tol * max(1.0, b.d_min[k])
+    ok = ok and (U - b.umax).max() <= tol and (b.umin - U).max() <= tol
+    if act.any():
+        ok = ok and ref["mu_h"][act.astype(bool)].min() >= -tol * scale
+    if (W != 0).any():
+        ok = ok and ref["mu_u"][W != 0].min() >= -tol * scale
+    return bool(ok)
