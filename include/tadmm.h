@@ -208,6 +208,31 @@ int tadmm_get_counters(tadmm_handle* h, int64_t* eqp, int64_t* fact, int64_t* pa
  * caller's data. */
 int tadmm_relinearize(tadmm_handle* h, void* stream);
 
+/* Sequential-QP loop over the linearization (an extension beyond the single
+ * linearized QP, with the termination rule of Sec. V.A: relative objective
+ * change and collision-free at every time step).  Outer step m = 1, 2, ...
+ * runs tadmm_solve(tol, max_iter) and then, per scenario, forms the objective
+ * J_m of Eq. (1) at the solution (every term, t = 0 included) and the smallest
+ * pair distance D_m = min |p_it - p_jt| over the coupled pairs and t = 1..T
+ * (float64).  A scenario stops at step m when its solve converged, m >= 2,
+ * |J_m - J_{m-1}| <= obj_rtol |J_{m-1}| and D_m >= d_min - dist_tol; the others
+ * are re-linearized at their solution as tadmm_relinearize does, for at most
+ * max_outer steps.  A scenario that stopped keeps its data, so its re-solves in
+ * later steps reproduce its solution bit for bit (the work is repeated: every
+ * solve runs all scenarios); afterwards tadmm_get_solution returns each
+ * scenario's solution at the step where it stopped (or the last one).
+ *   dist_tol < 0: 2 sqrt(dp) tol (a converged solve leaves each position within
+ *               tol, per component, of consensus copies that satisfy the
+ *               halfspace exactly)
+ *   outer       [n_scen] outer steps taken (the stopping step)
+ *   sqp_status  [n_scen] TADMM_CONVERGED when the rule was met, else
+ *               TADMM_NOT_CONVERGED (max_outer reached)
+ *   objective   [n_scen] J at the last step taken;  min_dist [n_scen] D there
+ * Outputs are host buffers, any may be NULL.  Synchronizes `stream` after
+ * every step (to read the measures).  tadmm_update restores the caller's data. */
+int tadmm_sqp(tadmm_handle* h, double tol, int32_t max_iter, int32_t max_outer, double obj_rtol, double dist_tol,
+              int32_t* outer, int32_t* sqp_status, double* objective, double* min_dist, void* stream);
+
 /* Penalty of each scenario at the end of the last solve and the number of
  * times residual balancing changed it (host buffers, synchronous; either may
  * be NULL).  Without residual balancing: the input rho and 0. */

@@ -338,3 +338,63 @@ def relinearize(batch, X_list):
             rows = a[po[k] + pk * T: po[k] + (pk + 1) * T]
             rows[ok] = d[ok] / nr[ok, None]
     return dataclasses.replace(batch, a=a, w0=w0)
+
+
+def objective(batch, k: int, X, U) -> float:
+    """Objective of Eq. (1) for scenario k at states X [N, T+1, nx] and inputs
+    U [N, T, nu]: every agent's sum over t < T of (x_t - x_ref)' Q (x_t - x_ref)
+    + u_t' R u_t, plus (x_T - x_ref)' Q_T (x_T - x_ref).  The t = 0 term is kept
+    (it is constant in the decision variables).  Plain numpy sums."""
+    ao = batch.agent_off
+    sl = slice(int(ao[k]), int(ao[k + 1]))
+    X = np.asarray(X, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    e = X - batch.x_ref[sl][:, None, :]                          # [N, T+1, nx]
+    stage = (e[:, :-1, :] ** 2 * batch.Qd[sl][:, None, :]).sum()
+    inputs = (U ** 2 * batch.Rd[sl][:, None, :]).sum()
+    final = (e[:, -1, :] ** 2 * batch.Qfd[sl]).sum()
+    return float(stage + inputs + final)
+
+
+def min_distance(batch, k: int, X) -> float:
+    """Smallest Euclidean distance |p_it - p_jt| over the coupled pairs of
+    scenario k and the constrained steps t = 1..T (inf without pairs)."""
+    X = np.asarray(X, dtype=np.float64)
+    pos = X[:, 1:, :batch.dp]
+    best = np.inf
+    for i, j in batch.pairs_of(k):
+        d = pos[i] - pos[j]
+        best = min(best, float(np.sqrt((d * d).sum(axis=1)).min()))
+    return best
+
+
+def sqp(batch, k: int = 0, tol=1e-4, max_iter=500, max_outer=10, obj_rtol=1e-4, dist_tol=None, **admm_kw):
+    """Sequential linearize-and-solve loop over the collision constraint of
+    Eq. (1) for scenario k: outer step m solves the halfspace-linearized QP by
+    ADMM (`admm`, options passed through), then stops when the solve converged,
+    m >= 2, the objective changed by at most obj_rtol relative to step m - 1
+    and every pair is at least d_min - dist_tol apart at t = 1..T (the
+    termination rule of Sec. V.A: relative objective change and collision-free
+    at every step), else re-linearizes at the solution (`relinearize`) and
+    repeats, for at most max_outer steps.  dist_tol None: 2 sqrt(dp) tol (a
+    converged solve's positions are within tol of consensus copies that satisfy
+    the halfspace exactly).  Returns the last step's ADMM result with `outer`
+    (steps taken), `sqp_status` (0 stopped by the rule, 1 max_outer reached),
+    `objective`, `min_dist` and `objectives` (one per step)."""
+    if dist_tol is None:
+        dist_tol = 2.0 * np.sqrt(batch.dp) * tol
+    b = batch.subset([k])
+    d_min = float(b.d_min[0])
+    J_prev, Js = None, []
+    for m in range(1, max_outer + 1):
+        o = admm(b, 0, tol=tol, max_iter=max_iter, **admm_kw)
+        J = objective(b, 0, o["X"], o["U"])
+        D = min_distance(b, 0, o["X"])
+        Js.append(J)
+        done = (o["status"] == CONVERGED and J_prev is not None and abs(J - J_prev) <= obj_rtol * abs(J_prev)
+                and D >= d_min - dist_tol)
+        if done or m == max_outer:
+            break
+        b = relinearize(b, [o["X"]])
+        J_prev = J
+    return dict(o, outer=m, sqp_status=0 if done else 1, objective=J, min_dist=D, objectives=Js)

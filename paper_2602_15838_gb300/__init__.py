@@ -67,6 +67,8 @@ def lib():
         L.tadmm_get_counters.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
         L.tadmm_get_penalty.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
         L.tadmm_relinearize.argtypes = [C.c_void_p, C.c_void_p]
+        L.tadmm_sqp.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_double, _i32p, _i32p,
+                                C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]
         L.tadmm_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, _i32p, _i32p, _i32p]
         L.tadmm_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -304,6 +306,25 @@ class Solver:
         consensus positions) at the last solution; the next solve() solves the
         new QP (one outer step of a linearize-and-solve loop)."""
         _check(lib().tadmm_relinearize(self.h, C.c_void_p(_stream_ptr(stream))), "tadmm_relinearize")
+
+    def sqp(self, tol=1e-4, max_iter=500, max_outer=10, obj_rtol=1e-4, dist_tol=-1.0, stream=None):
+        """Sequential linearize-and-solve loop with the termination rule of
+        Sec. V.A (relative objective change <= obj_rtol between outer steps and
+        every pair at least d_min - dist_tol apart; dist_tol < 0: 2 sqrt(dp) tol),
+        at most max_outer steps.  Returns per-scenario numpy arrays: outer
+        (steps taken), status (CONVERGED when the rule was met), objective and
+        min_dist at the last step; solution() then gives the stopping step's
+        solution of every scenario."""
+        n = self.n_scen
+        outer = np.zeros(n, dtype=np.int32)
+        stat = np.zeros(n, dtype=np.int32)
+        J = np.zeros(n, dtype=np.float64)
+        D = np.zeros(n, dtype=np.float64)
+        _check(lib().tadmm_sqp(self.h, float(tol), int(max_iter), int(max_outer), float(obj_rtol), float(dist_tol),
+                               outer.ctypes.data_as(_i32p), stat.ctypes.data_as(_i32p),
+                               J.ctypes.data_as(C.POINTER(C.c_double)), D.ctypes.data_as(C.POINTER(C.c_double)),
+                               C.c_void_p(_stream_ptr(stream))), "tadmm_sqp")
+        return dict(outer=outer, status=stat, objective=J, min_dist=D)
 
     def penalty(self):
         """Final rho per scenario and the number of residual-balancing changes."""

@@ -204,7 +204,7 @@ static void free_all(tadmm_handle* h) {
                   h->Qfd,    h->x_init, h->x_ref, h->a,        h->w0,         h->theta, h->phi, h->sx, h->models, h->st_models, h->X, h->h,
                   h->U,      h->Us,    h->cache, h->Wm,        h->Cm,         h->status, h->iters, h->cur_lvl,
                   h->res,    h->eqp,   h->fact,  h->rho_out, h->rho_chg, h->queue,     h->st_model,   h->st_agent, h->st_a, h->st_w0,
-                  h->ex_buf, h->flag,  h->red2, h->hprev, h->hmu, h->hdmu, h->st_costs, h->cost_flag};
+                  h->ex_buf, h->flag,  h->red2, h->hprev, h->hmu, h->hdmu, h->st_costs, h->cost_flag, h->sqp_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* bptrs[] = {h->bwd.act, h->bwd.cnt, h->bwd.amask, h->bwd.psi, h->bwd.kks, h->bwd.pos0, h->bwd.force,
@@ -688,7 +688,67 @@ extern "C" int tadmm_relinearize(tadmm_handle* h, void* stream) {
   if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
   if (!h->solved) return set_error(TADMM_ESTATE, "relinearize before solve");
   cudaStream_t st = (cudaStream_t)stream;
-  TADMM_DISPATCH(h, relinearize(h, st));
+  TADMM_DISPATCH(h, relinearize(h, nullptr, st));
+}
+
+extern "C" int tadmm_sqp(tadmm_handle* h, double tol, int32_t max_iter, int32_t max_outer, double obj_rtol,
+                         double dist_tol, int32_t* outer, int32_t* sqp_status, double* objective, double* min_dist,
+                         void* stream) {
+  if (!h) return set_error(TADMM_EINVAL, "handle is NULL");
+  if (max_outer < 1) return set_error(TADMM_EINVAL, "max_outer must be >= 1");
+  if (!(obj_rtol >= 0.0) || !std::isfinite(obj_rtol)) return set_error(TADMM_EINVAL, "obj_rtol must be finite and >= 0");
+  if (std::isnan(dist_tol) || std::isinf(dist_tol)) return set_error(TADMM_EINVAL, "dist_tol must be finite");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return set_error(TADMM_EINVAL, "tol must be finite and >= 0");
+  if (max_iter < 1) return set_error(TADMM_EINVAL, "max_iter must be >= 1");
+  if (dist_tol < 0.0) dist_tol = 2.0 * std::sqrt((double)h->dp) * tol;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = h->n_scen;
+  int rc;
+  if (!h->sqp_buf && (rc = dmalloc(&h->sqp_buf, sizeof(double) * 2 * n + n + 16))) return rc;
+  double* J_dev = h->sqp_buf;
+  double* D_dev = h->sqp_buf + n;
+  uint8_t* keep_dev = (uint8_t*)(h->sqp_buf + 2 * n);
+  std::vector<double> J(n), D(n), Jp(n, 0.0), Jout(n, 0.0), Dout(n, 0.0);
+  std::vector<int32_t> stat(n), steps(n, 0);
+  std::vector<uint8_t> done(n, 0);
+  int n_done = 0;
+  for (int m = 1; m <= max_outer; ++m) {
+    if ((rc = tadmm_solve(h, tol, max_iter, stream))) return rc;
+    auto measure = [&]() -> int { TADMM_DISPATCH(h, sqp_measure(h, J_dev, D_dev, st)); };
+    if ((rc = measure()) ||
+        (rc = cuda_check(cudaMemcpyAsync(J.data(), J_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "objective")) ||
+        (rc = cuda_check(cudaMemcpyAsync(D.data(), D_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "distance")) ||
+        (rc = cuda_check(cudaMemcpyAsync(stat.data(), h->status, 4 * n, cudaMemcpyDeviceToHost, st), "status")) ||
+        (rc = cuda_check(cudaStreamSynchronize(st), "sqp sync")))
+      return rc;
+    for (int s = 0; s < n; ++s) {
+      if (done[s]) continue;
+      steps[s] = m;
+      Jout[s] = J[s];
+      Dout[s] = D[s];
+      if (stat[s] == TADMM_CONVERGED && m >= 2 && std::fabs(J[s] - Jp[s]) <= obj_rtol * std::fabs(Jp[s]) &&
+          D[s] >= h->meta_h[s].d - dist_tol) {
+        done[s] = 1;
+        ++n_done;
+      }
+      Jp[s] = J[s];
+    }
+    if (n_done == n || m == max_outer) break;
+    // Scenarios that met the rule keep their linearization (their re-solve in
+    // the next step reproduces their solution bit for bit); the others are
+    // re-linearized at their solution.
+    auto relin = [&]() -> int { TADMM_DISPATCH(h, relinearize(h, keep_dev, st)); };
+    if ((rc = cuda_check(cudaMemcpyAsync(keep_dev, done.data(), n, cudaMemcpyHostToDevice, st), "sqp mask")) ||
+        (rc = relin()) || (rc = cuda_check(cudaStreamSynchronize(st), "sqp mask sync")))
+      return rc;
+  }
+  for (int s = 0; s < n; ++s) {
+    if (outer) outer[s] = steps[s];
+    if (sqp_status) sqp_status[s] = done[s] ? TADMM_CONVERGED : TADMM_NOT_CONVERGED;
+    if (objective) objective[s] = Jout[s];
+    if (min_dist) min_dist[s] = Dout[s];
+  }
+  return TADMM_OK;
 }
 
 extern "C" int tadmm_get_penalty(tadmm_handle* h, double* rho_final, int32_t* rho_changes) {

@@ -90,6 +90,7 @@ struct tadmm_handle {
   double* ex_buf = nullptr;     // export scratch
   double* st_costs = nullptr;   // tadmm_update_costs: float64 staging of Qd, Rd, Qfd, x_ref before validation
   int32_t* cost_flag = nullptr; //   its device-side validation flag
+  double* sqp_buf = nullptr;     // tadmm_sqp: [n_scen] objective | [n_scen] min distance | [n_scen] uint8 keep mask
   size_t ex_bytes = 0;
 
   // plain mode
@@ -135,7 +136,8 @@ struct Impl {
   static int max_ctas_per_sm(int tpc, int variant, const tadmm_handle* h);
   static int backward(tadmm_handle* h, const double* gX_dev, double theta_eps, double* gout_dev, double* xpol_dev,
                       cudaStream_t st);
-  static int relinearize(tadmm_handle* h, cudaStream_t st);
+  static int relinearize(tadmm_handle* h, const uint8_t* keep, cudaStream_t st);
+  static int sqp_measure(tadmm_handle* h, double* J, double* dmin, cudaStream_t st);
   static int import_costs(tadmm_handle* h, int which, cudaStream_t st);
   static int polish(tadmm_handle* h, double theta_eps, int max_rounds, double kkt_tol, uint8_t* act_dev, int8_t* W_dev,
                     int32_t* status, int32_t* rounds, cudaStream_t st);

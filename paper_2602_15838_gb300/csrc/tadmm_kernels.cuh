@@ -342,11 +342,12 @@ __global__ void k_import_a(const ScenMeta* __restrict__ meta, const int32_t* __r
 // with correctly rounded operations (no contraction), as in the oracle.
 template <typename F, int NX, int DP>
 __global__ void k_relin_a(Dev<F> D, F* __restrict__ a_out, const int32_t* __restrict__ pair_scen,
-                          int64_t tot_pairs) {
+                          int64_t tot_pairs, const uint8_t* __restrict__ keep) {
   const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int tm1 = blockIdx.y;
   if (gp >= tot_pairs) return;
   const int sc = pair_scen[gp];
+  if (keep && keep[sc]) return;
   const ScenMeta s = D.meta[sc];
   if (tm1 >= s.T) return;
   const int lp = (int)(gp - s.pair_off);
@@ -371,10 +372,11 @@ __global__ void k_relin_a(Dev<F> D, F* __restrict__ a_out, const int32_t* __rest
 // The next solve's initial consensus positions: the final iterate's positions.
 template <typename F, int NX, int DP>
 __global__ void k_relin_w0(Dev<F> D, F* __restrict__ w0_out, const int32_t* __restrict__ agent_scen,
-                           int64_t tot_agents) {
+                           int64_t tot_agents, const uint8_t* __restrict__ keep) {
   const int64_t ga = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (ga >= tot_agents) return;
   const int sc = agent_scen[ga];
+  if (keep && keep[sc]) return;
   const ScenMeta s = D.meta[sc];
   const int i = (int)(ga - s.agent_off);
   const F* X = D.X + (size_t)(D.cur_lvl[sc] & 1) * D.tot_xs * NX + s.xs_off * NX;
@@ -382,6 +384,69 @@ __global__ void k_relin_w0(Dev<F> D, F* __restrict__ w0_out, const int32_t* __re
 #pragma unroll
     for (int c = 0; c < DP; ++c)
       w0_out[s.as_off * DP + ((size_t)tm1 * DP + c) * s.N + i] = X[((size_t)(tm1 + 1) * NX + c) * s.N + i];
+}
+
+// Termination test of a sequential-QP loop over the linearization (the rule of
+// Sec. V.A: relative objective change and collision-free at every step), one
+// CTA per scenario at the final iterate of the last solve: J = the objective of
+// Eq. (1), every agent's sum over t < T of (x_t - x_ref)' Q (x_t - x_ref) +
+// u_t' R u_t plus (x_T - x_ref)' Q_T (x_T - x_ref), and dmin = the smallest
+// |p_it - p_jt| over the coupled pairs and t = 1..T (+inf without pairs).  In
+// float64 with a fixed reduction order, so repeated calls agree bit for bit.
+template <typename F, int NX, int NU, int DP>
+__global__ void __launch_bounds__(256) k_sqp_measure(Dev<F> D, double* __restrict__ J, double* __restrict__ dmin) {
+  constexpr int NT = 256;
+  __shared__ double rs[NT], rm[NT];
+  const int sc = blockIdx.x;
+  const ScenMeta s = D.meta[sc];
+  const int N = s.N, T = s.T;
+  const F* X = D.X + (size_t)(D.cur_lvl[sc] & 1) * D.tot_xs * NX + s.xs_off * NX;
+  const F* U = D.U + s.as_off * NU;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)N * (T + 1); e += NT) {
+    const int i = (int)(e % N), t = (int)(e / N);
+    const int64_t ga = s.agent_off + i;
+    const F* w = (t < T ? D.Qd : D.Qfd) + ga * NX;
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      const double d = __dadd_rn(double(X[((size_t)t * NX + r) * N + i]), -double(D.x_ref[ga * NX + r]));
+      acc = __dadd_rn(acc, __dmul_rn(double(w[r]), __dmul_rn(d, d)));
+    }
+    if (t < T)
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        const double u = double(U[((size_t)t * NU + c) * N + i]);
+        acc = __dadd_rn(acc, __dmul_rn(double(D.Rd[ga * NU + c]), __dmul_rn(u, u)));
+      }
+  }
+  double mn = __longlong_as_double(0x7FF0000000000000ll);  // +inf
+  for (int64_t e = threadIdx.x; e < (int64_t)s.P * T; e += NT) {
+    const int lp = (int)(e % s.P), tm1 = (int)(e / s.P);
+    const int pk = D.pairs[s.pair_off + lp];
+    const int i = pk & 0xFFFF, j = pk >> 16;
+    double n2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < DP; ++c) {
+      const size_t ro = ((size_t)(tm1 + 1) * NX + c) * N;
+      const double d = __dadd_rn(double(X[ro + i]), -double(X[ro + j]));
+      n2 = __dadd_rn(n2, __dmul_rn(d, d));
+    }
+    mn = fmin(mn, __dsqrt_rn(n2));
+  }
+  rs[threadIdx.x] = acc;
+  rm[threadIdx.x] = mn;
+  __syncthreads();
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      rs[threadIdx.x] = __dadd_rn(rs[threadIdx.x], rs[threadIdx.x + w]);
+      rm[threadIdx.x] = fmin(rm[threadIdx.x], rm[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    J[sc] = rs[0];
+    dmin[sc] = rm[0];
+  }
 }
 
 // w0: caller [agent-step][dp] (agent-major, then t) -> internal [T][DP][N]
@@ -567,16 +632,22 @@ int Impl<F, NX, NU, DP>::import_costs(tadmm_handle* h, int which, cudaStream_t s
 }
 
 template <typename F, int NX, int NU, int DP>
-int Impl<F, NX, NU, DP>::relinearize(tadmm_handle* h, cudaStream_t st) {
+int Impl<F, NX, NU, DP>::relinearize(tadmm_handle* h, const uint8_t* keep, cudaStream_t st) {
   Dev<F> D = make_dev<F>(h);
   int tmax = 0;
   for (const ScenMeta& m : h->meta_h) tmax = std::max(tmax, m.T);
   if (h->tot_pairs > 0)
     k_relin_a<F, NX, DP><<<dim3(grid_for(h->tot_pairs, 128, 1 << 30), tmax), 128, 0, st>>>(D, (F*)h->a, h->pair_scen,
-                                                                                          h->tot_pairs);
+                                                                                          h->tot_pairs, keep);
   k_relin_w0<F, NX, DP><<<grid_for(h->tot_agents, 128, 1 << 30), 128, 0, st>>>(D, (F*)h->w0, h->agent_scen,
-                                                                              h->tot_agents);
+                                                                              h->tot_agents, keep);
   return cuda_check(cudaGetLastError(), "relinearization kernels");
+}
+
+template <typename F, int NX, int NU, int DP>
+int Impl<F, NX, NU, DP>::sqp_measure(tadmm_handle* h, double* J, double* dmin, cudaStream_t st) {
+  k_sqp_measure<F, NX, NU, DP><<<h->n_scen, 256, 0, st>>>(make_dev<F>(h), J, dmin);
+  return cuda_check(cudaGetLastError(), "objective kernel");
 }
 
 template <typename F, int NX, int NU, int DP>

@@ -784,3 +784,54 @@ def test_mixed_batch_converged_scenarios_exact_active_sets_fp64(tg):
         assert np.array_equal(g[k]["theta"] > 0, o["theta"] > 0), k
         ok, _ = nondegenerate_w_equal(g[k]["W"], o, b, k)
         assert ok, k
+
+
+# ------------------------------------------------------------------ sequential QP loop
+def _sqp_against_oracle(tg, b, solver_kw, admm_kw, tol, max_iter, max_outer):
+    s = tg.Solver(b, **solver_kw)
+    r = s.sqp(tol=tol, max_iter=max_iter, max_outer=max_outer)
+    g = s.split(s.solution())
+    s.close()
+    for k in range(b.n_scen):
+        o = oracle.sqp(b, k, tol=tol, max_iter=max_iter, max_outer=max_outer, **admm_kw)
+        assert int(r["outer"][k]) == o["outer"] and int(r["status"][k]) == o["sqp_status"], k
+        assert g[k]["iters"] == o["iters"] and g[k]["status"] == o["status"], k
+        assert abs(r["objective"][k] - o["objective"]) <= 1e-9 * abs(o["objective"]), k
+        assert abs(r["min_dist"][k] - o["min_dist"]) <= 1e-9, k
+        assert rel(g[k]["X"], o["X"]) <= 1e-8 and rel(g[k]["U"], o["U"]) <= 1e-8, k
+    return r
+
+
+@pytest.mark.parametrize("mode", ["batched", "graph", "plain"])
+def test_sqp_loop_on_a_binding_crossing_matches_oracle(tg, mode):
+    """The linearize-and-solve loop with the termination rule of Sec. V.A on
+    the 2-agent crossing at d_min = 1.5 (the collision constraint binds): the
+    same number of outer steps, the same ADMM stopping iteration at the last
+    step, and the same objective, smallest distance and trajectory as the
+    oracle's loop, in every execution mode."""
+    import dataclasses
+    p = dataclasses.replace(make_workload("pair"), d_min=np.array([1.5]))
+    r = _sqp_against_oracle(tg, p, dict(mode=mode), {}, 1e-6, 5000, 20)
+    assert r["status"][0] == tg.CONVERGED and r["outer"][0] >= 3
+    assert r["min_dist"][0] >= 1.5 - 2 * np.sqrt(2) * 1e-6
+
+
+def test_sqp_loop_per_scenario_stopping_matches_oracle(tg):
+    """Mixed scenarios (3, 6 and 11 agents) under residual balancing stop at
+    different outer steps (6, 8 and 5 in the oracle): scenarios that stopped
+    keep their linearization while the rest go on, and every scenario's result
+    equals the oracle's loop run on it alone."""
+    b = make_workload("mixed", n_scen=4).subset([0, 2, 3])
+    adapt = (10, 10.0, 2.0)
+    r = _sqp_against_oracle(tg, b, dict(adapt=adapt), dict(adapt=adapt), 1e-4, 2000, 10)
+    assert (r["status"] == tg.CONVERGED).all()
+    assert len(set(r["outer"].tolist())) == 3
+
+
+def test_sqp_rejects_bad_arguments(tg):
+    s = tg.Solver(make_workload("pair"))
+    for kw in (dict(max_outer=0), dict(obj_rtol=-1.0), dict(obj_rtol=float("nan")), dict(dist_tol=float("inf")),
+               dict(tol=-1.0), dict(max_iter=0)):
+        with pytest.raises(tg.TadmmError, match="tadmm_sqp"):
+            s.sqp(**kw)
+    s.close()

@@ -782,3 +782,93 @@ def test_gradient_with_dependent_active_rows_matches_central_differences(consist
             assert abs(fd - gr["gR"][i, c]) <= 1e-5 * max(1.0, abs(fd)), (i, c, fd, gr["gR"][i, c])
             checked += 1
     assert checked == 50
+
+
+# ------------------------------------------------------------------ sequential QP over the linearization
+def _pair_with_active_collision():
+    """The 2-agent crossing with d_min = 1.5 (the generated guess passes the
+    agents within 0.97 of each other, so the collision constraint binds)."""
+    p = make_workload("pair")
+    return dataclasses.replace(p, d_min=np.array([1.5]))
+
+
+def test_objective_matches_the_global_qp_objective():
+    """oracle.objective (numpy) against the C global QP's own objective, which
+    leaves out the constant t = 0 state term."""
+    for name, n in (("pair", None), ("mixed", 3)):
+        b = make_workload(name) if n is None else make_workload(name, n_scen=n)
+        for k in range(b.n_scen):
+            g = oracle.global_qp(b, k)
+            ao = b.agent_off
+            e0 = b.x_init[ao[k]:ao[k + 1]] - b.x_ref[ao[k]:ao[k + 1]]
+            x0_term = float((e0 * e0 * b.Qd[ao[k]:ao[k + 1]]).sum())
+            J = oracle.objective(b, k, g["X"], g["U"])
+            assert abs((J - x0_term) - g["obj"]) <= 1e-11 * abs(g["obj"]), (name, k)
+
+
+def test_min_distance_matches_pairwise_distances():
+    from scipy.spatial.distance import pdist
+    b = make_workload("mixed", n_scen=3)
+    for k in range(b.n_scen):
+        o = oracle.admm(b, k, tol=0.0, max_iter=3)
+        pos = o["X"][:, 1:, :b.dp]
+        want = min(pdist(pos[:, t, :]).min() for t in range(pos.shape[1]))
+        assert oracle.min_distance(b, k, o["X"]) == pytest.approx(want, rel=1e-15)
+
+
+def test_sqp_fixed_point_is_a_local_optimum_of_the_nonconvex_problem():
+    """The loop's result on a crossing whose collision constraint binds is a
+    local minimizer of Eq. (1) with the exact constraint |p_it - p_jt| >= d_min
+    (not its linearization): SLSQP on that nonconvex problem, started at the
+    loop's inputs and at a perturbation of them, ends at the same inputs and
+    objective.  The stopping rule is also checked on the recorded objectives."""
+    p = _pair_with_active_collision()
+    r = oracle.sqp(p, 0, tol=1e-9, max_iter=20000, max_outer=30, obj_rtol=1e-12)
+    assert r["sqp_status"] == 0 and r["status"] == oracle.CONVERGED and r["outer"] >= 3
+    Js = r["objectives"]
+    assert abs(Js[-1] - Js[-2]) <= 1e-12 * abs(Js[-2])
+    assert all(abs(Js[m] - Js[m - 1]) > 1e-12 * abs(Js[m - 1]) for m in range(1, len(Js) - 1))
+    assert r["min_dist"] == pytest.approx(1.5, abs=1e-7)
+
+    N, T, nx, nu = 2, int(p.T[0]), p.nx, p.nu
+    A, B = p.A.reshape(nx, nx), p.B.reshape(nx, nu)
+
+    def states(u):
+        u = u.reshape(N, T, nu)
+        X = np.zeros((N, T + 1, nx))
+        X[:, 0] = p.x_init
+        for t in range(T):
+            X[:, t + 1] = X[:, t] @ A.T + u[:, t] @ B.T
+        return X
+
+    def cost(u):
+        X, uu = states(u), u.reshape(N, T, nu)
+        e = X - p.x_ref[:, None, :]
+        return (e[:, :T] ** 2 * p.Qd[:, None, :]).sum() + (uu ** 2 * p.Rd[:, None, :]).sum() + \
+            (e[:, T] ** 2 * p.Qfd).sum()
+
+    def separation(u):
+        d = states(u)[0, 1:, :2] - states(u)[1, 1:, :2]
+        return (d * d).sum(axis=1) - 1.5 ** 2
+
+    bounds = [(p.umin[c % nu], p.umax[c % nu]) for c in range(N * T * nu)]
+    u_sqp = r["U"].ravel()
+    assert cost(u_sqp) == pytest.approx(r["objective"], rel=1e-13)
+    rng = np.random.default_rng(5)
+    for u0 in (u_sqp, np.clip(u_sqp + 0.05 * rng.standard_normal(u_sqp.size), -1.0, 1.0)):
+        res = minimize(cost, u0, method="SLSQP", bounds=bounds, constraints=[{"type": "ineq", "fun": separation}],
+                       options=dict(ftol=1e-14, maxiter=1000))
+        assert res.fun >= r["objective"] * (1 - 1e-9)
+        assert abs(res.fun - r["objective"]) <= 1e-9 * r["objective"]
+        assert np.abs(res.x - u_sqp).max() <= 1e-4
+
+
+def test_sqp_stops_at_once_when_the_collision_constraint_is_slack():
+    """The stock crossing never comes within d_min = 0.5: the relinearized QP
+    has the same solution, so the loop stops at the second step with an
+    objective change at rounding level."""
+    p = make_workload("pair")
+    r = oracle.sqp(p, 0, tol=1e-4, max_iter=500, max_outer=5)
+    assert r["outer"] == 2 and r["sqp_status"] == 0
+    assert r["min_dist"] > 0.5
+    assert r["objectives"][1] == pytest.approx(r["objectives"][0], rel=1e-9)
