@@ -657,6 +657,7 @@ def sqp_loop(tg, torch, batch, args, max_outer=6):
     scenario and how many met the rule (only scenarios whose ADMM solve
     converged can)."""
     s = tg.Solver(batch, precision=64, adapt=(10, 10.0, 2.0))
+    tuned = s.autotune(probe_iter=60)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = s.sqp(tol=args.tol, max_iter=args.max_iter, max_outer=max_outer, obj_rtol=1e-4)
@@ -664,7 +665,7 @@ def sqp_loop(tg, torch, batch, args, max_outer=6):
     s.close()
     met = r["status"] == 0
     steps = np.bincount(r["outer"][met], minlength=max_outer + 1)[1:].tolist()
-    return {"ms_wall": wall, "max_outer": max_outer, "scenarios": int(batch.n_scen), "met_rule": int(met.sum()),
+    return {"ms_wall": wall, "launch": tuned, "max_outer": max_outer, "scenarios": int(batch.n_scen), "met_rule": int(met.sum()),
             "outer_steps_of_those": steps,
             "min_dist_over_d_min_of_those": float((r["min_dist"][met] / batch.d_min[met]).min()) if met.any() else None,
             "note": ("every outer step solves the whole batch (scenarios that met the rule keep their data); "
