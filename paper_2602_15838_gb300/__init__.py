@@ -356,10 +356,18 @@ def version() -> str:
     return lib().tadmm_version().decode()
 
 
-def solve(batch, tol: float = 1e-4, max_iter: int = 500, **kw):
-    """One-shot solve: returns (per-scenario results, solver)."""
+def solve(batch, tol: float = 1e-4, max_iter: int = 500, device: bool = False, **kw):
+    """One-shot solve.  device=False: returns (per-scenario results as numpy
+    arrays, solver).  device=True: returns (X, U, info, solver) with X and U
+    float64 CUDA tensors in the packed layouts of tadmm_get_solution and info
+    holding theta and W (CUDA tensors) and status, iters, res (numpy); the solver
+    stays open for backward() and is closed by the caller."""
     s = Solver(batch, **kw)
     s.solve(tol, max_iter)
+    if device:
+        sol = s.solution(device=True)
+        X, U = sol.pop("X"), sol.pop("U")
+        return X, U, sol, s
     return s.split(s.solution()), s
 
 

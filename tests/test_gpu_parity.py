@@ -835,3 +835,17 @@ def test_sqp_rejects_bad_arguments(tg):
         with pytest.raises(tg.TadmmError, match="tadmm_sqp"):
             s.sqp(**kw)
     s.close()
+
+
+def test_module_solve_returns_device_tensors(tg):
+    """tg.solve(..., device=True) gives float64 CUDA tensors equal to the host
+    results of the same solve."""
+    import torch
+    b = make_workload("mixed", n_scen=3)
+    X, U, info, s = tg.solve(b, 1e-4, 40, device=True)
+    host = s.solution()
+    s.close()
+    assert X.is_cuda and U.is_cuda and X.dtype == torch.float64
+    assert np.array_equal(X.cpu().numpy(), host["X"]) and np.array_equal(U.cpu().numpy(), host["U"])
+    assert np.array_equal(info["theta"].cpu().numpy(), host["theta"])
+    assert np.array_equal(info["status"], host["status"]) and np.array_equal(info["iters"], host["iters"])
