@@ -184,6 +184,10 @@ def profile_counters(tpc: int, variant: int):
     if int(kv.get("threads_per_cta", -1)) != tpc or variant not in variants:
         return None, "launch shape differs from the profiled ones"
     kv["dram_bytes_per_launch"] = kv["variant%d.dram_bytes_per_launch" % variant]
+    for key in ("executed_per_algorithmic_flop", "small_case"):
+        kv[key] = kv.get("variant%d.%s" % (variant, key), kv.get(key))
+    if kv.get("executed_per_algorithmic_flop") is None:
+        return None, "no executed-instruction counts for this variant"
     return kv, None
 
 

@@ -117,7 +117,8 @@ typedef struct {
   int32_t threads_per_cta; /* batched mode: threads per scenario CTA; 0 = tuned/default */
   int32_t ctas_per_sm;     /* batched mode: resident CTAs per SM; 0 = tuned/default */
   int32_t kernel_variant;  /* batched mode: register-budget variant 0..2 of the persistent kernel
-                              (0: no cap; 1: 32 threads x 12 CTAs/SM; 2: 64 threads x 8 CTAs/SM) */
+                              (0: no cap, small active-set rounds on lane groups; 1: 32 threads x
+                              12 CTAs/SM; 2: 64 threads x 8 CTAs/SM); results are the same bits */
   int32_t flags;           /* TADMM_FLAG_* bits; 0 = all optimizations on */
   /* Residual balancing of the penalty (an extension: the paper keeps rho fixed;
    * Boyd et al. 2011, Sec. 3.4.1).  Every adapt_every iterations (0 = off), after

@@ -936,8 +936,9 @@ __device__ EqpScan<F> eqp_solve(const AgentCtx<F, NX, NU, DP>& A) {
 // `go` marks the lanes whose agent takes the pass (at most NG of them, the
 // caller checks).  The owner lane receives its agent's scan.  Used by the
 // per-phase x-update kernels, where few agents share a warp and each agent's
-// recurrence latency sets the time; in the persistent kernel the FP64 pipe is
-// shared by eight warps per SM and a lane-group pass saves nothing.
+// recurrence latency sets the time, and by the register-unbounded variant 0 of
+// the persistent kernel for its later active-set rounds, which serve a few
+// agents of the warp (variant 1's 168-register budget leaves it out).
 template <typename F, int NX, int NU, int DP>
 __device__ EqpScan<F> eqp_coop(const AgentCtx<F, NX, NU, DP>& A, bool go) {
   constexpr unsigned FULL = 0xffffffffu;
@@ -2298,7 +2299,9 @@ __device__ void group_relaxed_sweep(const Dev<F>& D, GroupSm& gs, GroupStage<F, 
   }
 }
 
-template <typename F, int NX, int NU, int DP, bool DI>
+// COOP_EQP: active-set rounds that serve at most CoopShape<NX>::NG agents of the
+// warp take their EQP pass on lane groups (eqp_coop, the same bits as eqp_solve).
+template <typename F, int NX, int NU, int DP, bool DI, bool COOP_EQP = false>
 __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int* members, int G, GroupSm& gs,
                           GroupStage<F, DP>& st, F* sm, F* kcs) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -2364,7 +2367,8 @@ __device__ void run_group(const Dev<F>& D, const Model<F, NX, NU>& M, const int*
                                             : idle_agent<F, NX, NU, DP>(M, kcs + tid, nt, D.coop);
       const int as_max = D.as_max > 0 ? D.as_max : 10 * s.T * NU + 10;
       const F eps = D.eps_rel > 0 ? F(D.eps_rel) : (sizeof(F) == 8 ? F(1e-12) : F(1e-5));
-      const int st = xupdate_agent<F, NX, NU, DP, DI, false>(A, has, start_kind_of(D, k), as_max, eps, neqp, nfact);
+      const int st = xupdate_agent<F, NX, NU, DP, DI, COOP_EQP>(A, has, start_kind_of(D, k), as_max, eps, neqp,
+                                                                nfact);
       if (has && st) atomicMax(&gs.flag[my_m], st);
     }
     __syncthreads();

@@ -17,6 +17,8 @@ namespace tadmm {
 // ---------------------------------------------------------------------------
 // Register-budget variants of the persistent kernel (chosen by the autotuner):
 // (max threads per CTA, min resident CTAs per SM) for __launch_bounds__.
+// Variant 0, with no register cap, also runs small active-set rounds on lane
+// groups (COOP_EQP of run_group); the results are the same bits either way.
 template <int V> struct KVariant;
 template <> struct KVariant<0> { static constexpr int maxt = 256, minb = 1; };
 template <> struct KVariant<1> { static constexpr int maxt = 32, minb = 12; };
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(KVariant<V>::maxt, KVariant<V>::minb) k_batche
       const ScenMeta s = D.meta[sc];
       run_scenario<F, NX, NU, DP, DI>(D, M, s, sc, cs, sm, D.sm_pairs, kcs);
     } else {
-      run_group<F, NX, NU, DP, DI>(D, M, D.gmem + b0, G, gs, gst, sm, kcs);
+      run_group<F, NX, NU, DP, DI, (V == 0)>(D, M, D.gmem + b0, G, gs, gst, sm, kcs);
     }
   }
 }
