@@ -241,8 +241,10 @@ int tadmm_get_penalty(tadmm_handle* h, double* rho_final, int32_t* rho_changes);
 
 /* Times the candidate launch shapes of the batched persistent kernel (threads
  * per CTA, resident CTAs per SM, register-budget variant) on this batch with
- * `probe_iter` ADMM iterations each and keeps the fastest.  Synchronous.
- * Writes the choice to the non-NULL outputs. */
+ * `probe_iter` ADMM iterations each, times the three fastest again over
+ * 4 x probe_iter iterations and keeps the fastest of those.  Synchronous; the
+ * probe solves overwrite the last solution.  Writes the choice to the non-NULL
+ * outputs; on an error the previous shape is kept. */
 int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream, int32_t* threads_out,
                    int32_t* ctas_out, int32_t* variant_out);
 

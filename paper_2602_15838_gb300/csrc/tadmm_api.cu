@@ -780,11 +780,28 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_t = 128, best_c = 0, best_v = 0;
+  const int keep_t = h->tpc, keep_c = h->cps, keep_v = h->variant;
+  struct Shape { int v, tpc, cps; float ms; };
+  // device time of the last of `reps` solves of `iters` iterations (tol 0) in shape sh
+  auto time_shape = [&](const Shape& sh, int iters, int reps, float& ms) -> int {
+    h->variant = sh.v;
+    h->tpc = sh.tpc;
+    h->cps = sh.cps;
+    int rc = TADMM_OK;
+    for (int rep = 0; rep < reps && rc == TADMM_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = tadmm_solve(h, 0.0, iters, stream);
+      cudaEventRecord(e1, st);
+      if (rc == TADMM_OK) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
+      if (rc == TADMM_OK) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    return rc;
+  };
   struct Cand { int v, tpc; };
   const Cand cands[] = {{0, 32}, {0, 64}, {0, 128}, {1, 32}, {2, 64}};
+  std::vector<Shape> probed;
   int rc = TADMM_OK;
+  // stage 1: every candidate shape over probe_iter iterations
   for (const Cand& cd : cands) {
     const int tpc = cd.tpc;
     auto occ = [&]() -> int { TADMM_DISPATCH(h, max_ctas_per_sm(tpc, cd.v, h)); };
@@ -793,36 +810,43 @@ extern "C" int tadmm_autotune(tadmm_handle* h, int32_t probe_iter, void* stream,
     std::vector<int> cps_list = {maxc};
     if (maxc >= 4) cps_list.push_back(maxc / 2);
     for (int cps : cps_list) {
-      h->variant = cd.v;
-      h->tpc = tpc;
-      h->cps = cps;
-      float ms = 0;
-      for (int rep = 0; rep < 2 && rc == TADMM_OK; ++rep) {
-        cudaEventRecord(e0, st);
-        rc = tadmm_solve(h, 0.0, probe_iter, stream);
-        cudaEventRecord(e1, st);
-        if (rc == TADMM_OK) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
-        if (rc == TADMM_OK) cudaEventElapsedTime(&ms, e0, e1);
-      }
-      if (rc) break;
-      if (ms < best) {
-        best = ms;
-        best_t = tpc;
-        best_c = cps;
-        best_v = cd.v;
-      }
+      Shape sh{cd.v, tpc, cps, 0.0f};
+      if ((rc = time_shape(sh, probe_iter, 2, sh.ms))) break;
+      probed.push_back(sh);
     }
     if (rc) break;
   }
+  // stage 2: the three fastest again over 4 x probe_iter iterations, since the
+  // ranking of close shapes can change once the active-set transient of the
+  // first iterations has passed
+  Shape best{0, 128, 0, 1e30f};
+  if (rc == TADMM_OK && !probed.empty()) {
+    std::stable_sort(probed.begin(), probed.end(), [](const Shape& a, const Shape& b) { return a.ms < b.ms; });
+    best = probed[0];
+    const size_t nfin = std::min<size_t>(3, probed.size());
+    if (nfin > 1) {
+      best.ms = 1e30f;
+      for (size_t k = 0; k < nfin && rc == TADMM_OK; ++k) {
+        Shape sh = probed[k];
+        if ((rc = time_shape(sh, probe_iter > (1 << 28) ? probe_iter : 4 * probe_iter, 1, sh.ms))) break;
+        if (sh.ms < best.ms) best = sh;
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc) return rc;
-  h->tpc = best_t;
-  h->cps = best_c;
-  h->variant = best_v;
-  if (threads_out) *threads_out = best_t;
-  if (ctas_out) *ctas_out = best_c;
-  if (variant_out) *variant_out = best_v;
+  if (rc || probed.empty()) {
+    h->tpc = keep_t;
+    h->cps = keep_c;
+    h->variant = keep_v;
+    return rc ? rc : set_error(TADMM_EINVAL, "no launch shape fits this batch");
+  }
+  h->tpc = best.tpc;
+  h->cps = best.cps;
+  h->variant = best.v;
+  if (threads_out) *threads_out = best.tpc;
+  if (ctas_out) *ctas_out = best.cps;
+  if (variant_out) *variant_out = best.v;
   return TADMM_OK;
 }
 
